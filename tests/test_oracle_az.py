@@ -1,0 +1,172 @@
+"""Pins for oracle.az: Algorithm 1 against the dense TSVD solve, the paper's
+printed numbers (tests/golden/paper_values.txt) and Theorem 4.6's rank bound."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.az import AZ, direct_tsvd, relres
+from oracle.operators import Operator
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "paper_values.txt")
+
+
+def paper_value(key):
+    for line in open(GOLD):
+        line = line.split("#")[0].split()
+        if line and line[0] == key:
+            return float(line[1])
+    raise KeyError(key)
+
+
+def epsh_from_tau0(tau0):
+    # Eq. constant_shapeparam: eps = c N, c = pi / (2 T sqrt(2 log(1 + tau0^-2)));
+    # with h = 2T/N this is eps*h = pi / sqrt(2 log(1 + tau0^-2)).
+    return math.pi / math.sqrt(2 * math.log(1 + tau0 ** -2))
+
+
+def test_config1_az_matches_direct_tsvd():
+    p = W.config1()
+    op = Operator(p.grid, p.mask)
+    b = p.rhs()
+    x = AZ(op, p.k, 1, 1e-12).solve(b)
+    xd, _ = direct_tsvd(op.A_dense(), b, 1e-12)
+    r_az, r_d = relres(op, x, b)[0], relres(op, xd, b)[0]
+    assert abs(r_az - r_d) <= 1e-11
+    # the Gaussian saturation floor at eps*h = 1 (alias ratio ~ exp(-pi^2))
+    assert 5e-5 < r_d < 5e-4
+
+
+def test_algorithm1_dense_bruteforce():
+    # Algorithm 1 with every operator formed densely (Z* = pinv(A^c) E).
+    g = W.Grid(1, (40,), (2,), (1.0,), 1.0)
+    m = W.interval_mask(g, -0.45, 0.55)
+    op = Operator(g, m)
+    A = op.A_dense()
+    Z = op.Zstar_dense()
+    # tau = 1e-8 keeps only well-separated singular directions, so the
+    # coefficients themselves (not only the residual) are reproducible.
+    az = AZ(op, 16, 5, 1e-8)
+    Y = (A - A @ Z @ A) @ az.R
+    assert np.abs(Y - az.Y).max() <= 1e-12 * np.abs(Y).max()
+    b = np.cos(3 * W.kept_points(g, m))
+    U, s, Vt = np.linalg.svd(Y, full_matrices=False)
+    r = int(np.sum(s > 1e-8 * s[0]))
+    assert r == az.rank
+    u = Vt[:r].T @ (U[:, :r].T @ (b - A @ Z @ b) / s[:r, None])
+    x2 = az.R @ u
+    x = Z @ (b - A @ x2) + x2
+    assert np.abs(x - az.solve(b)).max() <= 1e-6 * np.abs(x).max()
+    assert abs(relres(op, x, b)[0] - relres(op, az.solve(b), b)[0]) < 1e-13
+
+
+@pytest.mark.parametrize("N", [64, 128, 256])
+def test_E1_periodic_max_error(N):
+    # Sec. 3.3: f = sin([N/5] pi x) on the whole box T=1, s=3, tau0=1e-10.
+    epsh = epsh_from_tau0(1e-10)
+    g = W.Grid(1, (N,), (3,), (1.0,), epsh)
+    op = Operator(g, np.ones(g.Ltot, np.uint8))
+    fq = math.floor(N / 5)
+    b = np.sin(fq * math.pi * W.grid_coords(g, 0))[:, None]
+    # The periodic problem is solved by the plain inverse Z* (Sec. 3.1).
+    a = op.Zstar(b)
+    gf = W.Grid(1, (N,), (16,), (1.0,), epsh)
+    opf = Operator(gf, np.ones(gf.Ltot, np.uint8))
+    err = np.abs(opf.Ac(a)[:, 0] - np.sin(fq * math.pi * W.grid_coords(gf, 0))).max()
+    assert err < paper_value("E1_max_error_bound")
+    if N == 256:
+        ratio = np.linalg.norm(a) / math.sqrt(N)
+        assert abs(ratio - paper_value("E1_coef_norm_over_sqrtN")) < 1.0
+
+
+def _perturbation_rank(N, delta, epsh=1.0):
+    g = W.Grid(1, (N,), (2,), (1.0,), epsh)
+    op = Operator(g, W.interval_mask(g, -0.5, 0.5))
+    A = op.A_dense()
+    Z = op.Zstar_dense()
+    s = np.linalg.svd(A - A @ Z @ A, compute_uv=False)
+    return int(np.sum(s > delta * np.linalg.norm(A, 2)))
+
+
+def test_E2_rank_constant_in_N_and_theorem_bound():
+    delta = 1e-8
+    ranks = [_perturbation_rank(N, delta) for N in (128, 256, 512, 1024)]
+    assert len(set(ranks)) == 1
+    # Theorem 4.6: rank <= 4W, W = (1/pi) sqrt(-2 log(delta) log(1 + tau0^-2)),
+    # with log(1 + tau0^-2) = pi^2 / (2 (eps h)^2) from Eq. constant_shapeparam.
+    W4 = 4 * math.sqrt(-math.log(delta)) / 1.0
+    assert ranks[0] <= W4
+    assert abs(ranks[0] - paper_value("E2_plunge_size")) <= 2
+
+
+@pytest.mark.parametrize("kind", ["approx", "poisson"])
+def test_whole_box_reduces_to_Zstar(kind):
+    g = W.Grid(1 if kind == "approx" else 2, (64,) if kind == "approx" else (12, 12),
+               (2,) if kind == "approx" else (2, 2), (1.0,) if kind == "approx" else (1.0, 1.0), 1.0)
+    op = Operator(g, np.ones(g.Ltot, np.uint8), kind=kind)
+    b = np.random.default_rng(4).standard_normal((op.M, 2))
+    az = AZ(op, 8, 9, 1e-12)
+    assert az.rank == 0
+    x = az.solve(b)
+    z = op.Zstar(b)
+    assert np.abs(x - z).max() <= 1e-12 * np.abs(z).max()
+
+
+def test_2d_disc_az_matches_direct():
+    p = W.config3(n=16, k=260)
+    op = Operator(p.grid, p.mask)
+    b = p.rhs()
+    # In 2D the two truncations act on different matrices (Y vs A) with many
+    # singular values in the transition region; the residuals agree to ~1%.
+    for tau in (1e-8, 1e-12):
+        x = AZ(op, p.k, 11, tau).solve(b)
+        xd, _ = direct_tsvd(op.A_dense(), b, tau)
+        r2, r1 = relres(op, x, b)[0], relres(op, xd, b)[0]
+        assert abs(r2 - r1) <= 0.03 * r1 and r1 < 1e-3
+
+
+def test_poisson_az_matches_direct():
+    p = W.config4(n=16, nb=64, k=300)
+    op = Operator(p.grid, p.mask, "poisson", p.boundary, p.weight)
+    b = np.concatenate([p.rhs() / (2 * op.eps ** 2), p.weight * p.boundary_rhs()])
+    for tau in (1e-8, 1e-12):
+        x = AZ(op, p.k, 11, tau).solve(b)
+        xd, _ = direct_tsvd(op.A_dense(), b, tau)
+        r2, r1 = relres(op, x, b)[0], relres(op, xd, b)[0]
+        assert abs(r2 - r1) <= 0.05 * r1 and r1 < 2e-3
+
+
+def test_refinement_keeps_relres():
+    p = W.config1()
+    op = Operator(p.grid, p.mask)
+    b = p.rhs()
+    az = AZ(op, p.k, 1, 1e-12)
+    r0 = relres(op, az.solve(b), b)[0]
+    r1 = relres(op, az.solve(b, refine=1), b)[0]
+    assert abs(r0 - r1) < 1e-10
+
+
+@pytest.mark.slow
+def test_E6_ellipse_linf_error():
+    # Sec. 5.4: ellipse x^2 + 4 y^2 <= 1, T = (1.4, 0.7), s = 2, tau0 = 1e-5,
+    # N = 100 x 50, f = sin(N^x/10 x + N^y/10 y).  Sketch width 2400 (the
+    # paper's 22 sqrt(N) - 120 = 1435 saturates at tau = 1e-12 here).
+    Nx, Ny = 100, 50
+    epsh = epsh_from_tau0(1e-5)
+    g = W.Grid(2, (Nx, Ny), (2, 2), (1.4, 0.7), epsh)
+    X, Y = np.meshgrid(W.grid_coords(g, 0), W.grid_coords(g, 1), indexing="ij")
+    m = (X ** 2 + 4 * Y ** 2 <= 1).astype(np.uint8)
+    op = Operator(g, m)
+    f = lambda p: np.sin(Nx / 10 * p[:, 0] + Ny / 10 * p[:, 1])
+    b = f(W.kept_points(g, m))[:, None]
+    x = AZ(op, 2400, 7, 1e-12).solve(b)
+    gf = W.Grid(2, (Nx, Ny), (8, 8), (1.4, 0.7), epsh)
+    opf = Operator(gf, np.ones(gf.Ltot, np.uint8))
+    Xf, Yf = np.meshgrid(W.grid_coords(gf, 0), W.grid_coords(gf, 1), indexing="ij")
+    inside = (Xf ** 2 + 4 * Yf ** 2 <= 1).reshape(-1)
+    pts = np.stack([Xf.reshape(-1), Yf.reshape(-1)], 1)[inside]
+    err = np.abs(opf.Ac(x)[:, 0][inside] - f(pts)).max()
+    ref = paper_value("E6_linf_error")
+    assert ref / 2.5 < err < 2.5 * ref
