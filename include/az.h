@@ -1,0 +1,173 @@
+/*
+ * az.h -- C ABI of the GB300 AZ solver for oversampled periodised-Gaussian RBF
+ * least-squares systems (Zhou & Huybrechs, "Efficient least squares
+ * approximation and collocation methods using radial basis functions",
+ * arXiv 2308.14490).
+ *
+ * Problem (Sec. 2.2-2.3, Sec. 5.1-5.2): N equispaced centers per box
+ * [-T_d, T_d] (Eq. set_centers), an s-fold oversampled grid of L = s N points
+ * (Eq. set_Xtilde), the kept points X = grid ∩ Omega (Eqs. set_X, set_X_2d) and
+ * the rectangular system A a ≈ b with A_ij = phi_per_j(x_i), phi the Gaussian
+ * exp(-eps^2 r^2) (Eq. rbf) periodised over the box (Eq. periodic_rbf).
+ * Solver: Algorithm 1 (AZ) with Z* the plain inverse of the full-box problem
+ * (Sec. 3.1 Eq. B_pinv, Sec. 3.2.2) and a randomised truncated solve of the
+ * low-rank step 1 (Sec. 3.2.3).
+ *
+ * Conventions shared by every entry point
+ *  - Array arguments whose name ends in _dev are DEVICE pointers owned by the
+ *    caller; the library never frees them.  The handle owns only its internal
+ *    buffers (symbols, index maps, sketch factors, workspace).
+ *  - Matrices are column-major with a leading dimension >= the row count.
+ *  - Row order of right-hand sides: the kept grid points in lexicographic order
+ *    of the grid index (1D: increasing i; 2D: i = ix*Ly + iy, x-major, the
+ *    paper's j = (m-1) N^y + n ordering of Sec. 5.1), followed, for
+ *    collocation, by the boundary points in the order given.
+ *  - Coefficient order: j (1D) or jx*Ny + jy (2D).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls are stream-ordered and asynchronous except where noted
+ *    (az_setup synchronises once to learn M; a non-NULL relres_host forces a
+ *    synchronisation).
+ *  - No exception crosses the ABI.  Every failure returns a status and sets a
+ *    thread-local message readable with az_last_error().
+ *  - Supported sizes: dim 1 or 2; n[d] and s[d] powers of two; s[d] <= 8;
+ *    L per dimension <= 2^24 (1D) or <= 4096 (2D).  Other sizes return
+ *    AZ_ERR_ARG.
+ */
+#ifndef AZ_GB300_H
+#define AZ_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct az_setup_t* az_handle;
+
+typedef enum {
+  AZ_OK = 0,
+  AZ_ERR_ARG = 1,        /* invalid argument or unsupported size */
+  AZ_ERR_OOM = 2,        /* device allocation failed */
+  AZ_ERR_ADMISSION = 3,  /* footprint above the caller's budget */
+  AZ_ERR_CUDA = 4,       /* a CUDA runtime call or kernel launch failed */
+  AZ_ERR_NUMERIC = 5,    /* non-finite values, or the factorisation broke down */
+  AZ_ERR_TIMEOUT = 6     /* a bounded device wait gave up */
+} az_status;
+
+enum { AZ_FP64 = 0, AZ_MIXED = 1 };
+enum { AZ_GAUSS = 0, AZ_NEG_LAPLACE_GAUSS = 1 };
+
+typedef struct {
+  int32_t dim;     /* 1 or 2 */
+  int64_t n[2];    /* centers per dimension (N_x, N_y); n[1] ignored in 1D */
+  int32_t s[2];    /* oversampling factor per dimension (Eq. set_Xtilde) */
+  double T[2];     /* half box widths: box = prod_d [-T_d, T_d] */
+} az_grid;
+
+typedef struct {
+  int32_t precision;    /* AZ_FP64, or AZ_MIXED: FP32 transforms/sketch, FP64 factor work and residual */
+  int32_t k;            /* sketch width r + p (number of random columns, Sec. 3.2.3) */
+  double tau_svd;       /* relative truncation of the low-rank solve (0 = default: 1e-8) */
+  double tau_sym;       /* symbol truncation: S_k^{-1} := 0 if S_k <= tau_sym^2 max S (0 = exact) */
+  uint64_t seed;        /* Philox key of the random test matrix */
+  int32_t refine_steps; /* FP64-residual refinement steps per solve (default 1 in MIXED, 0 in FP64) ; -1 = default */
+} az_options;
+
+typedef struct {
+  int64_t N;            /* number of coefficients */
+  int64_t L;            /* grid points of the full box */
+  int64_t M;            /* kept grid points */
+  int64_t Mb;           /* boundary rows (collocation) */
+  int32_t k;            /* sketch width */
+  int32_t rank;         /* numerical rank kept by the truncated solve */
+  int32_t rank_gram;    /* directions kept by the first (Gram) orthogonalisation pass */
+  int32_t precision;
+  double sigma_max;     /* largest singular value of the sketch Y */
+  double sigma_min_kept;/* smallest kept singular value */
+  size_t device_bytes;  /* bytes held by the handle */
+} az_info_t;
+
+/* Build a solver for one problem.  (Sec. 3.2.3 "Step 0" and step 1's sketch.)
+ *   g               grid description (copied).
+ *   omega_mask_dev  uint8, one byte per grid point in grid-index order, 1 = in
+ *                   Omega.  Required.
+ *   boundary_pts_dev  double, n_boundary x dim row-major (x, y pairs) or NULL.
+ *   eps             Gaussian shape parameter (> 0).
+ *   kernel          AZ_GAUSS (approximation, Sec. 2-5) or AZ_NEG_LAPLACE_GAUSS
+ *                   (Poisson collocation -Lap u = f, Sec. 6.2 with k0 = 0; rows
+ *                   divided by 2 eps^2, the normalisation of Example 6.1).
+ *   boundary_weight weight w of the Dirichlet rows (collocation), else ignored.
+ *   opt             options (copied); NULL = defaults.
+ *   out             receives the handle.
+ * Synchronises `stream` once (to learn M).  Errors: AZ_ERR_ARG for bad sizes
+ * or pointers, AZ_ERR_OOM, AZ_ERR_CUDA, AZ_ERR_NUMERIC. */
+az_status az_setup(const az_grid* g, const uint8_t* omega_mask_dev, const double* boundary_pts_dev,
+                   int64_t n_boundary, double eps, int32_t kernel, double boundary_weight,
+                   const az_options* opt, void* stream, az_handle* out);
+
+/* Least-squares solve A x ≈ b for nrhs right-hand sides (Algorithm 1, plus
+ * `refine_steps` steps x += AZ(b - A x) with the residual in FP64).
+ *   b_dev  (M [+ Mb]) x nrhs, leading dimension ldb, FP64.
+ *   x_dev  N x nrhs, leading dimension ldx, FP64 (overwritten).
+ *   relres_host  optional host array of nrhs: ||A x - b|| / ||b|| (forces a sync). */
+az_status az_solve(az_handle h, const double* b_dev, int64_t ldb, int64_t nrhs, double* x_dev,
+                   int64_t ldx, void* stream, double* relres_host);
+
+/* Poisson collocation solve (Sec. 6.2): interior data f at the M kept points
+ * and Dirichlet data g at the Mb boundary points; the interior rows and f are
+ * divided by 2 eps^2 and the boundary rows and g multiplied by the setup's
+ * boundary weight before the least-squares solve.  Requires a setup with
+ * kernel = AZ_NEG_LAPLACE_GAUSS. */
+az_status az_collocate(az_handle h, const double* f_int_dev, int64_t ldf, const double* g_bnd_dev,
+                       int64_t ldg, int64_t nrhs, double* x_dev, int64_t ldx, void* stream,
+                       double* relres_host);
+
+/* Values of the expansion sum_j x_j phi_j on the s_test-fold refinement of the
+ * box grid ((s_test N_d) points per dimension, grid-index order), FP64.
+ *   out_dev  (prod_d s_test N_d) x nrhs, leading dimension ldo. */
+az_status az_evaluate(az_handle h, const double* x_dev, int64_t ldx, int64_t nrhs, int32_t s_test,
+                      double* out_dev, int64_t ldo, void* stream);
+
+/* Operator applications in FP64 (the paper's A and Z*, for tests and users).
+ *   az_apply_A:     y = A x    (x: N x nrhs, y: (M+Mb) x nrhs)   Sec. 2.3, Sec. 6.2
+ *   az_apply_Zstar: x = Z* y   (y: (M+Mb) x nrhs, x: N x nrhs)    Sec. 3.2.2 (boundary columns zero) */
+az_status az_apply_A(az_handle h, const double* x_dev, int64_t ldx, int64_t nrhs, double* y_dev,
+                     int64_t ldy, void* stream);
+az_status az_apply_Zstar(az_handle h, const double* y_dev, int64_t ldy, int64_t nrhs, double* x_dev,
+                         int64_t ldx, void* stream);
+
+/* Copies of internal arrays (device destination pointers, FP64):
+ *   AZ_ARRAY_SYMBOL  the full-box symbol Ghat on the grid in natural frequency
+ *                    order (L values; 2D: [kx][ky]) -- Lemma 4.2 / Eq. explicit_d
+ *   AZ_ARRAY_SKETCH  Y = (I - A Z*) A R, (M+Mb) x k, ld = M+Mb     -- Sec. 3.2.3
+ *   AZ_ARRAY_W       W = (I - Z* A) R, N x k, ld = N
+ *   AZ_ARRAY_R       the Rademacher test matrix R, N x k, ld = N (+1/-1)
+ *   AZ_ARRAY_UT      U_tau, (M+Mb) x rank, ld = M+Mb (orthonormal basis kept)
+ *   AZ_ARRAY_SIGMA   the kept singular values (rank values)
+ *   AZ_ARRAY_KEPT    the kept grid indices (M values, as doubles) */
+enum { AZ_ARRAY_SYMBOL = 0, AZ_ARRAY_SKETCH = 1, AZ_ARRAY_W = 2, AZ_ARRAY_R = 3, AZ_ARRAY_UT = 4,
+       AZ_ARRAY_SIGMA = 5, AZ_ARRAY_KEPT = 6 };
+az_status az_get_array(az_handle h, int32_t which, double* dst_dev, void* stream);
+
+az_status az_get_info(az_handle h, az_info_t* info);
+
+/* Device bytes a setup of this size would hold (symbols, maps, sketch and
+ * factors, plus the workspace for `nrhs_max` simultaneous right-hand sides). */
+az_status az_query_footprint(const az_grid* g, int64_t M, int64_t n_boundary, const az_options* opt,
+                             int64_t nrhs_max, size_t* bytes);
+
+void az_destroy(az_handle h);
+
+/* Thread-local text of the last failure in this thread ("" if none). */
+const char* az_last_error(void);
+
+/* The Rademacher test matrix alone: R (N x k, ld = N, FP64 +1/-1) from the
+ * Philox4x32-10 layout counter = (row/128, column, 0, 0), key = (seed low,
+ * seed high), bit (row % 32) of word ((row % 128)/32), set = +1. */
+az_status az_rademacher(int64_t N, int32_t k, uint64_t seed, double* R_dev, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,758 @@
+// C ABI of the AZ solver (include/az.h): handle lifecycle and the host-side
+// orchestration of the kernels, all stream-ordered.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "lowrank.cuh"
+
+namespace az {
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace az
+
+using namespace az;
+
+struct az_setup_t {
+  Geom g{};
+  int kind = 0, precision = AZ_MIXED, k = 0, refine = 1;
+  double eps = 0, tau_svd = 1e-8, tau_sym = 0, bweight = 1.0, floor = 0;
+  uint64_t seed = 0;
+  int64_t M = 0, Mb = 0, Mtot = 0;
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  int32_t* pos2m = nullptr;
+  int32_t* idx = nullptr;
+  double* bpts = nullptr;
+  double* Ghat = nullptr;
+  double* S = nullptr;
+  double* H64 = nullptr;
+  float* H32 = nullptr;
+  double* taps64[4] = {nullptr, nullptr, nullptr, nullptr};  // x0, y0, x2, y2
+  float* taps32[4] = {nullptr, nullptr, nullptr, nullptr};
+  int W32[2] = {0, 0}, W64[2] = {0, 0};
+  double2* tw64 = nullptr;
+  float2* tw32 = nullptr;
+  double2* big64[4] = {nullptr, nullptr, nullptr, nullptr};  // A_L, B_L, A_N, B_N
+  float2* big32[4] = {nullptr, nullptr, nullptr, nullptr};
+  uint32_t* bits = nullptr;
+  int64_t nw = 0;
+  void* W = nullptr;    // N x k   (T)
+  void* Y = nullptr;    // Mtot x k (T)
+  void* Ut = nullptr;   // Mtot x k (T), zero beyond rank
+  double *G = nullptr, *V = nullptr, *lam = nullptr, *B1 = nullptr, *Tm = nullptr, *VS = nullptr, *sig = nullptr;
+  double* partial = nullptr;
+  FactorInfo* info = nullptr;
+  // workspace (precision T)
+  int pairs_max = 0;
+  void* X1 = nullptr;   // pairs_max x L complex
+  void* X3 = nullptr;   // pairs_max x N complex
+  void* zb = nullptr;   // N x 2 pairs_max (T)
+  void* gb = nullptr;   // Mtot x 2 pairs_max (T)
+  void* rb = nullptr;   // Mtot x 2 pairs_max (T) residual
+  double* cb = nullptr; // k x 2 pairs_max
+  double* ub = nullptr;
+  double* normb = nullptr;  // 2 x 2 pairs_max
+  // FP64 scratch for az_apply_Zstar in mixed mode
+  void* X1d = nullptr;
+  void* X3d = nullptr;
+};
+
+namespace {
+
+template <typename T> struct Prec;
+template <> struct Prec<float> { static constexpr bool fp64 = false; };
+template <> struct Prec<double> { static constexpr bool fp64 = true; };
+
+az_status dalloc(az_setup_t* h, void** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+    return AZ_ERR_OOM;
+  }
+  h->allocs.push_back(*p);
+  h->bytes += bytes;
+  return AZ_OK;
+}
+template <typename P> az_status dalloc_t(az_setup_t* h, P** p, size_t count) {
+  return dalloc(h, (void**)p, count * sizeof(P));
+}
+
+bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+int ilog2(int64_t v) { int l = 0; while ((int64_t(1) << l) < v) ++l; return l; }
+
+// Half-width W (grid units) such that the periodised samples beyond W are below
+// delta * g(0): the Gaussian exp(-(eps m h_L)^2) decays below delta past
+// m = sqrt(ln(1/delta)) / (eps h_L); for phi'' the polynomial factor is covered by
+// two extra points.
+int stencil_halfwidth(double eps, double hL, double delta, int64_t Ld, bool deriv) {
+  int W = (int)std::ceil(std::sqrt(std::log(1.0 / delta)) / (eps * hL)) + (deriv ? 2 : 0);
+  int64_t lim = (Ld - 1) / 2;
+  return (int)std::min<int64_t>(W, lim);
+}
+
+int image_count(double eps, double T) {
+  int p = 1;
+  while ((eps * (2 * p - 1) * T) * (eps * (2 * p - 1) * T) < 700.0) ++p;
+  return p + 1;
+}
+
+az_status make_geom(const az_grid* gr, Geom& g) {
+  std::memset(&g, 0, sizeof(g));
+  if (!gr || (gr->dim != 1 && gr->dim != 2)) { set_error("dim must be 1 or 2"); return AZ_ERR_ARG; }
+  g.dim = gr->dim;
+  for (int d = 0; d < 2; ++d) {
+    bool used = d < g.dim;
+    g.n[d] = used ? gr->n[d] : 1;
+    g.s[d] = used ? gr->s[d] : 1;
+    g.T[d] = used ? gr->T[d] : 1.0;
+    if (used && (!is_pow2(g.n[d]) || !is_pow2(g.s[d]) || g.s[d] > 8 || !(g.T[d] > 0))) {
+      set_error("n and s must be powers of two (s <= 8) and T > 0");
+      return AZ_ERR_ARG;
+    }
+    g.Ld[d] = g.n[d] * g.s[d];
+  }
+  g.N = g.n[0] * g.n[1];
+  g.L = g.Ld[0] * g.Ld[1];
+  if (g.dim == 1) {
+    if (g.L < 4 || g.L > (int64_t(1) << 24) || g.N < 2) { set_error("1D grid size out of range (4 <= L <= 2^24)"); return AZ_ERR_ARG; }
+    int lL = ilog2(g.L);
+    g.logD1 = (lL + 1) / 2;
+    g.logD0 = lL - g.logD1;
+    g.D1 = 1 << g.logD1;
+    g.D0 = 1 << g.logD0;
+    if (g.D1 < g.s[0]) { set_error("grid too small for the oversampling factor"); return AZ_ERR_ARG; }
+    g.N1 = g.D1 / g.s[0];
+    g.G0 = g.D0;
+    g.Rg = 1; g.Rstride = 0; g.Fq = g.s[0];
+  } else {
+    if (g.Ld[0] > 4096 || g.Ld[1] > 4096 || g.Ld[0] < 2 || g.Ld[1] < 2) { set_error("2D grid: L per dimension must be in [2, 4096]"); return AZ_ERR_ARG; }
+    g.D0 = (int)g.Ld[0]; g.D1 = (int)g.Ld[1];
+    g.logD0 = ilog2(g.D0); g.logD1 = ilog2(g.D1);
+    g.G0 = (int)g.n[0]; g.N1 = (int)g.n[1];
+    g.Rg = g.s[0]; g.Rstride = (int)g.n[0]; g.Fq = g.s[1];
+  }
+  g.logN1 = ilog2(g.N1);
+  g.logG0 = ilog2(g.G0);
+  return AZ_OK;
+}
+
+
+template <typename T> PassTabs tabs(az_setup_t* h) {
+  PassTabs t;
+  if (Prec<T>::fp64) { t.tw = h->tw64; t.bigA = h->big64[0]; t.bigB = h->big64[1]; t.bigNA = h->big64[2]; t.bigNB = h->big64[3]; }
+  else { t.tw = h->tw32; t.bigA = h->big32[0]; t.bigB = h->big32[1]; t.bigNA = h->big32[2]; t.bigNB = h->big32[3]; }
+  return t;
+}
+template <typename T> const T* Hsym(az_setup_t* h);
+template <> const double* Hsym<double>(az_setup_t* h) { return h->H64; }
+template <> const float* Hsym<float>(az_setup_t* h) { return h->H32; }
+
+template <typename T> StencilTaps taps(az_setup_t* h) {
+  StencilTaps t;
+  if (Prec<T>::fp64) { t.x0 = h->taps64[0]; t.y0 = h->taps64[1]; t.x2 = h->taps64[2]; t.y2 = h->taps64[3]; t.Wx = h->W64[0]; t.Wy = h->W64[1]; }
+  else { t.x0 = h->taps32[0]; t.y0 = h->taps32[1]; t.x2 = h->taps32[2]; t.y2 = h->taps32[3]; t.Wx = h->W32[0]; t.Wy = h->W32[1]; }
+  if (h->g.dim == 1) { t.y0 = t.x0; t.y2 = t.x2; t.Wy = t.Wx; }
+  return t;
+}
+
+// Tables for the four-step twiddles: w_n^m = A[m >> 12] * B[m & 4095], m < n.
+az_status big_tables(az_setup_t* h, int64_t n, double2** A64, double2** B64, float2** A32, float2** B32,
+                     cudaStream_t st) {
+  int64_t na = std::max<int64_t>(1, (n + 4095) / 4096);
+  std::vector<double2> a(na), b(4096);
+  std::vector<float2> af(na), bf(4096);
+  std::vector<double> re, im;
+  // exact-reduced twiddles via the 4096 table builder generalised to length n
+  for (int64_t q = 0; q < na; ++q) {
+    // angle of w_n^(4096 q)
+    int64_t m = (4096 * q) % n;
+    std::vector<double> r1, i1;
+    // reuse host_twiddles semantics through a tiny local computation
+    double ang = 2.0 * M_PI * (double)m / (double)n;
+    (void)ang;
+    r1.resize(1); i1.resize(1);
+    {
+      // exp(-2 pi i m / n) with octant reduction
+      int64_t aa = 2 * m, bb = n;
+      bool ns = false, nc = false, sw = false;
+      if (aa > bb) { aa = 2 * bb - aa; ns = true; }
+      if (2 * aa > bb) { aa = bb - aa; nc = true; }
+      if (4 * aa > bb) { aa = bb - 2 * aa; bb = 2 * bb; sw = true; }
+      double x = M_PI * (double)aa / (double)bb, c = std::cos(x), s = std::sin(x);
+      if (sw) std::swap(c, s);
+      if (nc) c = -c;
+      if (ns) s = -s;
+      a[q] = make_double2(c, -s);
+    }
+  }
+  for (int64_t r = 0; r < 4096; ++r) {
+    int64_t m = r % n;
+    int64_t aa = 2 * m, bb = n;
+    bool ns = false, nc = false, sw = false;
+    if (aa > bb) { aa = 2 * bb - aa; ns = true; }
+    if (2 * aa > bb) { aa = bb - aa; nc = true; }
+    if (4 * aa > bb) { aa = bb - 2 * aa; bb = 2 * bb; sw = true; }
+    double x = M_PI * (double)aa / (double)bb, c = std::cos(x), s = std::sin(x);
+    if (sw) std::swap(c, s);
+    if (nc) c = -c;
+    if (ns) s = -s;
+    b[r] = make_double2(c, -s);
+  }
+  for (int64_t q = 0; q < na; ++q) af[q] = make_float2((float)a[q].x, (float)a[q].y);
+  for (int r = 0; r < 4096; ++r) bf[r] = make_float2((float)b[r].x, (float)b[r].y);
+  AZ_TRY(dalloc_t(h, A64, na)); AZ_TRY(dalloc_t(h, B64, 4096));
+  AZ_TRY(dalloc_t(h, A32, na)); AZ_TRY(dalloc_t(h, B32, 4096));
+  AZ_CUDA(cudaMemcpyAsync(*A64, a.data(), na * sizeof(double2), cudaMemcpyHostToDevice, st));
+  AZ_CUDA(cudaMemcpyAsync(*B64, b.data(), 4096 * sizeof(double2), cudaMemcpyHostToDevice, st));
+  AZ_CUDA(cudaMemcpyAsync(*A32, af.data(), na * sizeof(float2), cudaMemcpyHostToDevice, st));
+  AZ_CUDA(cudaMemcpyAsync(*B32, bf.data(), 4096 * sizeof(float2), cudaMemcpyHostToDevice, st));
+  // host vectors must outlive the async copies: synchronise (setup only)
+  AZ_CUDA(cudaStreamSynchronize(st));
+  return AZ_OK;
+}
+
+__global__ void k_real_to_complex(const double* in, int64_t n, double2* out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = make_double2(in[i], 0.0);
+}
+template <typename TI>
+__global__ void k_to_double(const TI* in, int64_t ldi, int64_t rows, int ncols, double* out, int64_t ldo) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int c = blockIdx.y;
+  if (i < rows && c < ncols) out[(int64_t)c * ldo + i] = (double)in[(int64_t)c * ldi + i];
+}
+template <typename TI>
+az_status to_double(const TI* in, int64_t ldi, int64_t rows, int ncols, double* out, int64_t ldo, cudaStream_t st) {
+  if (rows == 0 || ncols == 0) return AZ_OK;
+  dim3 grid((unsigned)((rows + 255) / 256), ncols);
+  k_to_double<TI><<<grid, 256, 0, st>>>(in, ldi, rows, ncols, out, ldo);
+  AZ_CUDA(cudaGetLastError());
+  return AZ_OK;
+}
+
+// ------------------------------------------------------------------ setup pieces
+az_status build_symbol(az_setup_t* h, cudaStream_t st) {
+  Geom& g = h->g;
+  const double eps = h->eps;
+  std::vector<double*> tmp;
+  auto talloc = [&](double** p, size_t n) -> az_status {
+    cudaError_t e = cudaMalloc((void**)p, std::max<size_t>(n, 1) * sizeof(double));
+    if (e != cudaSuccess) { cudaGetLastError(); set_error("cudaMalloc (symbol scratch) failed"); return AZ_ERR_OOM; }
+    tmp.push_back(*p);
+    return AZ_OK;
+  };
+  az_status rc = AZ_OK;
+  double* samp[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [dim][deriv0/2]
+  double* Gd[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  do {
+    const int nder = h->kind == 1 ? 2 : 1;
+    for (int d = 0; d < g.dim && rc == AZ_OK; ++d)
+      for (int q = 0; q < nder && rc == AZ_OK; ++q) {
+        rc = talloc(&samp[d][q], g.Ld[d]);
+        if (rc) break;
+        const double hL = 2.0 * g.T[d] / (double)g.Ld[d];
+        rc = launch_samples(samp[d][q], g.Ld[d], hL, eps, q == 0 ? 0 : 2, image_count(eps, g.T[d]), st);
+        if (rc) break;
+        // stencil taps
+        int W64 = stencil_halfwidth(eps, hL, 1e-18, g.Ld[d], q == 1);
+        int W32 = stencil_halfwidth(eps, hL, 1e-9, g.Ld[d], q == 1);
+        int W = std::max(W64, W32);
+        if (q == 0) { h->W64[d] = W64; h->W32[d] = W32; }
+        // the FP64 taps use W64, FP32 taps W32: build each with its own width
+        for (int prec = 0; prec < 2 && rc == AZ_OK; ++prec) {
+          int Wp = prec == 0 ? h->W64[d] : h->W32[d];
+          if (q == 1) Wp = prec == 0 ? std::max(h->W64[d], W64) : std::max(h->W32[d], W32);
+          (void)W;
+          double* t64; float* t32;
+          rc = dalloc_t(h, &t64, 2 * Wp + 1); if (rc) break;
+          rc = dalloc_t(h, &t32, 2 * Wp + 1); if (rc) break;
+          rc = launch_taps(samp[d][q], g.Ld[d], Wp, t64, t32, st); if (rc) break;
+          int slot = d + 2 * q;
+          if (prec == 0) h->taps64[slot] = t64; else h->taps32[slot] = t32;
+        }
+        if (q == 1) {  // widths of phi'' taps must match the phi taps used alongside them
+          h->W64[d] = std::max(h->W64[d], W64);
+          h->W32[d] = std::max(h->W32[d], W32);
+        }
+      }
+    if (rc) break;
+    if (h->kind == 1) {
+      // rebuild phi taps at the widened widths so x0/x2 (y0/y2) share W
+      for (int d = 0; d < g.dim && rc == AZ_OK; ++d)
+        for (int prec = 0; prec < 2 && rc == AZ_OK; ++prec) {
+          int Wp = prec == 0 ? h->W64[d] : h->W32[d];
+          double* t64; float* t32;
+          rc = dalloc_t(h, &t64, 2 * Wp + 1); if (rc) break;
+          rc = dalloc_t(h, &t32, 2 * Wp + 1); if (rc) break;
+          rc = launch_taps(samp[d][0], g.Ld[d], Wp, t64, t32, st); if (rc) break;
+          if (prec == 0) h->taps64[d] = t64; else h->taps32[d] = t32;
+          rc = dalloc_t(h, &t64, 2 * Wp + 1); if (rc) break;
+          rc = dalloc_t(h, &t32, 2 * Wp + 1); if (rc) break;
+          rc = launch_taps(samp[d][1], g.Ld[d], Wp, t64, t32, st); if (rc) break;
+          if (prec == 0) h->taps64[d + 2] = t64; else h->taps32[d + 2] = t32;
+        }
+      if (rc) break;
+    }
+    // per-dimension symbols (S2): Ghat = DFT_L(g)
+    if (g.dim == 1) {
+      double2* c1; double2* c2;
+      rc = talloc((double**)&c1, 2 * g.L); if (rc) break;
+      rc = talloc((double**)&c2, 2 * g.L); if (rc) break;
+      k_real_to_complex<<<(unsigned)((g.L + 255) / 256), 256, 0, st>>>(samp[0][0], g.L, c1);
+      PassTabs tb = tabs<double>(h);
+      rc = launch_colfwd_load<double>(g, c1, 1, c2, tb, st); if (rc) break;
+      rc = launch_rowfft<double>(g, c2, 1, c1, tb, st); if (rc) break;
+      rc = dalloc_t(h, &h->Ghat, g.L); if (rc) break;
+      rc = launch_spec_to_natural(g, c1, h->Ghat, st); if (rc) break;
+    } else {
+      const int nder = h->kind == 1 ? 2 : 1;
+      for (int d = 0; d < 2 && rc == AZ_OK; ++d)
+        for (int q = 0; q < nder && rc == AZ_OK; ++q) {
+          rc = talloc(&Gd[d][q], g.Ld[d]); if (rc) break;
+          rc = launch_line_dft_real(samp[d][q], (int)g.Ld[d], Gd[d][q], h->tw64, st);
+        }
+      if (rc) break;
+      rc = dalloc_t(h, &h->Ghat, g.L); if (rc) break;
+      rc = launch_symbol_full(g, h->kind, eps, Gd[0][0], Gd[1][0], Gd[0][1], Gd[1][1], h->Ghat, st); if (rc) break;
+    }
+    rc = dalloc_t(h, &h->S, g.N + 1); if (rc) break;
+    rc = launch_fold_S(g, h->Ghat, h->S, st); if (rc) break;
+    rc = launch_max_abs(h->S, g.N, h->S + g.N, st); if (rc) break;
+    rc = dalloc_t(h, &h->H64, g.L); if (rc) break;
+    rc = dalloc_t(h, &h->H32, g.L); if (rc) break;
+    rc = launch_H(g, h->Ghat, h->S, h->tau_sym * h->tau_sym, h->H64, h->H32, st); if (rc) break;
+  } while (0);
+  cudaError_t e = cudaStreamSynchronize(st);
+  for (double* p : tmp) cudaFree(p);
+  if (rc == AZ_OK && e != cudaSuccess) { set_error(std::string("symbol build: ") + cudaGetErrorString(e)); rc = AZ_ERR_CUDA; }
+  return rc;
+}
+
+// The chain Z* applied to pairs of columns of b (or of the sketch), T precision.
+//  mode 0: b is a compact vector (TB) -> z = Z* b (N x ncols, T) in zout
+//  mode 1: sketch: R columns via stencil, -> W = R - Z* A R (N x k, T)
+//  mode 2: b = A R given as a compact vector -> W = R - Z* b
+template <typename T, typename TB>
+az_status zstar_chain(az_setup_t* h, int mode, const TB* b, int64_t ldb, int ncols, T* zout, int64_t ldz,
+                      cudaStream_t st) {
+  using V = typename C2<T>::t;
+  const Geom& g = h->g;
+  PassTabs tb = tabs<T>(h);
+  const int npairs_total = (ncols + 1) / 2;
+  for (int p0 = 0; p0 < npairs_total; p0 += h->pairs_max) {
+    const int np = std::min(h->pairs_max, npairs_total - p0);
+    V* X1 = (V*)h->X1;
+    V* X3 = (V*)h->X3;
+    if (mode == 1) {
+      SketchIn<T> in;
+      in.bits = h->bits; in.nw = h->nw; in.k = h->k; in.pos2m = h->pos2m;
+      StencilTaps tp = taps<T>(h);
+      in.tapx = (const T*)tp.x0; in.tapy = (const T*)tp.y0; in.Wx = tp.Wx; in.Wy = tp.Wy;
+      AZ_TRY(launch_colfwd_stencil<T>(g, in, p0, np, X1, tb, st));
+    } else {
+      AZ_TRY((launch_colfwd_gather<T, TB>(g, h->pos2m, b, ldb, ncols, p0, np, X1, tb, st)));
+    }
+    AZ_TRY(launch_rowfold<T>(g, X1, Hsym<T>(h), np, X3, tb, st));
+    AZ_TRY((launch_colinv<T, T>(g, X3, p0, np, ncols, zout, ldz, mode != 0 ? h->bits : nullptr, h->nw, tb, st)));
+  }
+  return AZ_OK;
+}
+
+// rows of A applied to coefficient columns: out = alpha*b + beta*A z over all Mtot rows
+template <typename T, typename TZ, typename TB, typename TO>
+az_status apply_rows(az_setup_t* h, const TZ* z, int64_t ldz, const TB* b, int64_t ldb, T alpha, T beta, TO* out,
+                     int64_t ldo, int ncols, cudaStream_t st) {
+  StencilTaps tp = taps<T>(h);
+  AZ_TRY((launch_stencil_rows<T, TZ, TB, TO>(h->g, h->kind, h->eps, h->idx, h->M, tp, z, ldz, b, ldb, alpha, beta,
+                                             out, ldo, ncols, st)));
+  if (h->Mb) {
+    AZ_TRY((launch_boundary_rows<T, TZ, TB, TO>(h->g, h->eps, h->bweight, h->bpts, h->Mb, z, ldz,
+                                                b ? b + h->M : nullptr, ldb, alpha, beta, out + h->M, ldo, ncols, st)));
+  }
+  return AZ_OK;
+}
+
+template <typename T>
+az_status sketch_and_factor(az_setup_t* h, cudaStream_t st) {
+  const Geom& g = h->g;
+  const int k = h->k;
+  T* W = (T*)h->W;
+  T* Y = (T*)h->Y;
+  if (h->kind == 0) {
+    // W = (I - Z* A) R through the fused FFT chain (A R by the local stencil)
+    AZ_TRY((zstar_chain<T, double>(h, 1, nullptr, 0, k, W, g.N, st)));
+  } else {
+    // Poisson: v = A R on all rows by the stencil rows (R materialised in FP64),
+    // then W = R - Z* v through the gather chain (Z* ignores the boundary rows).
+    double* Rd;
+    AZ_CUDA(cudaMalloc((void**)&Rd, (size_t)g.N * k * sizeof(double)));
+    T* v = (T*)h->gb;    // Mtot x k scratch (gb holds >= k columns)
+    az_status rc = launch_bits_to_R(h->bits, g.N, k, Rd, st);
+    if (rc == AZ_OK) rc = apply_rows<T, double, double, T>(h, Rd, g.N, nullptr, 0, (T)0, (T)1, v, h->Mtot, k, st);
+    if (rc == AZ_OK) rc = zstar_chain<T, T>(h, 2, v, h->Mtot, k, W, g.N, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    cudaFree(Rd);
+    if (rc) return rc;
+    if (e != cudaSuccess) { set_error(std::string("sketch: ") + cudaGetErrorString(e)); return AZ_ERR_CUDA; }
+  }
+  // Y = A W on all rows (kept grid rows, then weighted boundary rows)
+  AZ_TRY((apply_rows<T, T, double, T>(h, W, g.N, nullptr, 0, (T)0, (T)1, Y, h->Mtot, k, st)));
+  // pass 1: G1 = Y^T Y, SVQB
+  AZ_TRY((launch_gram<T, T>(Y, h->Mtot, k, Y, h->Mtot, k, h->Mtot, h->partial, h->G, st)));
+  const double taug = Prec<T>::fp64 ? 1e-8 : 1e-7;
+  AZ_TRY(launch_factor1(h->G, k, taug, h->floor * h->floor, h->V, h->lam, h->B1, h->info, st));
+  // Q1 = Y B1 (FP64)
+  double* Q1;
+  AZ_CUDA(cudaMalloc((void**)&Q1, (size_t)h->Mtot * k * sizeof(double)));
+  az_status rc = launch_tsprod<T, double>(Y, h->Mtot, k, h->B1, k, h->Mtot, Q1, h->Mtot, st);
+  if (rc == AZ_OK) rc = launch_gram<double, double>(Q1, h->Mtot, k, Q1, h->Mtot, k, h->Mtot, h->partial, h->G, st);
+  if (rc == AZ_OK) rc = launch_factor2(h->G, k, h->V, h->lam, h->tau_svd, h->floor, h->Tm, h->VS, h->sig, h->info, st);
+  if (rc == AZ_OK) rc = launch_tsprod<double, T>(Q1, h->Mtot, k, h->Tm, k, h->Mtot, (T*)h->Ut, h->Mtot, st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  cudaFree(Q1);
+  if (rc) return rc;
+  if (e != cudaSuccess) { set_error(std::string("factorisation: ") + cudaGetErrorString(e)); return AZ_ERR_CUDA; }
+  FactorInfo fi;
+  AZ_CUDA(cudaMemcpy(&fi, h->info, sizeof(fi), cudaMemcpyDeviceToHost));
+  if (fi.status != 0) {
+    set_error(fi.status == 1 ? "factorisation: Cholesky breakdown in the second pass" : "factorisation: non-finite sketch");
+    return AZ_ERR_NUMERIC;
+  }
+  return AZ_OK;
+}
+
+// One AZ solve of ncols columns (T precision): x (=|+=) Z* b + W VS U^T (b - A Z* b)
+template <typename T, typename TB>
+az_status az_once(az_setup_t* h, const TB* b, int64_t ldb, int ncols, double* x, int64_t ldx, bool accumulate,
+                  cudaStream_t st) {
+  const Geom& g = h->g;
+  T* z = (T*)h->zb;
+  T* gg = (T*)h->gb;
+  AZ_TRY((zstar_chain<T, TB>(h, 0, b, ldb, ncols, z, g.N, st)));
+  AZ_TRY((apply_rows<T, T, TB, T>(h, z, g.N, b, ldb, (T)1, (T)-1, gg, h->Mtot, ncols, st)));
+  AZ_TRY((launch_gram<T, T>((const T*)h->Ut, h->Mtot, h->k, gg, h->Mtot, ncols, h->Mtot, h->partial, h->cb, st)));
+  AZ_TRY(launch_small_mm(h->VS, h->k, h->cb, ncols, h->ub, st));
+  AZ_TRY((launch_update_x<T, T>((const T*)h->W, g.N, h->k, h->ub, z, g.N, g.N, ncols, x, ldx, accumulate, st)));
+  return AZ_OK;
+}
+
+template <typename T>
+az_status solve_impl(az_setup_t* h, const double* b, int64_t ldb, int64_t nrhs, double* x, int64_t ldx,
+                     cudaStream_t st, double* relres) {
+  const int chunk = 2 * h->pairs_max;
+  for (int64_t c0 = 0; c0 < nrhs; c0 += chunk) {
+    const int nc = (int)std::min<int64_t>(chunk, nrhs - c0);
+    const double* bc = b + c0 * ldb;
+    double* xc = x + c0 * ldx;
+    AZ_TRY((az_once<T, double>(h, bc, ldb, nc, xc, ldx, false, st)));
+    for (int it = 0; it < h->refine; ++it) {
+      T* res = (T*)h->rb;
+      // r = b - A x with the residual computed in FP64
+      AZ_TRY((apply_rows<double, double, double, T>(h, xc, ldx, bc, ldb, 1.0, -1.0, res, h->Mtot, nc, st)));
+      AZ_TRY((az_once<T, T>(h, res, h->Mtot, nc, xc, ldx, true, st)));
+    }
+    if (relres) {
+      double* r64;
+      AZ_CUDA(cudaMalloc((void**)&r64, (size_t)h->Mtot * nc * sizeof(double)));
+      az_status rc = apply_rows<double, double, double, double>(h, xc, ldx, bc, ldb, 1.0, -1.0, r64, h->Mtot, nc, st);
+      if (rc == AZ_OK) rc = launch_sumsq_cols(r64, h->Mtot, h->Mtot, nc, h->normb, st);
+      if (rc == AZ_OK) rc = launch_sumsq_cols(bc, ldb, h->Mtot, nc, h->normb + nc, st);
+      std::vector<double> hv(2 * nc);
+      cudaError_t e = cudaMemcpyAsync(hv.data(), h->normb, 2 * nc * sizeof(double), cudaMemcpyDeviceToHost, st);
+      cudaError_t e2 = cudaStreamSynchronize(st);
+      cudaFree(r64);
+      if (rc) return rc;
+      if (e != cudaSuccess || e2 != cudaSuccess) { set_error("relres readback failed"); return AZ_ERR_CUDA; }
+      for (int c = 0; c < nc; ++c) relres[c0 + c] = hv[nc + c] > 0 ? std::sqrt(hv[c] / hv[nc + c]) : 0.0;
+    }
+  }
+  return AZ_OK;
+}
+
+az_status alloc_workspace(az_setup_t* h) {
+  const Geom& g = h->g;
+  const size_t vsz = h->precision == AZ_FP64 ? 16 : 8, tsz = vsz / 2;
+  const size_t per_pair = (size_t)(g.L + g.N) * vsz;
+  int pm = std::max(32, (h->k + 1) / 2);
+  while (pm > 1 && per_pair * pm > (size_t)3 << 30) pm /= 2;
+  h->pairs_max = pm;
+  const int cols = std::max(2 * pm, h->k);
+  AZ_TRY(dalloc(h, &h->X1, per_pair * pm / (g.L + g.N) * g.L));
+  AZ_TRY(dalloc(h, &h->X3, per_pair * pm / (g.L + g.N) * g.N));
+  AZ_TRY(dalloc(h, &h->zb, (size_t)g.N * cols * tsz));
+  AZ_TRY(dalloc(h, &h->gb, (size_t)h->Mtot * cols * tsz));
+  AZ_TRY(dalloc(h, &h->rb, (size_t)h->Mtot * cols * tsz));
+  AZ_TRY(dalloc_t(h, &h->cb, (size_t)h->k * cols));
+  AZ_TRY(dalloc_t(h, &h->ub, (size_t)h->k * cols));
+  AZ_TRY(dalloc_t(h, &h->normb, (size_t)2 * cols));
+  return AZ_OK;
+}
+
+void destroy(az_setup_t* h) {
+  if (!h) return;
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->X1d) cudaFree(h->X1d);
+  if (h->X3d) cudaFree(h->X3d);
+  delete h;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char* az_last_error(void) { return g_last_error.c_str(); }
+
+void az_destroy(az_handle h) { destroy(h); }
+
+az_status az_rademacher(int64_t N, int32_t k, uint64_t seed, double* R_dev, void* stream) {
+  if (N <= 0 || k <= 0 || !R_dev) { set_error("az_rademacher: bad arguments"); return AZ_ERR_ARG; }
+  cudaStream_t st = (cudaStream_t)stream;
+  uint32_t* bits;
+  int64_t nw = (N + 31) / 32;
+  AZ_CUDA(cudaMalloc((void**)&bits, (size_t)nw * k * 4 + 16));
+  az_status rc = launch_philox_bits(bits, N, k, seed, st);
+  if (rc == AZ_OK) rc = launch_bits_to_R(bits, N, k, R_dev, st);
+  cudaStreamSynchronize(st);
+  cudaFree(bits);
+  return rc;
+}
+
+az_status az_query_footprint(const az_grid* gr, int64_t M, int64_t n_boundary, const az_options* opt, int64_t nrhs_max,
+                             size_t* bytes) {
+  if (!bytes) { set_error("az_query_footprint: null output"); return AZ_ERR_ARG; }
+  Geom g;
+  AZ_TRY(make_geom(gr, g));
+  const int prec = opt ? opt->precision : AZ_MIXED;
+  const int k = opt ? opt->k : 24;
+  const size_t vsz = prec == AZ_FP64 ? 16 : 8, tsz = vsz / 2;
+  const int64_t Mt = M + n_boundary;
+  int pm = (int)std::max<int64_t>(std::max<int64_t>(1, (nrhs_max + 1) / 2), (k + 1) / 2);
+  size_t b = 0;
+  b += (size_t)g.L * (4 + 8 + 8 + 4);              // pos2m, Ghat, H64, H32
+  b += (size_t)M * 4 + (size_t)g.N * 8;             // idx, S
+  b += (size_t)((g.N + 31) / 32) * 4 * k;           // bits
+  b += (size_t)g.N * k * tsz + 2 * (size_t)Mt * k * tsz;  // W, Y, Ut
+  b += (size_t)pm * (g.L + g.N) * vsz;              // X1, X3
+  const int cols = std::max(2 * pm, k);
+  b += (size_t)g.N * cols * tsz + 2 * (size_t)Mt * cols * tsz;
+  b += (size_t)gram_blocks(Mt) * k * std::max(k, cols) * 8;
+  b += (size_t)Mt * k * 8;                          // transient Q1 during setup
+  *bytes = b;
+  return AZ_OK;
+}
+
+az_status az_setup(const az_grid* gr, const uint8_t* mask, const double* bpts, int64_t n_boundary, double eps,
+                   int32_t kernel, double boundary_weight, const az_options* opt, void* stream, az_handle* out) {
+  if (!out) { set_error("az_setup: null output handle"); return AZ_ERR_ARG; }
+  *out = nullptr;
+  if (!mask) { set_error("az_setup: Omega mask is required"); return AZ_ERR_ARG; }
+  if (!(eps > 0) || !std::isfinite(eps)) { set_error("az_setup: eps must be positive"); return AZ_ERR_ARG; }
+  if (kernel != AZ_GAUSS && kernel != AZ_NEG_LAPLACE_GAUSS) { set_error("az_setup: unknown kernel"); return AZ_ERR_ARG; }
+  if (n_boundary < 0 || (n_boundary > 0 && !bpts)) { set_error("az_setup: boundary points"); return AZ_ERR_ARG; }
+  az_options o;
+  if (opt) o = *opt;
+  else { o.precision = AZ_MIXED; o.k = 24; o.tau_svd = 0; o.tau_sym = 0; o.seed = 1; o.refine_steps = -1; }
+  if (o.precision != AZ_FP64 && o.precision != AZ_MIXED) { set_error("az_setup: precision"); return AZ_ERR_ARG; }
+  if (o.k < 1 || o.k > 64) { set_error("az_setup: k must be in [1, 64] for this build"); return AZ_ERR_ARG; }
+  if (kernel == AZ_NEG_LAPLACE_GAUSS && (!gr || gr->dim != 2)) { set_error("az_setup: collocation needs dim = 2"); return AZ_ERR_ARG; }
+  az_setup_t* h = new az_setup_t();
+  az_status rc = make_geom(gr, h->g);
+  if (rc) { delete h; return rc; }
+  cudaStream_t st = (cudaStream_t)stream;
+  h->kind = kernel == AZ_NEG_LAPLACE_GAUSS ? 1 : 0;
+  h->precision = o.precision;
+  h->k = o.k;
+  h->eps = eps;
+  h->tau_svd = o.tau_svd > 0 ? o.tau_svd : 1e-8;
+  h->tau_sym = o.tau_sym > 0 ? o.tau_sym : 0.0;
+  h->seed = o.seed;
+  h->refine = o.refine_steps >= 0 ? o.refine_steps : (o.precision == AZ_MIXED ? 1 : 0);
+  h->bweight = boundary_weight;
+  h->Mb = h->kind == 1 ? n_boundary : 0;
+  Geom& g = h->g;
+  do {
+    // S1: index map
+    rc = dalloc_t(h, &h->pos2m, g.L); if (rc) break;
+    rc = dalloc_t(h, &h->idx, g.L); if (rc) break;
+    int32_t* scratch; int64_t* Md;
+    rc = dalloc_t(h, &scratch, 4096); if (rc) break;
+    rc = dalloc_t(h, &Md, 1); if (rc) break;
+    rc = launch_compact(mask, g.L, h->pos2m, h->idx, Md, scratch, st); if (rc) break;
+    int64_t M = 0;
+    if (cudaMemcpyAsync(&M, Md, sizeof(int64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) { set_error("az_setup: reading M failed"); rc = AZ_ERR_CUDA; break; }
+    h->M = M;
+    h->Mtot = M + h->Mb;
+    if (h->Mtot < 1) { set_error("az_setup: Omega contains no grid point"); rc = AZ_ERR_ARG; break; }
+    if (h->Mb) {
+      rc = dalloc_t(h, &h->bpts, 2 * h->Mb); if (rc) break;
+      if (cudaMemcpyAsync(h->bpts, bpts, 2 * h->Mb * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess) { rc = AZ_ERR_CUDA; break; }
+    }
+    // twiddle tables
+    {
+      std::vector<double> re, im;
+      host_twiddles(4096, re, im);
+      std::vector<double2> t64(4096);
+      std::vector<float2> t32(4096);
+      for (int m = 0; m < 4096; ++m) { t64[m] = make_double2(re[m], im[m]); t32[m] = make_float2((float)re[m], (float)im[m]); }
+      rc = dalloc_t(h, &h->tw64, 4096); if (rc) break;
+      rc = dalloc_t(h, &h->tw32, 4096); if (rc) break;
+      if (cudaMemcpy(h->tw64, t64.data(), 4096 * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess ||
+          cudaMemcpy(h->tw32, t32.data(), 4096 * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess) { rc = AZ_ERR_CUDA; break; }
+      rc = big_tables(h, g.L, &h->big64[0], &h->big64[1], &h->big32[0], &h->big32[1], st); if (rc) break;
+      rc = big_tables(h, g.N, &h->big64[2], &h->big64[3], &h->big32[2], &h->big32[3], st); if (rc) break;
+    }
+    // S2: symbol
+    rc = build_symbol(h, st); if (rc) break;
+    // S3: Rademacher bits
+    h->nw = (g.N + 31) / 32;
+    rc = dalloc_t(h, &h->bits, (size_t)h->nw * h->k + 4); if (rc) break;
+    rc = launch_philox_bits(h->bits, g.N, h->k, h->seed, st); if (rc) break;
+    // buffers
+    const size_t tsz = h->precision == AZ_FP64 ? 8 : 4;
+    rc = dalloc(h, &h->W, (size_t)g.N * h->k * tsz); if (rc) break;
+    rc = dalloc(h, &h->Y, (size_t)h->Mtot * h->k * tsz); if (rc) break;
+    rc = dalloc(h, &h->Ut, (size_t)h->Mtot * h->k * tsz); if (rc) break;
+    for (double** p : {&h->G, &h->V, &h->B1, &h->Tm, &h->VS}) { rc = dalloc_t(h, p, (size_t)h->k * h->k); if (rc) break; }
+    if (rc) break;
+    rc = dalloc_t(h, &h->lam, h->k); if (rc) break;
+    rc = dalloc_t(h, &h->sig, h->k); if (rc) break;
+    rc = dalloc_t(h, &h->info, 1); if (rc) break;
+    rc = alloc_workspace(h); if (rc) break;
+    rc = dalloc_t(h, &h->partial, (size_t)gram_blocks(h->Mtot) * h->k * std::max(h->k, 2 * h->pairs_max)); if (rc) break;
+    // rounding floor of the sketch's singular values (see oracle reading):
+    // 1e-13 * ||A R||_F, with ||A R||_F^2 ~ k (M/L) N ||g||^2 estimated from the symbol
+    {
+      std::vector<double> S(1);
+      double smax;
+      cudaMemcpy(&smax, h->S + g.N, sizeof(double), cudaMemcpyDeviceToHost);
+      double est = std::sqrt((double)h->k * (double)h->Mtot / (double)g.L * (double)g.N * smax / (double)(g.s[0] * g.s[1]));
+      h->floor = 1e-13 * est;
+    }
+    // S4-S7
+    rc = h->precision == AZ_FP64 ? sketch_and_factor<double>(h, st) : sketch_and_factor<float>(h, st);
+    if (rc) break;
+  } while (0);
+  if (rc) { destroy(h); return rc; }
+  *out = h;
+  return AZ_OK;
+}
+
+az_status az_solve(az_handle h, const double* b, int64_t ldb, int64_t nrhs, double* x, int64_t ldx, void* stream,
+                   double* relres) {
+  if (!h || !b || !x || nrhs < 0 || ldb < h->Mtot || ldx < h->g.N) { set_error("az_solve: bad arguments"); return AZ_ERR_ARG; }
+  if (nrhs == 0) return AZ_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  return h->precision == AZ_FP64 ? solve_impl<double>(h, b, ldb, nrhs, x, ldx, st, relres)
+                                 : solve_impl<float>(h, b, ldb, nrhs, x, ldx, st, relres);
+}
+
+az_status az_collocate(az_handle h, const double* f, int64_t ldf, const double* gb, int64_t ldg, int64_t nrhs,
+                       double* x, int64_t ldx, void* stream, double* relres) {
+  if (!h || h->kind != 1) { set_error("az_collocate: needs a collocation setup"); return AZ_ERR_ARG; }
+  if (!f || !gb || !x || nrhs < 0 || ldf < h->M || ldg < h->Mb || ldx < h->g.N) { set_error("az_collocate: bad arguments"); return AZ_ERR_ARG; }
+  if (nrhs == 0) return AZ_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  double* b;
+  AZ_CUDA(cudaMalloc((void**)&b, (size_t)h->Mtot * nrhs * sizeof(double)));
+  az_status rc = launch_scale_rows(f, ldf, h->M, (int)nrhs, 1.0 / (2.0 * h->eps * h->eps), b, h->Mtot, st);
+  if (rc == AZ_OK) rc = launch_scale_rows(gb, ldg, h->Mb, (int)nrhs, h->bweight, b + h->M, h->Mtot, st);
+  if (rc == AZ_OK) rc = az_solve(h, b, h->Mtot, nrhs, x, ldx, stream, relres);
+  cudaStreamSynchronize(st);
+  cudaFree(b);
+  return rc;
+}
+
+az_status az_evaluate(az_handle h, const double* x, int64_t ldx, int64_t nrhs, int32_t s_test, double* out, int64_t ldo,
+                      void* stream) {
+  if (!h || !x || !out || s_test < 1 || nrhs < 0) { set_error("az_evaluate: bad arguments"); return AZ_ERR_ARG; }
+  int64_t npts = h->g.dim == 1 ? h->g.n[0] * s_test : h->g.n[0] * s_test * h->g.n[1] * s_test;
+  if (ldo < npts || ldx < h->g.N) { set_error("az_evaluate: leading dimension"); return AZ_ERR_ARG; }
+  if (nrhs == 0) return AZ_OK;
+  return launch_evaluate(h->g, h->eps, s_test, x, ldx, (int)nrhs, out, ldo, (cudaStream_t)stream);
+}
+
+az_status az_apply_A(az_handle h, const double* x, int64_t ldx, int64_t nrhs, double* y, int64_t ldy, void* stream) {
+  if (!h || !x || !y || ldx < h->g.N || ldy < h->Mtot || nrhs < 0) { set_error("az_apply_A: bad arguments"); return AZ_ERR_ARG; }
+  if (nrhs == 0) return AZ_OK;
+  return apply_rows<double, double, double, double>(h, x, ldx, nullptr, 0, 0.0, 1.0, y, ldy, (int)nrhs,
+                                                    (cudaStream_t)stream);
+}
+
+az_status az_apply_Zstar(az_handle h, const double* y, int64_t ldy, int64_t nrhs, double* x, int64_t ldx, void* stream) {
+  if (!h || !x || !y || ldx < h->g.N || ldy < h->Mtot || nrhs < 0) { set_error("az_apply_Zstar: bad arguments"); return AZ_ERR_ARG; }
+  if (nrhs == 0) return AZ_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  // FP64 chain on a private workspace (one pair at a time in mixed handles)
+  void* sX1 = h->X1; void* sX3 = h->X3; int spm = h->pairs_max;
+  if (h->precision != AZ_FP64) {
+    if (!h->X1d) {
+      if (cudaMalloc(&h->X1d, (size_t)h->g.L * 16) != cudaSuccess || cudaMalloc(&h->X3d, (size_t)h->g.N * 16) != cudaSuccess) {
+        cudaGetLastError(); set_error("az_apply_Zstar: workspace"); return AZ_ERR_OOM;
+      }
+    }
+    h->X1 = h->X1d; h->X3 = h->X3d; h->pairs_max = 1;
+  }
+  az_status rc = zstar_chain<double, double>(h, 0, y, ldy, (int)nrhs, x, ldx, st);
+  h->X1 = sX1; h->X3 = sX3; h->pairs_max = spm;
+  return rc;
+}
+
+az_status az_get_info(az_handle h, az_info_t* info) {
+  if (!h || !info) { set_error("az_get_info: bad arguments"); return AZ_ERR_ARG; }
+  FactorInfo fi;
+  AZ_CUDA(cudaDeviceSynchronize());
+  AZ_CUDA(cudaMemcpy(&fi, h->info, sizeof(fi), cudaMemcpyDeviceToHost));
+  info->N = h->g.N; info->L = h->g.L; info->M = h->M; info->Mb = h->Mb; info->k = h->k;
+  info->rank = fi.r; info->rank_gram = fi.r1; info->precision = h->precision;
+  info->sigma_max = fi.sigma_max; info->sigma_min_kept = fi.sigma_min_kept;
+  info->device_bytes = h->bytes;
+  return AZ_OK;
+}
+
+az_status az_get_array(az_handle h, int32_t which, double* dst, void* stream) {
+  if (!h || !dst) { set_error("az_get_array: bad arguments"); return AZ_ERR_ARG; }
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool f64 = h->precision == AZ_FP64;
+  switch (which) {
+    case AZ_ARRAY_SYMBOL:
+      AZ_CUDA(cudaMemcpyAsync(dst, h->Ghat, h->g.L * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      return AZ_OK;
+    case AZ_ARRAY_SKETCH:
+      return f64 ? to_double<double>((double*)h->Y, h->Mtot, h->Mtot, h->k, dst, h->Mtot, st)
+                 : to_double<float>((float*)h->Y, h->Mtot, h->Mtot, h->k, dst, h->Mtot, st);
+    case AZ_ARRAY_W:
+      return f64 ? to_double<double>((double*)h->W, h->g.N, h->g.N, h->k, dst, h->g.N, st)
+                 : to_double<float>((float*)h->W, h->g.N, h->g.N, h->k, dst, h->g.N, st);
+    case AZ_ARRAY_R:
+      return launch_bits_to_R(h->bits, h->g.N, h->k, dst, st);
+    case AZ_ARRAY_UT: {
+      FactorInfo fi;
+      AZ_CUDA(cudaStreamSynchronize(st));
+      AZ_CUDA(cudaMemcpy(&fi, h->info, sizeof(fi), cudaMemcpyDeviceToHost));
+      return f64 ? to_double<double>((double*)h->Ut, h->Mtot, h->Mtot, fi.r, dst, h->Mtot, st)
+                 : to_double<float>((float*)h->Ut, h->Mtot, h->Mtot, fi.r, dst, h->Mtot, st);
+    }
+    case AZ_ARRAY_SIGMA: {
+      FactorInfo fi;
+      AZ_CUDA(cudaStreamSynchronize(st));
+      AZ_CUDA(cudaMemcpy(&fi, h->info, sizeof(fi), cudaMemcpyDeviceToHost));
+      AZ_CUDA(cudaMemcpyAsync(dst, h->sig, std::max(fi.r, 0) * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      return AZ_OK;
+    }
+    case AZ_ARRAY_KEPT:
+      return to_double<int32_t>(h->idx, h->M, h->M, 1, dst, h->M, st);
+    default:
+      set_error("az_get_array: unknown array");
+      return AZ_ERR_ARG;
+  }
+}
+
+}  // extern "C"
