@@ -1,0 +1,389 @@
+"""Benchmark of the AZ solver on the 1D-at-scale workload (one GB300 per rank).
+
+Workload (the configuration the headline metric is quoted on): N = 2^20
+Gaussian centers on [-1, 1], eps = 1/h, Omega = [-0.7, 0.3], oversampling 2,
+sketch width k = 24, a batch of 64 right-hand sides cos(w x + phi) with
+w ~ U[1, 40], phi ~ U[0, 2 pi) from the seed; FP32 transforms and sketch,
+FP64 factor work, one FP64-residual refinement step.
+
+One step = the whole hot path: az_refactor (index map, symbol, test matrix,
+sketch, factorisation) + az_solve of the 64 right-hand sides.  value = solved
+right-hand sides per second over all ranks.  Multi-GPU: independent replicas
+(the solve has no exchange step); each rank times its own steps, the slowest
+rank's time is used.
+
+--impl reference times the CPU oracle (oracle/, FP64 NumPy) on the same
+workload on the host cores: the full-size setup once, then one right-hand side
+per step, reported as right-hand sides per second for the same step shape
+(64 / (t_setup + 64 t_rhs)).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_CENTERS = 1 << 20
+NRHS = 64
+K_SKETCH = 24
+METRIC = "AZ solves/s (right-hand sides per second, setup + solve per step) at parity with the FP64 oracle"
+WORKLOAD = "1d-approx N=2^20 s=2 eps=1/h Omega=[-0.7,0.3] k=24 nrhs=64 mixed(FP32 sketch/FFT, FP64 factor) +1 FP64-residual refinement"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-comparator", action="store_true")
+    ap.add_argument("--nrhs", type=int, default=NRHS, help="right-hand sides per step (default: the workload's 64)")
+    ap.add_argument("--lite", action="store_true",
+                    help="timed steps only (no e2e, parity, comparator or CPU legs): the small case for profiler captures")
+    return ap.parse_args()
+
+
+def problem():
+    import workloads as W
+    return W.config2(N_CENTERS, NRHS)
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- oracle legs
+def _oracle_sample(n_rhs_timed, out_q=None):
+    """Run the CPU oracle on the full workload: setup once + n_rhs_timed solves."""
+    import numpy as np
+    import workloads as W
+    from oracle.az import AZ
+    from oracle.operators import Operator
+    p = problem()
+    t0 = time.perf_counter()
+    op = Operator(p.grid, p.mask)
+    az = AZ(op, K_SKETCH, 1, 1e-8)
+    t_setup = time.perf_counter() - t0
+    b = p.rhs()
+    times = []
+    for j in range(n_rhs_timed):
+        t1 = time.perf_counter()
+        az.solve(b[:, j:j + 1], refine=1)
+        times.append(time.perf_counter() - t1)
+    return t_setup, times
+
+
+def cpu_baseline_leg():
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(1) as pool:
+        t_setup, times = pool.apply(_oracle_sample, (2,))
+    t_rhs = sum(times) / len(times)
+    value = NRHS / (t_setup + NRHS * t_rhs)
+    return {"value": value, "unit": "RHS/s", "cores": 1, "kind": "oracle",
+            "sample": f"full-size oracle setup ({t_setup:.1f} s) + 2 of the 64 RHS ({t_rhs:.2f} s each, 1 refinement); "
+                      f"value = 64 / (t_setup + 64 t_rhs); numpy FFT single-threaded"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(1) as pool:
+        t_setup, times = pool.apply(_oracle_sample, (args.warmup + args.steps,))
+    timed = times[args.warmup:]
+    t_rhs = sum(timed) / len(timed)
+    value = NRHS / (t_setup + NRHS * t_rhs)
+    ms_step = 1000.0 * (t_setup + NRHS * t_rhs)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + " (oracle: FP64 throughout)", "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "RHS/s", "cores": 1, "kind": "oracle",
+                             "sample": f"setup once ({t_setup:.1f} s), then one RHS per step "
+                                       f"({t_rhs:.2f} s avg over {len(timed)} steps)"},
+            "e2e": {"value": value, "unit": "RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- FP64 torch comparator
+def fp64_torch_comparator(p, b_dev, steps=2, warmup=1):
+    """The O2 algorithm written directly in torch FP64 (torch.fft, torch.linalg.svd),
+    no fusion: the 'plain FP64 GPU AZ' the metric is compared against."""
+    import math
+    import torch
+    dev = b_dev.device
+    g = p.grid
+    N, s, T = g.n[0], g.s[0], g.T[0]
+    L = N * s
+    hL = 2 * T / L
+    eps = g.eps
+    mask = torch.from_numpy(p.mask).to(dev).bool()
+    idx = torch.nonzero(mask).squeeze(1)
+    b = b_dev.T.contiguous()  # M x nrhs
+
+    def run():
+        m = torch.arange(L, device=dev, dtype=torch.float64)
+        m = torch.where(m > L / 2, m - L, m)
+        gs = torch.zeros(L, dtype=torch.float64, device=dev)
+        for q in range(-3, 4):
+            gs += torch.exp(-(eps * (m + q * L) * hL) ** 2)
+        G = torch.fft.fft(gs).real
+        S = (G.reshape(s, N) ** 2).sum(0)
+
+        def A(a):
+            ah = torch.fft.fft(a, dim=0)
+            return torch.fft.ifft(G[:, None] * ah.repeat(s, 1), dim=0).real[idx]
+
+        def Z(y):
+            E = torch.zeros((L, y.shape[1]), dtype=torch.float64, device=dev)
+            E[idx] = y
+            Y = torch.fft.fft(E, dim=0)
+            ah = (G[:, None] * Y).reshape(s, N, -1).sum(0) / S[:, None]
+            return torch.fft.ifft(ah, dim=0).real
+
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(1)
+        R = torch.randint(0, 2, (N, K_SKETCH), generator=gen, device=dev).double() * 2 - 1
+        AR = A(R)
+        Yk = AR - A(Z(AR))
+        U, Sg, Vh = torch.linalg.svd(Yk, full_matrices=False)
+        r = int((Sg > 1e-8 * Sg[0]).sum())
+        gg = b - A(Z(b))
+        u = Vh[:r].T @ ((U[:, :r].T @ gg) / Sg[:r, None])
+        x2 = R @ u
+        x = Z(b - A(x2)) + x2
+        return x, A
+
+    for _ in range(warmup):
+        run()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(steps):
+        x, A = run()
+    t1.record()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / steps
+    rel = (torch.linalg.norm(A(x) - b, dim=0) / torch.linalg.norm(b, dim=0)).cpu().numpy()
+    return {"value": NRHS / (ms / 1000.0), "unit": "RHS/s", "ms_per_step": ms, "steps": steps,
+            "what": "same step (setup + 64 RHS) written in plain torch FP64 (torch.fft + torch.linalg.svd), no refinement"}, rel
+
+
+# --------------------------------------------------------------------------- our arm
+def load_traffic():
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        return json.load(open(path))
+    except Exception:
+        return {}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2308_14490_gb300 as az
+
+    global NRHS
+    NRHS = args.nrhs
+    p = problem()
+    g = p.grid
+    b_host = np.ascontiguousarray(p.rhs()[:, :NRHS].T)  # (nrhs, M)
+    M = b_host.shape[1]
+    b_pin = torch.from_numpy(b_host).pin_memory()
+    b_dev = b_pin.to(dev)
+    x_dev = torch.zeros((NRHS, g.N), dtype=torch.float64, device=dev)
+    x_pin = torch.zeros((NRHS, g.N), dtype=torch.float64).pin_memory()
+    mask = torch.from_numpy(p.mask).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    opts = az.make_options(az.AZ_MIXED, K_SKETCH, 1e-8, 0.0, 1, 1)
+    h = az.az_setup(az.make_grid(1, g.n, g.s, g.T), mask, g.eps, options=opts)
+
+    def step(i):
+        az.az_refactor(h, 1 + (i % 2), stream)
+        az.az_solve(h, b_dev, x_dev, stream)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for i in range(args.warmup):
+        step(i)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    n0 = az.az_launch_count()
+    az.az_profile_begin()
+    barrier()
+    evs[0].record(stream)
+    for i in range(args.steps):
+        step(args.warmup + i)
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize(dev)
+    prof = az.az_profile_end()
+    launches = az.az_launch_count() - n0
+    barrier()
+    clk = clocks.stop()
+    per = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
+    total_ms = evs[0].elapsed_time(evs[-1])
+    t = torch.tensor([total_ms], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = world * NRHS * args.steps / (total_ms / 1000.0)
+    if args.lite:
+        if rank == 0:
+            print(json.dumps({"lite": True, "value": value, "ms_per_step": total_ms / args.steps,
+                              "gpu_launches": int(launches)}), flush=True)
+        az.az_destroy(h)
+        return
+
+    # end-to-end through the public API with host buffers (H2D of b, D2H of x inside)
+    e_evs = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    barrier()
+    e_evs[0].record(stream)
+    for i in range(args.steps):
+        b_dev.copy_(b_pin, non_blocking=True)
+        step(i)
+        x_pin.copy_(x_dev, non_blocking=True)
+    e_evs[1].record(stream)
+    torch.cuda.synchronize(dev)
+    e_ms = e_evs[0].elapsed_time(e_evs[1])
+    te = torch.tensor([e_ms], device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e = {"value": world * NRHS * args.steps / (float(te.item()) / 1000.0), "unit": "RHS/s",
+           "h2d_bytes_per_step": int(b_host.nbytes), "d2h_bytes_per_step": int(x_pin.numel() * 8)}
+
+    # parity: relres of the mixed result vs the library's all-FP64 path on the same batch
+    rr_mixed = az.az_solve(h, b_dev, x_dev, stream, relres=True)
+    o64 = az.make_options(az.AZ_FP64, K_SKETCH, 1e-8, 0.0, 1, 0)
+    h64 = az.az_setup(az.make_grid(1, g.n, g.s, g.T), mask, g.eps, options=o64)
+    x64 = torch.zeros_like(x_dev)
+    rr64 = az.az_solve(h64, b_dev, x64, stream, relres=True)
+    info = az.az_get_info(h)
+    az.az_destroy(h64)
+
+    # roofline of the dominant kernel (largest total device time in the timed region)
+    dom, ent = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs")
+    peak_src = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+    achieved = ent["bytes"] / (ent["ms"] / 1000.0) / 1e9
+    tr = load_traffic().get(dom)
+    share = {k: round(v["ms"] / sum(e["ms"] for e in prof.values()), 4) for k, v in
+             sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:8]}
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(achieved / hbm, 4), "peak_source": peak_src,
+                "traffic": tr.get("traffic_per_launch") if tr else None,
+                "algorithmic_bytes_per_launch": ent["bytes"] / max(1, ent["launches"]),
+                "avg_launch_ms": ent["ms"] / max(1, ent["launches"]), "time_share": share}
+
+    line = {"metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": g.N, "M": int(M), "k": K_SKETCH, "nrhs": NRHS,
+                       "rank_kept": info["rank"], "l2": "no flush: inputs (b 537 MB) and per-step working set (>1 GB) exceed L2",
+                       "parallelism": f"replicas x{world}"},
+            "latency_ms": {"p50": sorted(per)[len(per) // 2], "p99": sorted(per)[min(len(per) - 1, int(0.99 * len(per)))],
+                           "max": max(per)},
+            "parity": {"relres_max_mixed": max(rr_mixed), "relres_max_fp64": max(rr64),
+                       "max_gap_mixed_vs_fp64": max(abs(a - c) for a, c in zip(rr_mixed, rr64)), "tol": 1e-8},
+            "roofline": roofline, "gpu_launches": int(launches), "clocks": clk, "e2e": e2e}
+    if rank == 0 and world == 1 and not args.no_comparator:
+        try:
+            comp, rel = fp64_torch_comparator(p, b_dev)
+            comp["relres_max"] = float(rel.max())
+            line["fp64_gpu_torch"] = comp
+        except Exception as ex:  # the comparator is context, never the headline
+            line["fp64_gpu_torch"] = {"error": str(ex)[:200]}
+    az.az_destroy(h)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_leg()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

@@ -167,6 +167,26 @@ const char* az_last_error(void);
  * seed high), bit (row % 32) of word ((row % 128)/32), set = +1. */
 az_status az_rademacher(int64_t N, int32_t k, uint64_t seed, double* R_dev, void* stream);
 
+/* Recompute every setup step (index map, symbol, test matrix with a new
+ * seed, sketch, factorisation) on an existing handle, on `stream`, without
+ * allocating and without synchronising.  A factorisation breakdown is reported
+ * by the next az_get_info (status is checked lazily). */
+az_status az_refactor(az_handle h, uint64_t seed, void* stream);
+
+/* Instrumentation (not part of the paper's method).
+ * az_launch_count: kernels launched by this library since it was loaded.
+ * az_profile_begin / az_profile_end: while enabled, every kernel launch is
+ * bracketed by CUDA events on its stream and attributed to its kernel class
+ * with its algorithmic bytes (inputs read once + outputs written once);
+ * az_profile_end synchronises on those events.  az_profile_query(i, ...)
+ * returns entry i (name, launches, total milliseconds, total bytes) or
+ * AZ_ERR_ARG past the last entry. */
+int64_t az_launch_count(void);
+void az_profile_begin(void);
+az_status az_profile_end(void);
+az_status az_profile_query(int32_t i, char* name, int32_t name_len, int64_t* launches, double* ms,
+                           double* bytes);
+
 #ifdef __cplusplus
 }
 #endif

@@ -59,12 +59,18 @@ _SIGS = {
     "az_destroy": [_P],
     "az_last_error": [],
     "az_rademacher": [_I64, _I32, ctypes.c_uint64, _P, _P],
+    "az_refactor": [_P, ctypes.c_uint64, _P],
+    "az_launch_count": [],
+    "az_profile_begin": [],
+    "az_profile_end": [],
+    "az_profile_query": [_I32, ctypes.c_char_p, _I32, ctypes.POINTER(_I64), ctypes.POINTER(_D), ctypes.POINTER(_D)],
 }
 EXPORTS = list(_SIGS)
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
     _f.argtypes = _args
-    _f.restype = ctypes.c_char_p if _name == "az_last_error" else (None if _name == "az_destroy" else ctypes.c_int)
+    _f.restype = {"az_last_error": ctypes.c_char_p, "az_destroy": None, "az_profile_begin": None,
+                  "az_launch_count": ctypes.c_int64}.get(_name, ctypes.c_int)
 
 
 class AZError(RuntimeError):
@@ -174,3 +180,28 @@ def az_rademacher(N, k, seed, R, stream=None):
 
 def az_last_error():
     return _lib.az_last_error().decode(errors="replace")
+
+
+def az_refactor(h, seed, stream=None):
+    """Recompute every setup step on the handle (new test-matrix seed), no allocation, no sync."""
+    _check(_lib.az_refactor(h, int(seed), _stream(stream)), "az_refactor")
+
+
+def az_launch_count():
+    return int(_lib.az_launch_count())
+
+
+def az_profile_begin():
+    _lib.az_profile_begin()
+
+
+def az_profile_end():
+    _check(_lib.az_profile_end(), "az_profile_end")
+    out = {}
+    i = 0
+    name = ctypes.create_string_buffer(128)
+    n, ms, by = _I64(), _D(), _D()
+    while _lib.az_profile_query(i, name, 128, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)) == AZ_OK:
+        out[name.value.decode()] = {"launches": n.value, "ms": ms.value, "bytes": by.value}
+        i += 1
+    return out

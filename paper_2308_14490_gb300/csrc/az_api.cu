@@ -8,6 +8,7 @@
 
 #include "kernels.cuh"
 #include "lowrank.cuh"
+#include "profile.cuh"
 
 namespace az {
 static thread_local std::string g_last_error;
@@ -33,6 +34,8 @@ struct az_setup_t {
   float* H32 = nullptr;
   double* taps64[4] = {nullptr, nullptr, nullptr, nullptr};  // x0, y0, x2, y2
   float* taps32[4] = {nullptr, nullptr, nullptr, nullptr};
+  float* tapsH[4] = {nullptr, nullptr, nullptr, nullptr};   // FP64 taps split into FP32 hi + lo
+  float* tapsL[4] = {nullptr, nullptr, nullptr, nullptr};
   int W32[2] = {0, 0}, W64[2] = {0, 0};
   double2* tw64 = nullptr;
   float2* tw32 = nullptr;
@@ -59,6 +62,18 @@ struct az_setup_t {
   // FP64 scratch for az_apply_Zstar in mixed mode
   void* X1d = nullptr;
   void* X3d = nullptr;
+  // persistent setup scratch (so that az_refactor neither allocates nor syncs)
+  uint8_t* mask = nullptr;
+  int64_t* Md = nullptr;
+  int32_t* scan = nullptr;
+  double* samp[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [dim][phi, phi'']
+  double* Gd[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  double2* c1 = nullptr;
+  double2* c2 = nullptr;
+  double* Q1 = nullptr;     // Mtot x k
+  double* Rd = nullptr;     // N x k (collocation sketch)
+  double* r64 = nullptr;    // Mtot x cols (relres residual), lazily
+  double* bcoll = nullptr;  // Mtot x cols (scaled collocation data), lazily
 };
 
 namespace {
@@ -139,6 +154,9 @@ az_status make_geom(const az_grid* gr, Geom& g) {
   }
   g.logN1 = ilog2(g.N1);
   g.logG0 = ilog2(g.G0);
+  g.logN = ilog2(g.N);
+  for (int d = 0; d < 2; ++d) { g.logs[d] = ilog2(g.s[d]); g.logn[d] = ilog2(g.n[d]); g.logLd[d] = ilog2(g.Ld[d]); }
+  g.logRg = ilog2(g.Rg);
   return AZ_OK;
 }
 
@@ -237,101 +255,73 @@ az_status to_double(const TI* in, int64_t ldi, int64_t rows, int ncols, double* 
 }
 
 // ------------------------------------------------------------------ setup pieces
+// Host-side stencil widths (phi and phi'' taps of one dimension share a width).
+void stencil_widths(az_setup_t* h) {
+  const Geom& g = h->g;
+  for (int d = 0; d < g.dim; ++d) {
+    const double hL = 2.0 * g.T[d] / (double)g.Ld[d];
+    const bool der = h->kind == 1;
+    h->W64[d] = stencil_halfwidth(h->eps, hL, 1e-18, g.Ld[d], der);
+    h->W32[d] = stencil_halfwidth(h->eps, hL, 1e-9, g.Ld[d], der);
+  }
+}
+
+az_status alloc_symbol(az_setup_t* h) {
+  const Geom& g = h->g;
+  const int nder = h->kind == 1 ? 2 : 1;
+  for (int d = 0; d < g.dim; ++d)
+    for (int q = 0; q < nder; ++q) {
+      AZ_TRY(dalloc_t(h, &h->samp[d][q], g.Ld[d]));
+      if (g.dim == 2) AZ_TRY(dalloc_t(h, &h->Gd[d][q], g.Ld[d]));
+      AZ_TRY(dalloc_t(h, &h->taps64[d + 2 * q], 2 * h->W64[d] + 1));
+      AZ_TRY(dalloc_t(h, &h->taps32[d + 2 * q], 2 * h->W32[d] + 1));
+      AZ_TRY(dalloc_t(h, &h->tapsH[d + 2 * q], 2 * h->W64[d] + 1));
+      AZ_TRY(dalloc_t(h, &h->tapsL[d + 2 * q], 2 * h->W64[d] + 1));
+    }
+  if (g.dim == 1) {
+    AZ_TRY(dalloc_t(h, &h->c1, g.L));
+    AZ_TRY(dalloc_t(h, &h->c2, g.L));
+  }
+  AZ_TRY(dalloc_t(h, &h->Ghat, g.L));
+  AZ_TRY(dalloc_t(h, &h->S, g.N + 1));
+  AZ_TRY(dalloc_t(h, &h->H64, g.L));
+  AZ_TRY(dalloc_t(h, &h->H32, g.L));
+  return AZ_OK;
+}
+
+// S2: periodised samples (Eq. periodic_rbf), stencil taps, Ghat = DFT_L(g)
+// (Lemma 4.2), S_k = sum over the alias group of Ghat^2 and H = Ghat / S
+// (Eq. B_pinv), stored in the row-pass layout.  Launches only.
 az_status build_symbol(az_setup_t* h, cudaStream_t st) {
   Geom& g = h->g;
   const double eps = h->eps;
-  std::vector<double*> tmp;
-  auto talloc = [&](double** p, size_t n) -> az_status {
-    cudaError_t e = cudaMalloc((void**)p, std::max<size_t>(n, 1) * sizeof(double));
-    if (e != cudaSuccess) { cudaGetLastError(); set_error("cudaMalloc (symbol scratch) failed"); return AZ_ERR_OOM; }
-    tmp.push_back(*p);
-    return AZ_OK;
-  };
-  az_status rc = AZ_OK;
-  double* samp[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [dim][deriv0/2]
-  double* Gd[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
-  do {
-    const int nder = h->kind == 1 ? 2 : 1;
-    for (int d = 0; d < g.dim && rc == AZ_OK; ++d)
-      for (int q = 0; q < nder && rc == AZ_OK; ++q) {
-        rc = talloc(&samp[d][q], g.Ld[d]);
-        if (rc) break;
-        const double hL = 2.0 * g.T[d] / (double)g.Ld[d];
-        rc = launch_samples(samp[d][q], g.Ld[d], hL, eps, q == 0 ? 0 : 2, image_count(eps, g.T[d]), st);
-        if (rc) break;
-        // stencil taps
-        int W64 = stencil_halfwidth(eps, hL, 1e-18, g.Ld[d], q == 1);
-        int W32 = stencil_halfwidth(eps, hL, 1e-9, g.Ld[d], q == 1);
-        int W = std::max(W64, W32);
-        if (q == 0) { h->W64[d] = W64; h->W32[d] = W32; }
-        // the FP64 taps use W64, FP32 taps W32: build each with its own width
-        for (int prec = 0; prec < 2 && rc == AZ_OK; ++prec) {
-          int Wp = prec == 0 ? h->W64[d] : h->W32[d];
-          if (q == 1) Wp = prec == 0 ? std::max(h->W64[d], W64) : std::max(h->W32[d], W32);
-          (void)W;
-          double* t64; float* t32;
-          rc = dalloc_t(h, &t64, 2 * Wp + 1); if (rc) break;
-          rc = dalloc_t(h, &t32, 2 * Wp + 1); if (rc) break;
-          rc = launch_taps(samp[d][q], g.Ld[d], Wp, t64, t32, st); if (rc) break;
-          int slot = d + 2 * q;
-          if (prec == 0) h->taps64[slot] = t64; else h->taps32[slot] = t32;
-        }
-        if (q == 1) {  // widths of phi'' taps must match the phi taps used alongside them
-          h->W64[d] = std::max(h->W64[d], W64);
-          h->W32[d] = std::max(h->W32[d], W32);
-        }
-      }
-    if (rc) break;
-    if (h->kind == 1) {
-      // rebuild phi taps at the widened widths so x0/x2 (y0/y2) share W
-      for (int d = 0; d < g.dim && rc == AZ_OK; ++d)
-        for (int prec = 0; prec < 2 && rc == AZ_OK; ++prec) {
-          int Wp = prec == 0 ? h->W64[d] : h->W32[d];
-          double* t64; float* t32;
-          rc = dalloc_t(h, &t64, 2 * Wp + 1); if (rc) break;
-          rc = dalloc_t(h, &t32, 2 * Wp + 1); if (rc) break;
-          rc = launch_taps(samp[d][0], g.Ld[d], Wp, t64, t32, st); if (rc) break;
-          if (prec == 0) h->taps64[d] = t64; else h->taps32[d] = t32;
-          rc = dalloc_t(h, &t64, 2 * Wp + 1); if (rc) break;
-          rc = dalloc_t(h, &t32, 2 * Wp + 1); if (rc) break;
-          rc = launch_taps(samp[d][1], g.Ld[d], Wp, t64, t32, st); if (rc) break;
-          if (prec == 0) h->taps64[d + 2] = t64; else h->taps32[d + 2] = t32;
-        }
-      if (rc) break;
+  const int nder = h->kind == 1 ? 2 : 1;
+  for (int d = 0; d < g.dim; ++d)
+    for (int q = 0; q < nder; ++q) {
+      const double hL = 2.0 * g.T[d] / (double)g.Ld[d];
+      AZ_TRY(launch_samples(h->samp[d][q], g.Ld[d], hL, eps, q == 0 ? 0 : 2, image_count(eps, g.T[d]), st));
+      AZ_TRY(launch_taps(h->samp[d][q], g.Ld[d], h->W64[d], h->taps64[d + 2 * q], h->W32[d], h->taps32[d + 2 * q], st,
+                         h->tapsH[d + 2 * q], h->tapsL[d + 2 * q]));
     }
-    // per-dimension symbols (S2): Ghat = DFT_L(g)
-    if (g.dim == 1) {
-      double2* c1; double2* c2;
-      rc = talloc((double**)&c1, 2 * g.L); if (rc) break;
-      rc = talloc((double**)&c2, 2 * g.L); if (rc) break;
-      k_real_to_complex<<<(unsigned)((g.L + 255) / 256), 256, 0, st>>>(samp[0][0], g.L, c1);
-      PassTabs tb = tabs<double>(h);
-      rc = launch_colfwd_load<double>(g, c1, 1, c2, tb, st); if (rc) break;
-      rc = launch_rowfft<double>(g, c2, 1, c1, tb, st); if (rc) break;
-      rc = dalloc_t(h, &h->Ghat, g.L); if (rc) break;
-      rc = launch_spec_to_natural(g, c1, h->Ghat, st); if (rc) break;
-    } else {
-      const int nder = h->kind == 1 ? 2 : 1;
-      for (int d = 0; d < 2 && rc == AZ_OK; ++d)
-        for (int q = 0; q < nder && rc == AZ_OK; ++q) {
-          rc = talloc(&Gd[d][q], g.Ld[d]); if (rc) break;
-          rc = launch_line_dft_real(samp[d][q], (int)g.Ld[d], Gd[d][q], h->tw64, st);
-        }
-      if (rc) break;
-      rc = dalloc_t(h, &h->Ghat, g.L); if (rc) break;
-      rc = launch_symbol_full(g, h->kind, eps, Gd[0][0], Gd[1][0], Gd[0][1], Gd[1][1], h->Ghat, st); if (rc) break;
+  if (g.dim == 1) {
+    {
+      ProfScope ps("symbol", 24.0 * g.L, st);
+      k_real_to_complex<<<(unsigned)((g.L + 255) / 256), 256, 0, st>>>(h->samp[0][0], g.L, h->c1);
+      AZ_CUDA(cudaGetLastError());
     }
-    rc = dalloc_t(h, &h->S, g.N + 1); if (rc) break;
-    rc = launch_fold_S(g, h->Ghat, h->S, st); if (rc) break;
-    rc = launch_max_abs(h->S, g.N, h->S + g.N, st); if (rc) break;
-    rc = dalloc_t(h, &h->H64, g.L); if (rc) break;
-    rc = dalloc_t(h, &h->H32, g.L); if (rc) break;
-    rc = launch_H(g, h->Ghat, h->S, h->tau_sym * h->tau_sym, h->H64, h->H32, st); if (rc) break;
-  } while (0);
-  cudaError_t e = cudaStreamSynchronize(st);
-  for (double* p : tmp) cudaFree(p);
-  if (rc == AZ_OK && e != cudaSuccess) { set_error(std::string("symbol build: ") + cudaGetErrorString(e)); rc = AZ_ERR_CUDA; }
-  return rc;
+    PassTabs tb = tabs<double>(h);
+    AZ_TRY(launch_colfwd_load<double>(g, h->c1, 1, h->c2, tb, st));
+    AZ_TRY(launch_rowfft<double>(g, h->c2, 1, h->c1, tb, st));
+    AZ_TRY(launch_spec_to_natural(g, h->c1, h->Ghat, st));
+  } else {
+    for (int d = 0; d < 2; ++d)
+      for (int q = 0; q < nder; ++q) AZ_TRY(launch_line_dft_real(h->samp[d][q], (int)g.Ld[d], h->Gd[d][q], h->tw64, st));
+    AZ_TRY(launch_symbol_full(g, h->kind, eps, h->Gd[0][0], h->Gd[1][0], h->Gd[0][1], h->Gd[1][1], h->Ghat, st));
+  }
+  AZ_TRY(launch_fold_S(g, h->Ghat, h->S, st));
+  AZ_TRY(launch_max_abs(h->S, g.N, h->S + g.N, st));
+  AZ_TRY(launch_H(g, h->Ghat, h->S, h->tau_sym * h->tau_sym, h->H64, h->H32, st));
+  return AZ_OK;
 }
 
 // The chain Z* applied to pairs of columns of b (or of the sketch), T precision.
@@ -356,7 +346,7 @@ az_status zstar_chain(az_setup_t* h, int mode, const TB* b, int64_t ldb, int nco
       in.tapx = (const T*)tp.x0; in.tapy = (const T*)tp.y0; in.Wx = tp.Wx; in.Wy = tp.Wy;
       AZ_TRY(launch_colfwd_stencil<T>(g, in, p0, np, X1, tb, st));
     } else {
-      AZ_TRY((launch_colfwd_gather<T, TB>(g, h->pos2m, b, ldb, ncols, p0, np, X1, tb, st)));
+      AZ_TRY((launch_colfwd_gather<T, TB>(g, h->pos2m, b, ldb, ncols, p0, np, X1, tb, st, h->M)));
     }
     AZ_TRY(launch_rowfold<T>(g, X1, Hsym<T>(h), np, X3, tb, st));
     AZ_TRY((launch_colinv<T, T>(g, X3, p0, np, ncols, zout, ldz, mode != 0 ? h->bits : nullptr, h->nw, tb, st)));
@@ -378,28 +368,26 @@ az_status apply_rows(az_setup_t* h, const TZ* z, int64_t ldz, const TB* b, int64
   return AZ_OK;
 }
 
+// S3-S7: Rademacher bits, sketch W = (I - Z* A) R and Y = A W, then the
+// SVQB + Cholesky factorisation and truncated SVD.  Launches only.
 template <typename T>
 az_status sketch_and_factor(az_setup_t* h, cudaStream_t st) {
   const Geom& g = h->g;
   const int k = h->k;
   T* W = (T*)h->W;
   T* Y = (T*)h->Y;
+  AZ_TRY(launch_philox_bits(h->bits, g.N, k, h->seed, st));
   if (h->kind == 0) {
     // W = (I - Z* A) R through the fused FFT chain (A R by the local stencil)
     AZ_TRY((zstar_chain<T, double>(h, 1, nullptr, 0, k, W, g.N, st)));
   } else {
-    // Poisson: v = A R on all rows by the stencil rows (R materialised in FP64),
-    // then W = R - Z* v through the gather chain (Z* ignores the boundary rows).
-    double* Rd;
-    AZ_CUDA(cudaMalloc((void**)&Rd, (size_t)g.N * k * sizeof(double)));
+    // Collocation: v = A R on all rows by the stencil rows (R materialised in
+    // FP64), then W = R - Z* v through the gather chain (Z* has zero columns
+    // for the boundary rows).
     T* v = (T*)h->gb;    // Mtot x k scratch (gb holds >= k columns)
-    az_status rc = launch_bits_to_R(h->bits, g.N, k, Rd, st);
-    if (rc == AZ_OK) rc = apply_rows<T, double, double, T>(h, Rd, g.N, nullptr, 0, (T)0, (T)1, v, h->Mtot, k, st);
-    if (rc == AZ_OK) rc = zstar_chain<T, T>(h, 2, v, h->Mtot, k, W, g.N, st);
-    cudaError_t e = cudaStreamSynchronize(st);
-    cudaFree(Rd);
-    if (rc) return rc;
-    if (e != cudaSuccess) { set_error(std::string("sketch: ") + cudaGetErrorString(e)); return AZ_ERR_CUDA; }
+    AZ_TRY(launch_bits_to_R(h->bits, g.N, k, h->Rd, st));
+    AZ_TRY((apply_rows<T, double, double, T>(h, h->Rd, g.N, nullptr, 0, (T)0, (T)1, v, h->Mtot, k, st)));
+    AZ_TRY((zstar_chain<T, T>(h, 2, v, h->Mtot, k, W, g.N, st)));
   }
   // Y = A W on all rows (kept grid rows, then weighted boundary rows)
   AZ_TRY((apply_rows<T, T, double, T>(h, W, g.N, nullptr, 0, (T)0, (T)1, Y, h->Mtot, k, st)));
@@ -407,38 +395,45 @@ az_status sketch_and_factor(az_setup_t* h, cudaStream_t st) {
   AZ_TRY((launch_gram<T, T>(Y, h->Mtot, k, Y, h->Mtot, k, h->Mtot, h->partial, h->G, st)));
   const double taug = Prec<T>::fp64 ? 1e-8 : 1e-7;
   AZ_TRY(launch_factor1(h->G, k, taug, h->floor * h->floor, h->V, h->lam, h->B1, h->info, st));
-  // Q1 = Y B1 (FP64)
-  double* Q1;
-  AZ_CUDA(cudaMalloc((void**)&Q1, (size_t)h->Mtot * k * sizeof(double)));
-  az_status rc = launch_tsprod<T, double>(Y, h->Mtot, k, h->B1, k, h->Mtot, Q1, h->Mtot, st);
-  if (rc == AZ_OK) rc = launch_gram<double, double>(Q1, h->Mtot, k, Q1, h->Mtot, k, h->Mtot, h->partial, h->G, st);
-  if (rc == AZ_OK) rc = launch_factor2(h->G, k, h->V, h->lam, h->tau_svd, h->floor, h->Tm, h->VS, h->sig, h->info, st);
-  if (rc == AZ_OK) rc = launch_tsprod<double, T>(Q1, h->Mtot, k, h->Tm, k, h->Mtot, (T*)h->Ut, h->Mtot, st);
-  cudaError_t e = cudaStreamSynchronize(st);
-  cudaFree(Q1);
-  if (rc) return rc;
-  if (e != cudaSuccess) { set_error(std::string("factorisation: ") + cudaGetErrorString(e)); return AZ_ERR_CUDA; }
-  FactorInfo fi;
-  AZ_CUDA(cudaMemcpy(&fi, h->info, sizeof(fi), cudaMemcpyDeviceToHost));
-  if (fi.status != 0) {
-    set_error(fi.status == 1 ? "factorisation: Cholesky breakdown in the second pass" : "factorisation: non-finite sketch");
-    return AZ_ERR_NUMERIC;
+  // pass 2: Q1 = Y B1, G2 = Q1^T Q1, Cholesky, SVD of the small factor, Ut = Q1 T
+  if (Prec<T>::fp64) {
+    AZ_TRY((launch_tsprod<T, double>(Y, h->Mtot, k, h->B1, k, h->Mtot, h->Q1, h->Mtot, st)));
+    AZ_TRY((launch_gram<double, double>(h->Q1, h->Mtot, k, h->Q1, h->Mtot, k, h->Mtot, h->partial, h->G, st)));
+    AZ_TRY(launch_factor2(h->G, k, h->V, h->lam, h->tau_svd, h->floor, h->Tm, h->VS, h->sig, h->info, st));
+    AZ_TRY((launch_tsprod<double, T>(h->Q1, h->Mtot, k, h->Tm, k, h->Mtot, (T*)h->Ut, h->Mtot, st)));
+  } else {
+    // mixed: Q1 = Y B1 needs extended precision (its small directions cancel
+    // by up to sigma_1 / sigma_r1), computed in double-float and rounded to
+    // FP32; Q1 is then well conditioned, so G2 and Ut = Q1 T run in FP32.
+    float* Q1f = (float*)h->Q1;
+    AZ_TRY(launch_tsprod_df<float>((const float*)Y, h->Mtot, k, h->B1, k, h->Mtot, Q1f, h->Mtot, st));
+    AZ_TRY((launch_gram<float, float>(Q1f, h->Mtot, k, Q1f, h->Mtot, k, h->Mtot, h->partial, h->G, st, true)));
+    AZ_TRY(launch_factor2(h->G, k, h->V, h->lam, h->tau_svd, h->floor, h->Tm, h->VS, h->sig, h->info, st));
+    AZ_TRY((launch_tsprod<float, float>(Q1f, h->Mtot, k, h->Tm, k, h->Mtot, (float*)h->Ut, h->Mtot, st)));
   }
   return AZ_OK;
+}
+
+az_status compute_setup(az_setup_t* h, cudaStream_t st, bool with_index_map) {
+  if (with_index_map) AZ_TRY(launch_compact(h->mask, h->g.L, h->pos2m, h->idx, h->Md, h->scan, st));
+  AZ_TRY(build_symbol(h, st));
+  return h->precision == AZ_FP64 ? sketch_and_factor<double>(h, st) : sketch_and_factor<float>(h, st);
 }
 
 // One AZ solve of ncols columns (T precision): x (=|+=) Z* b + W VS U^T (b - A Z* b)
 template <typename T, typename TB>
 az_status az_once(az_setup_t* h, const TB* b, int64_t ldb, int ncols, double* x, int64_t ldx, bool accumulate,
-                  cudaStream_t st) {
+                  cudaStream_t st, bool want_xf = false) {
   const Geom& g = h->g;
   T* z = (T*)h->zb;
   T* gg = (T*)h->gb;
   AZ_TRY((zstar_chain<T, TB>(h, 0, b, ldb, ncols, z, g.N, st)));
   AZ_TRY((apply_rows<T, T, TB, T>(h, z, g.N, b, ldb, (T)1, (T)-1, gg, h->Mtot, ncols, st)));
-  AZ_TRY((launch_gram<T, T>((const T*)h->Ut, h->Mtot, h->k, gg, h->Mtot, ncols, h->Mtot, h->partial, h->cb, st)));
+  AZ_TRY((launch_gram<T, T>((const T*)h->Ut, h->Mtot, h->k, gg, h->Mtot, ncols, h->Mtot, h->partial, h->cb, st, true)));
   AZ_TRY(launch_small_mm(h->VS, h->k, h->cb, ncols, h->ub, st));
-  AZ_TRY((launch_update_x<T, T>((const T*)h->W, g.N, h->k, h->ub, z, g.N, g.N, ncols, x, ldx, accumulate, st)));
+  // the mixed path also leaves the (exactly FP32) first-pass solution in the z buffer
+  float* xf = (want_xf && !Prec<T>::fp64) ? (float*)z : nullptr;
+  AZ_TRY((launch_update_x<T, T>((const T*)h->W, g.N, h->k, h->ub, z, g.N, g.N, ncols, x, ldx, accumulate, st, xf)));
   return AZ_OK;
 }
 
@@ -450,23 +445,39 @@ az_status solve_impl(az_setup_t* h, const double* b, int64_t ldb, int64_t nrhs, 
     const int nc = (int)std::min<int64_t>(chunk, nrhs - c0);
     const double* bc = b + c0 * ldb;
     double* xc = x + c0 * ldx;
-    AZ_TRY((az_once<T, double>(h, bc, ldb, nc, xc, ldx, false, st)));
+    AZ_TRY((az_once<T, double>(h, bc, ldb, nc, xc, ldx, false, st, h->refine > 0)));
     for (int it = 0; it < h->refine; ++it) {
       T* res = (T*)h->rb;
-      // r = b - A x with the residual computed in FP64
-      AZ_TRY((apply_rows<double, double, double, T>(h, xc, ldx, bc, ldb, 1.0, -1.0, res, h->Mtot, nc, st)));
+      if (!Prec<T>::fp64 && it == 0) {
+        // r = b - A x, FP64-accurate: x is exactly FP32 after the first pass, so
+        // double-FP32 arithmetic on the split FP64 taps reproduces the FP64
+        // residual (about 48 significant bits) at FP32 throughput
+        const float* th[4] = {h->tapsH[0], h->tapsH[1], h->tapsH[2], h->tapsH[3]};
+        const float* tl[4] = {h->tapsL[0], h->tapsL[1], h->tapsL[2], h->tapsL[3]};
+        AZ_TRY(launch_resid_df(h->g, h->kind, h->eps, h->idx, h->M, th, tl, h->W64[0], h->W64[1], (const float*)h->zb,
+                               h->g.N, bc, ldb, (float*)res, h->Mtot, nc, st));
+        if (h->Mb) {
+          AZ_TRY((launch_boundary_rows<double, double, double, T>(h->g, h->eps, h->bweight, h->bpts, h->Mb, xc, ldx,
+                                                                  bc + h->M, ldb, 1.0, -1.0, res + h->M, h->Mtot, nc, st)));
+        }
+      } else {
+        // r = b - A x with the residual computed in FP64
+        AZ_TRY((apply_rows<double, double, double, T>(h, xc, ldx, bc, ldb, 1.0, -1.0, res, h->Mtot, nc, st)));
+      }
       AZ_TRY((az_once<T, T>(h, res, h->Mtot, nc, xc, ldx, true, st)));
     }
     if (relres) {
-      double* r64;
-      AZ_CUDA(cudaMalloc((void**)&r64, (size_t)h->Mtot * nc * sizeof(double)));
+      if (!h->r64) {
+        cudaError_t e0 = cudaMalloc((void**)&h->r64, (size_t)h->Mtot * chunk * sizeof(double));
+        if (e0 != cudaSuccess) { cudaGetLastError(); h->r64 = nullptr; set_error("relres buffer"); return AZ_ERR_OOM; }
+      }
+      double* r64 = h->r64;
       az_status rc = apply_rows<double, double, double, double>(h, xc, ldx, bc, ldb, 1.0, -1.0, r64, h->Mtot, nc, st);
       if (rc == AZ_OK) rc = launch_sumsq_cols(r64, h->Mtot, h->Mtot, nc, h->normb, st);
       if (rc == AZ_OK) rc = launch_sumsq_cols(bc, ldb, h->Mtot, nc, h->normb + nc, st);
       std::vector<double> hv(2 * nc);
       cudaError_t e = cudaMemcpyAsync(hv.data(), h->normb, 2 * nc * sizeof(double), cudaMemcpyDeviceToHost, st);
       cudaError_t e2 = cudaStreamSynchronize(st);
-      cudaFree(r64);
       if (rc) return rc;
       if (e != cudaSuccess || e2 != cudaSuccess) { set_error("relres readback failed"); return AZ_ERR_CUDA; }
       for (int c = 0; c < nc; ++c) relres[c0 + c] = hv[nc + c] > 0 ? std::sqrt(hv[c] / hv[nc + c]) : 0.0;
@@ -499,6 +510,8 @@ void destroy(az_setup_t* h) {
   for (void* p : h->allocs) cudaFree(p);
   if (h->X1d) cudaFree(h->X1d);
   if (h->X3d) cudaFree(h->X3d);
+  if (h->r64) cudaFree(h->r64);
+  if (h->bcoll) cudaFree(h->bcoll);
   delete h;
 }
 
@@ -578,15 +591,16 @@ az_status az_setup(const az_grid* gr, const uint8_t* mask, const double* bpts, i
   h->Mb = h->kind == 1 ? n_boundary : 0;
   Geom& g = h->g;
   do {
-    // S1: index map
+    // S1: index map (the count M fixes the remaining allocations: one sync)
+    rc = dalloc_t(h, &h->mask, g.L); if (rc) break;
+    if (cudaMemcpyAsync(h->mask, mask, g.L, cudaMemcpyDeviceToDevice, st) != cudaSuccess) { set_error("az_setup: mask copy"); rc = AZ_ERR_CUDA; break; }
     rc = dalloc_t(h, &h->pos2m, g.L); if (rc) break;
     rc = dalloc_t(h, &h->idx, g.L); if (rc) break;
-    int32_t* scratch; int64_t* Md;
-    rc = dalloc_t(h, &scratch, 4096); if (rc) break;
-    rc = dalloc_t(h, &Md, 1); if (rc) break;
-    rc = launch_compact(mask, g.L, h->pos2m, h->idx, Md, scratch, st); if (rc) break;
+    rc = dalloc_t(h, &h->scan, 4096); if (rc) break;
+    rc = dalloc_t(h, &h->Md, 1); if (rc) break;
+    rc = launch_compact(h->mask, g.L, h->pos2m, h->idx, h->Md, h->scan, st); if (rc) break;
     int64_t M = 0;
-    if (cudaMemcpyAsync(&M, Md, sizeof(int64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+    if (cudaMemcpyAsync(&M, h->Md, sizeof(int64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) { set_error("az_setup: reading M failed"); rc = AZ_ERR_CUDA; break; }
     h->M = M;
     h->Mtot = M + h->Mb;
@@ -595,7 +609,7 @@ az_status az_setup(const az_grid* gr, const uint8_t* mask, const double* bpts, i
       rc = dalloc_t(h, &h->bpts, 2 * h->Mb); if (rc) break;
       if (cudaMemcpyAsync(h->bpts, bpts, 2 * h->Mb * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess) { rc = AZ_ERR_CUDA; break; }
     }
-    // twiddle tables
+    // twiddle tables (host-built constants)
     {
       std::vector<double> re, im;
       host_twiddles(4096, re, im);
@@ -609,17 +623,16 @@ az_status az_setup(const az_grid* gr, const uint8_t* mask, const double* bpts, i
       rc = big_tables(h, g.L, &h->big64[0], &h->big64[1], &h->big32[0], &h->big32[1], st); if (rc) break;
       rc = big_tables(h, g.N, &h->big64[2], &h->big64[3], &h->big32[2], &h->big32[3], st); if (rc) break;
     }
-    // S2: symbol
-    rc = build_symbol(h, st); if (rc) break;
-    // S3: Rademacher bits
+    stencil_widths(h);
+    rc = alloc_symbol(h); if (rc) break;
     h->nw = (g.N + 31) / 32;
     rc = dalloc_t(h, &h->bits, (size_t)h->nw * h->k + 4); if (rc) break;
-    rc = launch_philox_bits(h->bits, g.N, h->k, h->seed, st); if (rc) break;
-    // buffers
     const size_t tsz = h->precision == AZ_FP64 ? 8 : 4;
     rc = dalloc(h, &h->W, (size_t)g.N * h->k * tsz); if (rc) break;
     rc = dalloc(h, &h->Y, (size_t)h->Mtot * h->k * tsz); if (rc) break;
     rc = dalloc(h, &h->Ut, (size_t)h->Mtot * h->k * tsz); if (rc) break;
+    rc = dalloc_t(h, &h->Q1, (size_t)h->Mtot * h->k); if (rc) break;
+    if (h->kind == 1) { rc = dalloc_t(h, &h->Rd, (size_t)g.N * h->k); if (rc) break; }
     for (double** p : {&h->G, &h->V, &h->B1, &h->Tm, &h->VS}) { rc = dalloc_t(h, p, (size_t)h->k * h->k); if (rc) break; }
     if (rc) break;
     rc = dalloc_t(h, &h->lam, h->k); if (rc) break;
@@ -627,22 +640,37 @@ az_status az_setup(const az_grid* gr, const uint8_t* mask, const double* bpts, i
     rc = dalloc_t(h, &h->info, 1); if (rc) break;
     rc = alloc_workspace(h); if (rc) break;
     rc = dalloc_t(h, &h->partial, (size_t)gram_blocks(h->Mtot) * h->k * std::max(h->k, 2 * h->pairs_max)); if (rc) break;
-    // rounding floor of the sketch's singular values (see oracle reading):
-    // 1e-13 * ||A R||_F, with ||A R||_F^2 ~ k (M/L) N ||g||^2 estimated from the symbol
+    // rounding floor of the sketch's singular values: 1e-13 * ||A R||_F, with
+    // ||A R||_F^2 ~ k (Mtot/L) sum_k S_k / s (estimate from the symbol's peak)
+    rc = build_symbol(h, st); if (rc) break;
     {
-      std::vector<double> S(1);
-      double smax;
-      cudaMemcpy(&smax, h->S + g.N, sizeof(double), cudaMemcpyDeviceToHost);
+      double smax = 0;
+      if (cudaMemcpyAsync(&smax, h->S + g.N, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess) { set_error("az_setup: symbol readback"); rc = AZ_ERR_CUDA; break; }
       double est = std::sqrt((double)h->k * (double)h->Mtot / (double)g.L * (double)g.N * smax / (double)(g.s[0] * g.s[1]));
       h->floor = 1e-13 * est;
     }
-    // S4-S7
+    // S3-S7
     rc = h->precision == AZ_FP64 ? sketch_and_factor<double>(h, st) : sketch_and_factor<float>(h, st);
     if (rc) break;
+    FactorInfo fi;
+    if (cudaMemcpyAsync(&fi, h->info, sizeof(fi), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) { set_error("az_setup: factorisation readback"); rc = AZ_ERR_CUDA; break; }
+    if (fi.status != 0) {
+      set_error(fi.status == 1 ? "factorisation: Cholesky breakdown in the second pass" : "factorisation: non-finite sketch");
+      rc = AZ_ERR_NUMERIC;
+      break;
+    }
   } while (0);
   if (rc) { destroy(h); return rc; }
   *out = h;
   return AZ_OK;
+}
+
+az_status az_refactor(az_handle h, uint64_t seed, void* stream) {
+  if (!h) { set_error("az_refactor: null handle"); return AZ_ERR_ARG; }
+  h->seed = seed;
+  return compute_setup(h, (cudaStream_t)stream, true);
 }
 
 az_status az_solve(az_handle h, const double* b, int64_t ldb, int64_t nrhs, double* x, int64_t ldx, void* stream,

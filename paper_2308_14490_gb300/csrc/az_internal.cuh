@@ -67,6 +67,7 @@ struct Geom {
   int G0, N1, logG0, logN1;   // N-grid (fold output) factorisation
   int Rg, Rstride, Fq;        // fold: rows per group, row stride, within-row alias count
   int Wst32[2], Wst64[2];     // stencil half-widths (grid units of the L-grid)
+  int logN, logs[2], logn[2], logLd[2], logRg;
 };
 
 // Device tables owned by a setup.

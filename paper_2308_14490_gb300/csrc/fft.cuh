@@ -108,16 +108,18 @@ template <typename V, int R, bool INV> __device__ __forceinline__ void dftR(V* a
   else dft16<V, INV>(a);
 }
 
-// One Stockham stage over all lines.  tw: table of n twiddles exp(-2 pi i m/n).
-template <typename V, int R, bool INV>
-__device__ __forceinline__ void stockham_stage(const V* __restrict__ in, V* __restrict__ out, int n, int Ns,
-                                               int nlines, int cs, int is, const V* __restrict__ tw, int tws) {
-  const int nbf = n / R;
-  const int total = nbf * nlines;
+// One Stockham stage over all lines (nlines = 2^lognl, n = 2^logn).
+template <typename V, int R, int LOGR, bool INV>
+__device__ __forceinline__ void stockham_stage(const V* __restrict__ in, V* __restrict__ out, int logn, int Ns,
+                                               int lognl, int cs, int is, const V* __restrict__ tw, int tws) {
+  const int n = 1 << logn;
+  const int lognbf = logn - LOGR;
+  const int nbf = 1 << lognbf;
+  const int total = nbf << lognl;
   const int step = n / (Ns * R);
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
     int c, j;
-    if (cs == 1) { c = t % nlines; j = t / nlines; } else { j = t % nbf; c = t / nbf; }
+    if (cs == 1) { c = t & ((1 << lognl) - 1); j = t >> lognl; } else { j = t & (nbf - 1); c = t >> lognbf; }
     const int k = j & (Ns - 1);
     V a[R];
 #pragma unroll
@@ -137,19 +139,18 @@ __device__ __forceinline__ void stockham_stage(const V* __restrict__ in, V* __re
   }
 }
 
-// Full FFT of length n = 2^logn on nlines lines.  Data starts in buf[0]; the
+// Full FFT of length n = 2^logn on 2^lognl lines.  Data starts in buf0; the
 // result ends in buf[return value] (0 or 1).  Contains __syncthreads().
 template <typename V, bool INV>
-__device__ int fft_lines(V* buf0, V* buf1, int logn, int nlines, int cs, int is, const V* __restrict__ tw, int tws) {
+__device__ int fft_lines(V* buf0, V* buf1, int logn, int lognl, int cs, int is, const V* __restrict__ tw, int tws) {
   V* b[2] = {buf0, buf1};
   int cur = 0, Ns = 1, rem = logn;
-  const int n = 1 << logn;
   while (rem > 0) {
     // radix plan: 16 while >= 4 bits remain (but avoid leaving 1 bit: use 8 then)
-    if (rem >= 4 && rem != 5) { stockham_stage<V, 16, INV>(b[cur], b[cur ^ 1], n, Ns, nlines, cs, is, tw, tws); Ns <<= 4; rem -= 4; }
-    else if (rem >= 3) { stockham_stage<V, 8, INV>(b[cur], b[cur ^ 1], n, Ns, nlines, cs, is, tw, tws); Ns <<= 3; rem -= 3; }
-    else if (rem == 2) { stockham_stage<V, 4, INV>(b[cur], b[cur ^ 1], n, Ns, nlines, cs, is, tw, tws); Ns <<= 2; rem -= 2; }
-    else { stockham_stage<V, 2, INV>(b[cur], b[cur ^ 1], n, Ns, nlines, cs, is, tw, tws); Ns <<= 1; rem -= 1; }
+    if (rem >= 4 && rem != 5) { stockham_stage<V, 16, 4, INV>(b[cur], b[cur ^ 1], logn, Ns, lognl, cs, is, tw, tws); Ns <<= 4; rem -= 4; }
+    else if (rem >= 3) { stockham_stage<V, 8, 3, INV>(b[cur], b[cur ^ 1], logn, Ns, lognl, cs, is, tw, tws); Ns <<= 3; rem -= 3; }
+    else if (rem == 2) { stockham_stage<V, 4, 2, INV>(b[cur], b[cur ^ 1], logn, Ns, lognl, cs, is, tw, tws); Ns <<= 2; rem -= 2; }
+    else { stockham_stage<V, 2, 1, INV>(b[cur], b[cur ^ 1], logn, Ns, lognl, cs, is, tw, tws); Ns <<= 1; rem -= 1; }
     cur ^= 1;
     __syncthreads();
   }

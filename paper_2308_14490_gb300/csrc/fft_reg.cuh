@@ -1,0 +1,106 @@
+// Register-resident Stockham FFT of one line distributed over P threads.
+//
+// A line of length n = 2^logn (n >= E) is held by P = n / E threads, E
+// elements each.  Each Stockham stage of radix R = 2^LR (R <= E) gives every
+// thread E/R butterflies j = tl + g P (g < E/R); butterfly j reads positions
+// j + u n/R, applies the twiddles w_{Ns R}^{u k} (k = j mod Ns), does a radix-R
+// DFT and writes positions (j - k) R + k + u Ns.  The first stage takes its
+// inputs from a caller-supplied prologue, the last stage hands its outputs to
+// an epilogue, and the stages in between exchange data through one
+// shared-memory buffer, padded by one element every 2^PADSH elements to spread
+// strided accesses over the banks.  Stage radices are compile-time (one stage
+// of radix 2^(logn mod log E) first, then radix-E stages) so the E values stay
+// in registers.  Every thread of the block must call this (it contains
+// __syncthreads()); threads with active == false only take part in barriers.
+#pragma once
+#include "fft.cuh"
+
+namespace az {
+
+template <int PADSH> __device__ __forceinline__ int padix(int e) { return e + (e >> PADSH); }
+
+template <typename V, int E, int LR, bool INV, int PADSH, class Pro, class Epi>
+__device__ __forceinline__ void fft_stage(V (&v)[E], V* __restrict__ sm, int logn, int Ns, bool first, bool last,
+                                          bool active, int line, int tl, int cs, int is, const V* __restrict__ tw,
+                                          int tws, Pro& pro, Epi& epi, bool sync_first) {
+  constexpr int R = 1 << LR;
+  constexpr int NG = E / R;
+  const int n = 1 << logn;
+  const int nbf = n >> LR;
+  const int P = n / E;
+  const int step = n / (Ns * R);
+  if (active) {
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+      const int j = tl + g * P;
+#pragma unroll
+      for (int u = 0; u < R; ++u) {
+        const int p = j + u * nbf;
+        if (first) v[g * R + u] = pro(p);
+        else v[g * R + u] = sm[padix<PADSH>(line * cs + p * is)];
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+      const int j = tl + g * P;
+      const int k = j & (Ns - 1);
+      if (Ns > 1) {
+#pragma unroll
+        for (int u = 1; u < R; ++u) {
+          V w = __ldg(tw + ((u * k * step) & (n - 1)) * tws);
+          if (INV) w.y = -w.y;
+          v[g * R + u] = cmul(v[g * R + u], w);
+        }
+      }
+      dftR<V, R, INV>(v + g * R);
+    }
+  }
+  if (!first || sync_first) __syncthreads();  // everyone has read the previous stage's buffer
+  if (active) {
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+      const int j = tl + g * P;
+      const int k = j & (Ns - 1);
+#pragma unroll
+      for (int u = 0; u < R; ++u) {
+        const int o = (j - k) * R + k + u * Ns;
+        if (last) epi(o, v[g * R + u]);
+        else sm[padix<PADSH>(line * cs + o * is)] = v[g * R + u];
+      }
+    }
+  }
+  if (!last) __syncthreads();   // stage output visible
+}
+
+// sync_first: the prologue reads the shared buffer itself, so the first
+// stage must also wait for every thread's reads before storing.
+template <typename V, int E, bool INV, int PADSH, class Pro, class Epi>
+__device__ __forceinline__ void fft_reg(V* __restrict__ sm, int logn, bool active, int line, int tl, int cs, int is,
+                                        const V* __restrict__ tw, int tws, Pro pro, Epi epi, bool sync_first = false) {
+  constexpr int LOGE = E == 16 ? 4 : (E == 8 ? 3 : (E == 4 ? 2 : 1));
+  V v[E];
+  const int r0 = logn % LOGE;
+  const int nfull = logn / LOGE;
+  int Ns = 1;
+  bool first = true;
+  if (r0 != 0) {
+    const bool last = nfull == 0;
+    if (r0 == 1) fft_stage<V, E, 1, INV, PADSH>(v, sm, logn, Ns, true, last, active, line, tl, cs, is, tw, tws, pro, epi, sync_first);
+    if constexpr (LOGE > 2) {
+      if (r0 == 2) fft_stage<V, E, 2, INV, PADSH>(v, sm, logn, Ns, true, last, active, line, tl, cs, is, tw, tws, pro, epi, sync_first);
+    }
+    if constexpr (LOGE > 3) {
+      if (r0 == 3) fft_stage<V, E, 3, INV, PADSH>(v, sm, logn, Ns, true, last, active, line, tl, cs, is, tw, tws, pro, epi, sync_first);
+    }
+    Ns <<= r0;
+    first = false;
+  }
+  for (int st = 0; st < nfull; ++st) {
+    fft_stage<V, E, LOGE, INV, PADSH>(v, sm, logn, Ns, first, st == nfull - 1, active, line, tl, cs, is, tw, tws, pro, epi,
+                                      first && sync_first);
+    Ns <<= LOGE;
+    first = false;
+  }
+}
+
+}  // namespace az

@@ -4,10 +4,13 @@
 #include <cmath>
 #include <algorithm>
 #include "kernels.cuh"
+#include "profile.cuh"
+#include "fft_reg.cuh"
 
 namespace az {
 
 static constexpr int TW_N = 4096;  // master twiddle table length
+static inline size_t padix_host(size_t e, int sh) { return e + (e >> sh); }
 
 // ------------------------------------------------------------------ utilities
 template <typename K>
@@ -108,6 +111,7 @@ az_status launch_compact(const uint8_t* mask, int64_t L, int32_t* pos2m, int32_t
                          int32_t* scratch, cudaStream_t st) {
   int nb = (int)((L + 4095) / 4096);
   if (nb > 4096) { set_error("grid too large for the index map"); return AZ_ERR_ARG; }
+  ProfScope ps("compact", 6.0 * L, st, 3);
   k_count<<<nb, 256, 0, st>>>(mask, L, scratch);
   k_scan_blocks<<<1, 32, 0, st>>>(scratch, nb, M_dev);
   k_scatter<<<nb, 256, 0, st>>>(mask, L, scratch, pos2m, idx);
@@ -129,19 +133,25 @@ __global__ void k_samples(double* g, int64_t L, double hL, double eps, int deriv
   g[m] = acc;
 }
 az_status launch_samples(double* g, int64_t L, double hL, double eps, int deriv, int pimg, cudaStream_t st) {
+  ProfScope ps("samples", 8.0 * L, st);
   k_samples<<<(unsigned)((L + 255) / 256), 256, 0, st>>>(g, L, hL, eps, deriv, pimg);
   AZ_LAUNCH_CHECK();
   return AZ_OK;
 }
-__global__ void k_taps(const double* g, int64_t L, int W, double* t64, float* t32) {
+__global__ void k_taps(const double* g, int64_t L, int W64, double* t64, int W32, float* t32, float* th, float* tl) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i > 2 * W) return;
-  int64_t m = fmod_pos((int64_t)i - W, L);
-  t64[i] = g[m];
-  t32[i] = (float)g[m];
+  if (i <= 2 * W64) {
+    const double v = g[fmod_pos((int64_t)i - W64, L)];
+    t64[i] = v;
+    if (th) { const float h = (float)v; th[i] = h; tl[i] = (float)(v - (double)h); }
+  }
+  if (i <= 2 * W32) t32[i] = (float)g[fmod_pos((int64_t)i - W32, L)];
 }
-az_status launch_taps(const double* g, int64_t L, int W, double* t64, float* t32, cudaStream_t st) {
-  k_taps<<<(2 * W + 1 + 127) / 128, 128, 0, st>>>(g, L, W, t64, t32);
+az_status launch_taps(const double* g, int64_t L, int W64, double* t64, int W32, float* t32, cudaStream_t st,
+                      float* th, float* tl) {
+  const int W = W64 > W32 ? W64 : W32;
+  ProfScope ps("taps", 12.0 * (2 * W + 1), st);
+  k_taps<<<(2 * W + 1 + 127) / 128, 128, 0, st>>>(g, L, W64, t64, W32, t32, th, tl);
   AZ_LAUNCH_CHECK();
   return AZ_OK;
 }
@@ -165,6 +175,7 @@ __global__ void k_philox_bits(uint32_t* bits, int64_t N, int k, uint32_t k0, uin
 az_status launch_philox_bits(uint32_t* bits, int64_t N, int k, uint64_t seed, cudaStream_t st) {
   int64_t nblk = (N + 127) / 128;
   dim3 grid((unsigned)((nblk + 127) / 128), (unsigned)k);
+  ProfScope ps("philox_bits", 4.0 * ((N + 31) / 32) * k, st);
   k_philox_bits<<<grid, 128, 0, st>>>(bits, N, k, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32));
   AZ_LAUNCH_CHECK();
   return AZ_OK;
@@ -177,6 +188,7 @@ __global__ void k_bits_to_R(const uint32_t* bits, int64_t N, int k, double* R) {
 }
 az_status launch_bits_to_R(const uint32_t* bits, int64_t N, int k, double* R, cudaStream_t st) {
   dim3 grid((unsigned)((N + 255) / 256), (unsigned)k);
+  ProfScope ps("bits_to_R", 8.25 * N * k, st);
   k_bits_to_R<<<grid, 256, 0, st>>>(bits, N, k, R);
   AZ_LAUNCH_CHECK();
   return AZ_OK;
@@ -184,11 +196,16 @@ az_status launch_bits_to_R(const uint32_t* bits, int64_t N, int k, double* R, cu
 
 // ------------------------------------------------------------------ FFT pass helpers
 template <typename V>
-__device__ __forceinline__ V big_tw(const V* __restrict__ A, const V* __restrict__ B, int64_t m, bool inv) {
+__device__ __forceinline__ V big_tw(const V* __restrict__ A, const V* __restrict__ B, int m, bool inv) {
   V w = cmul(__ldg(A + (m >> 12)), __ldg(B + (m & 4095)));
   if (inv) w.y = -w.y;
   return w;
 }
+// ceil(a / 2^l) and floor(a / 2^l) for signed a (arithmetic shift floors)
+__device__ __forceinline__ int cdiv_p2(int a, int l) { return -((-a) >> l); }
+__device__ __forceinline__ int fdiv_p2(int a, int l) { return a >> l; }
+
+static int ilog2i(int v) { int l = 0; while ((1 << l) < v) ++l; return l; }
 
 // Column tile width for a column pass of FFT length n (ping-pong buffers <= 128 KB).
 template <typename V> static int col_tile(int n, int ncols) {
@@ -201,29 +218,31 @@ template <typename V> static int col_tile(int n, int ncols) {
 // Forward column FFT of the tile held in s0 (layout [i*C + c]) then store with
 // the four-step twiddle (1D) into X1[pair][k0*D1 + n1].
 template <typename T>
-__device__ void colfwd_finish(const Geom& g, typename C2<T>::t* s0, typename C2<T>::t* s1, int C, int c0,
+__device__ void colfwd_finish(const Geom& g, typename C2<T>::t* s0, typename C2<T>::t* s1, int logC, int c0,
                               typename C2<T>::t* __restrict__ X1, const PassTabs& tb) {
   using V = typename C2<T>::t;
   __syncthreads();
-  int cur = fft_lines<V, false>(s0, s1, g.logD0, C, 1, C, (const V*)tb.tw, TW_N >> g.logD0);
+  int cur = fft_lines<V, false>(s0, s1, g.logD0, logC, 1, 1 << logC, (const V*)tb.tw, TW_N >> g.logD0);
   V* res = cur ? s1 : s0;
-  const int64_t total = (int64_t)g.D0 * C;
-  for (int64_t t = threadIdx.x; t < total; t += blockDim.x) {
-    int c = (int)(t % C), k0 = (int)(t / C);
-    int n1 = c0 + c;
+  const int total = g.D0 << logC;
+  const int Cm = (1 << logC) - 1;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int c = t & Cm, k0 = t >> logC;
+    const int n1 = c0 + c;
     V v = res[t];
-    if (g.dim == 1 && k0 != 0 && n1 != 0) v = cmul(v, big_tw<V>((const V*)tb.bigA, (const V*)tb.bigB, (int64_t)n1 * k0, false));
-    X1[(int64_t)k0 * g.D1 + n1] = v;
+    if (g.dim == 1 && k0 != 0 && n1 != 0) v = cmul(v, big_tw<V>((const V*)tb.bigA, (const V*)tb.bigB, n1 * k0, false));
+    X1[(k0 << g.logD1) + n1] = v;
   }
 }
 
 // Sketch prologue: v = mask * (A^c R) at the tile's grid points, two Rademacher
 // columns packed as (real, imag).
 template <typename T>
-__global__ void k_colfwd_stencil(Geom g, SketchIn<T> in, int pair0, int C, typename C2<T>::t* X1base,
-                                 PassTabs tb) {
+__global__ void __launch_bounds__(256) k_colfwd_stencil(Geom g, SketchIn<T> in, int pair0, int logC,
+                                                        typename C2<T>::t* X1base, PassTabs tb) {
   using V = typename C2<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int C = 1 << logC, Cm = C - 1;
   V* s0 = (V*)smem_raw;
   V* s1 = s0 + (size_t)g.D0 * C;
   const int c0 = blockIdx.x * C;
@@ -232,18 +251,19 @@ __global__ void k_colfwd_stencil(Geom g, SketchIn<T> in, int pair0, int C, typen
   const bool hasB = colB < in.k;
   V* X1 = X1base + (int64_t)blockIdx.y * g.L;
   if (g.dim == 1) {
-    const int s = g.s[0];
-    const int64_t N = g.N;
-    const int64_t total = (int64_t)g.D0 * C;
-    for (int64_t t = threadIdx.x; t < total; t += blockDim.x) {
-      int c = (int)(t % C), n0 = (int)(t / C);
-      int64_t pos = (int64_t)n0 * g.D1 + c0 + c;
+    const int ls = g.logs[0], s = g.s[0];
+    const int Nm = (int)g.N - 1;
+    const int W = in.Wx;
+    const int total = g.D0 << logC;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+      const int c = t & Cm, n0 = t >> logC;
+      const int pos = (n0 << g.logD1) + c0 + c;
       T re = 0, im = 0;
       if (__ldg(in.pos2m + pos) >= 0) {
-        int64_t jlo = fdiv(pos - in.Wx + s - 1, s), jhi = fdiv(pos + in.Wx, s);
-        for (int64_t j = jlo; j <= jhi; ++j) {
-          T tap = __ldg(in.tapx + (pos - s * j + in.Wx));
-          int64_t jj = fmod_pos(j, N);
+        const int jlo = cdiv_p2(pos - W, ls), jhi = fdiv_p2(pos + W, ls);
+        for (int j = jlo; j <= jhi; ++j) {
+          const T tap = __ldg(in.tapx + (pos - s * j + W));
+          const int jj = j & Nm;
           re += tap * (T)rad_bit(in.bits, in.nw, jj, colA);
           if (hasB) im += tap * (T)rad_bit(in.bits, in.nw, jj, colB);
         }
@@ -255,17 +275,16 @@ __global__ void k_colfwd_stencil(Geom g, SketchIn<T> in, int pair0, int C, typen
     // separable: t[jx][c] = sum_jy gy(iy - sy jy) R[jx, jy]  (into s1), then
     // v[ix][c] = mask * sum_jx gx(ix - sx jx) t[jx][c]      (into s0)
     const int sx = g.s[0], sy = g.s[1];
-    const int64_t Nx = g.n[0], Ny = g.n[1];
-    const int64_t tot1 = Nx * C;
-    for (int64_t t = threadIdx.x; t < tot1; t += blockDim.x) {
-      int c = (int)(t % C);
-      int64_t jx = t / C;
-      int64_t iy = c0 + c;
-      int64_t jlo = fdiv(iy - in.Wy + sy - 1, sy), jhi = fdiv(iy + in.Wy, sy);
+    const int Nxm = (int)g.n[0] - 1, Nym = (int)g.n[1] - 1, lNy = g.logn[1];
+    const int tot1 = (int)g.n[0] << logC;
+    for (int t = threadIdx.x; t < tot1; t += blockDim.x) {
+      const int c = t & Cm, jx = t >> logC;
+      const int iy = c0 + c;
+      const int jlo = cdiv_p2(iy - in.Wy, g.logs[1]), jhi = fdiv_p2(iy + in.Wy, g.logs[1]);
       T re = 0, im = 0;
-      for (int64_t jy = jlo; jy <= jhi; ++jy) {
-        T tap = __ldg(in.tapy + (iy - sy * jy + in.Wy));
-        int64_t j = jx * Ny + fmod_pos(jy, Ny);
+      for (int jy = jlo; jy <= jhi; ++jy) {
+        const T tap = __ldg(in.tapy + (iy - sy * jy + in.Wy));
+        const int j = (jx << lNy) + (jy & Nym);
         re += tap * (T)rad_bit(in.bits, in.nw, j, colA);
         if (hasB) im += tap * (T)rad_bit(in.bits, in.nw, j, colB);
       }
@@ -273,17 +292,16 @@ __global__ void k_colfwd_stencil(Geom g, SketchIn<T> in, int pair0, int C, typen
       s1[t] = v;
     }
     __syncthreads();
-    const int64_t tot0 = (int64_t)g.D0 * C;
-    for (int64_t t = threadIdx.x; t < tot0; t += blockDim.x) {
-      int c = (int)(t % C);
-      int64_t ix = t / C;
-      int64_t pos = ix * g.D1 + c0 + c;
+    const int tot0 = g.D0 << logC;
+    for (int t = threadIdx.x; t < tot0; t += blockDim.x) {
+      const int c = t & Cm, ix = t >> logC;
+      const int pos = (ix << g.logD1) + c0 + c;
       V v; v.x = 0; v.y = 0;
       if (__ldg(in.pos2m + pos) >= 0) {
-        int64_t jlo = fdiv(ix - in.Wx + sx - 1, sx), jhi = fdiv(ix + in.Wx, sx);
-        for (int64_t jx = jlo; jx <= jhi; ++jx) {
-          T tap = __ldg(in.tapx + (ix - sx * jx + in.Wx));
-          V u = s1[fmod_pos(jx, Nx) * C + c];
+        const int jlo = cdiv_p2(ix - in.Wx, g.logs[0]), jhi = fdiv_p2(ix + in.Wx, g.logs[0]);
+        for (int jx = jlo; jx <= jhi; ++jx) {
+          const T tap = __ldg(in.tapx + (ix - sx * jx + in.Wx));
+          const V u = s1[((jx & Nxm) << logC) + c];
           v.x += tap * u.x; v.y += tap * u.y;
         }
       }
@@ -291,76 +309,83 @@ __global__ void k_colfwd_stencil(Geom g, SketchIn<T> in, int pair0, int C, typen
     }
     __syncthreads();  // s1 is reused by the FFT
   }
-  colfwd_finish<T>(g, s0, s1, C, c0, X1, tb);
+  colfwd_finish<T>(g, s0, s1, logC, c0, X1, tb);
 }
 
 template <typename T, typename TB>
-__global__ void k_colfwd_gather(Geom g, const int32_t* __restrict__ pos2m, const TB* __restrict__ b, int64_t ldb,
-                                int ncols, int pair0, int C, typename C2<T>::t* X1base, PassTabs tb) {
+__global__ void __launch_bounds__(256) k_colfwd_gather(Geom g, const int32_t* __restrict__ pos2m, const TB* __restrict__ b,
+                                                       int64_t ldb, int ncols, int pair0, int logC,
+                                                       typename C2<T>::t* X1base, PassTabs tb) {
   using V = typename C2<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int C = 1 << logC, Cm = C - 1;
   V* s0 = (V*)smem_raw;
   V* s1 = s0 + (size_t)g.D0 * C;
   const int c0 = blockIdx.x * C;
   const int pair = pair0 + blockIdx.y;
   const int colA = 2 * pair, colB = 2 * pair + 1;
+  const TB* bA = b + (int64_t)colA * ldb;
+  const TB* bB = b + (int64_t)colB * ldb;
+  const bool hasB = colB < ncols;
   V* X1 = X1base + (int64_t)blockIdx.y * g.L;
-  const int64_t total = (int64_t)g.D0 * C;
-  for (int64_t t = threadIdx.x; t < total; t += blockDim.x) {
-    int c = (int)(t % C), n0 = (int)(t / C);
-    int64_t pos = (int64_t)n0 * g.D1 + c0 + c;
-    int m = __ldg(pos2m + pos);
+  const int total = g.D0 << logC;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int c = t & Cm, n0 = t >> logC;
+    const int pos = (n0 << g.logD1) + c0 + c;
+    const int m = __ldg(pos2m + pos);
     V v; v.x = 0; v.y = 0;
     if (m >= 0) {
-      v.x = (T)b[(int64_t)colA * ldb + m];
-      if (colB < ncols) v.y = (T)b[(int64_t)colB * ldb + m];
+      v.x = (T)bA[m];
+      if (hasB) v.y = (T)bB[m];
     }
     s0[t] = v;
   }
-  colfwd_finish<T>(g, s0, s1, C, c0, X1, tb);
+  colfwd_finish<T>(g, s0, s1, logC, c0, X1, tb);
 }
 
 template <typename T>
-__global__ void k_colfwd_load(Geom g, const typename C2<T>::t* __restrict__ inbase, int C,
-                              typename C2<T>::t* X1base, PassTabs tb) {
+__global__ void __launch_bounds__(256) k_colfwd_load(Geom g, const typename C2<T>::t* __restrict__ inbase, int logC,
+                                                     typename C2<T>::t* X1base, PassTabs tb) {
   using V = typename C2<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int C = 1 << logC, Cm = C - 1;
   V* s0 = (V*)smem_raw;
   V* s1 = s0 + (size_t)g.D0 * C;
   const int c0 = blockIdx.x * C;
   const V* in = inbase + (int64_t)blockIdx.y * g.L;
   V* X1 = X1base + (int64_t)blockIdx.y * g.L;
-  const int64_t total = (int64_t)g.D0 * C;
-  for (int64_t t = threadIdx.x; t < total; t += blockDim.x) {
-    int c = (int)(t % C), n0 = (int)(t / C);
-    s0[t] = in[(int64_t)n0 * g.D1 + c0 + c];
+  const int total = g.D0 << logC;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int c = t & Cm, n0 = t >> logC;
+    s0[t] = in[(n0 << g.logD1) + c0 + c];
   }
-  colfwd_finish<T>(g, s0, s1, C, c0, X1, tb);
+  colfwd_finish<T>(g, s0, s1, logC, c0, X1, tb);
 }
 
 template <typename T>
-az_status launch_colfwd_stencil(const Geom& g, const SketchIn<T>& in, int pair0, int npairs,
+az_status launch_colfwd_stencil_v1(const Geom& g, const SketchIn<T>& in, int pair0, int npairs,
                                 typename C2<T>::t* X1, const PassTabs& tb, cudaStream_t st) {
   using V = typename C2<T>::t;
   int C = col_tile<V>(g.D0, g.D1);
   size_t sm = 2 * (size_t)g.D0 * C * sizeof(V);
-  if (g.dim == 2 && (size_t)g.n[0] * C > (size_t)g.D0 * C) return AZ_ERR_ARG;
   if (set_smem(k_colfwd_stencil<T>, sm) != cudaSuccess) { set_error("smem attribute"); return AZ_ERR_CUDA; }
   dim3 grid(g.D1 / C, npairs);
-  k_colfwd_stencil<T><<<grid, 256, sm, st>>>(g, in, pair0, C, X1, tb);
+  ProfScope ps(sizeof(T) == 4 ? "colfwd_sketch_f32" : "colfwd_sketch_f64", (double)npairs * g.L * sizeof(V) + npairs * 2.0 * g.N / 8 + 4.0 * g.L, st);
+  k_colfwd_stencil<T><<<grid, 256, sm, st>>>(g, in, pair0, ilog2i(C), X1, tb);
   AZ_LAUNCH_CHECK();
   return AZ_OK;
 }
 template <typename T, typename TB>
-az_status launch_colfwd_gather(const Geom& g, const int32_t* pos2m, const TB* b, int64_t ldb, int ncols,
+az_status launch_colfwd_gather_v1(const Geom& g, const int32_t* pos2m, const TB* b, int64_t ldb, int ncols,
                                int pair0, int npairs, typename C2<T>::t* X1, const PassTabs& tb,
-                               cudaStream_t st) {
+                               cudaStream_t st, int64_t M_rows) {
   using V = typename C2<T>::t;
   int C = col_tile<V>(g.D0, g.D1);
   size_t sm = 2 * (size_t)g.D0 * C * sizeof(V);
   if (set_smem(k_colfwd_gather<T, TB>, sm) != cudaSuccess) { set_error("smem attribute"); return AZ_ERR_CUDA; }
   dim3 grid(g.D1 / C, npairs);
-  k_colfwd_gather<T, TB><<<grid, 256, sm, st>>>(g, pos2m, b, ldb, ncols, pair0, C, X1, tb);
+  ProfScope ps(sizeof(T) == 4 ? "colfwd_gather_f32" : "colfwd_gather_f64", (double)npairs * g.L * sizeof(V) + (double)std::min(ncols - 2 * pair0, 2 * npairs) * M_rows * sizeof(TB) + 4.0 * g.L, st);
+  k_colfwd_gather<T, TB><<<grid, 256, sm, st>>>(g, pos2m, b, ldb, ncols, pair0, ilog2i(C), X1, tb);
   AZ_LAUNCH_CHECK();
   return AZ_OK;
 }
@@ -372,7 +397,8 @@ az_status launch_colfwd_load(const Geom& g, const typename C2<T>::t* in, int npa
   size_t sm = 2 * (size_t)g.D0 * C * sizeof(V);
   if (set_smem(k_colfwd_load<T>, sm) != cudaSuccess) { set_error("smem attribute"); return AZ_ERR_CUDA; }
   dim3 grid(g.D1 / C, npairs);
-  k_colfwd_load<T><<<grid, 256, sm, st>>>(g, in, C, X1, tb);
+  ProfScope ps("colfwd_load", 2.0 * npairs * g.L * sizeof(V), st);
+  k_colfwd_load<T><<<grid, 256, sm, st>>>(g, in, ilog2i(C), X1, tb);
   AZ_LAUNCH_CHECK();
   return AZ_OK;
 }
@@ -389,21 +415,22 @@ template <typename V> static int row_groups_per_cta(const Geom& g) {
 }
 
 template <typename T>
-__global__ void k_rowfft(Geom g, const typename C2<T>::t* __restrict__ X1base, int GPB,
-                         typename C2<T>::t* X2base, PassTabs tb) {
+__global__ void __launch_bounds__(256) k_rowfft(Geom g, const typename C2<T>::t* __restrict__ X1base, int logGPB,
+                                                typename C2<T>::t* X2base, PassTabs tb) {
   using V = typename C2<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int GPB = 1 << logGPB;
   V* s0 = (V*)smem_raw;
   V* s1 = s0 + (size_t)GPB * g.D1;
   const V* X1 = X1base + (int64_t)blockIdx.y * g.L;
   V* X2 = X2base + (int64_t)blockIdx.y * g.L;
   const int r0 = blockIdx.x * GPB;
-  const int64_t total = (int64_t)GPB * g.D1;
-  for (int64_t t = threadIdx.x; t < total; t += blockDim.x) s0[t] = X1[(int64_t)r0 * g.D1 + t];
+  const int total = GPB << g.logD1;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) s0[t] = X1[(r0 << g.logD1) + t];
   __syncthreads();
-  int cur = fft_lines<V, false>(s0, s1, g.logD1, GPB, g.D1, 1, (const V*)tb.tw, TW_N >> g.logD1);
+  int cur = fft_lines<V, false>(s0, s1, g.logD1, logGPB, g.D1, 1, (const V*)tb.tw, TW_N >> g.logD1);
   V* res = cur ? s1 : s0;
-  for (int64_t t = threadIdx.x; t < total; t += blockDim.x) X2[(int64_t)r0 * g.D1 + t] = res[t];
+  for (int t = threadIdx.x; t < total; t += blockDim.x) X2[(r0 << g.logD1) + t] = res[t];
 }
 template <typename T>
 az_status launch_rowfft(const Geom& g, const typename C2<T>::t* X1, int npairs, typename C2<T>::t* X2,
@@ -415,7 +442,8 @@ az_status launch_rowfft(const Geom& g, const typename C2<T>::t* X1, int npairs, 
   size_t sm = 2 * (size_t)GPB * g.D1 * sizeof(V);
   if (set_smem(k_rowfft<T>, sm) != cudaSuccess) { set_error("smem attribute"); return AZ_ERR_CUDA; }
   dim3 grid(g.D0 / GPB, npairs);
-  k_rowfft<T><<<grid, 256, sm, st>>>(g, X1, GPB, X2, tb);
+  ProfScope ps("rowfft", 2.0 * npairs * g.L * sizeof(V), st);
+  k_rowfft<T><<<grid, 256, sm, st>>>(g, X1, ilog2i(GPB), X2, tb);
   AZ_LAUNCH_CHECK();
   return AZ_OK;
 }
@@ -424,39 +452,44 @@ az_status launch_rowfft(const Geom& g, const typename C2<T>::t* X1, int npairs, 
 // alias group with H = Ghat/S (Eq. B_pinv), inverse FFT of length N1, twiddle
 // (1D four-step), store on the N-grid layout X3[pair][G*N1 + n1].
 template <typename T>
-__global__ void k_rowfold(Geom g, const typename C2<T>::t* __restrict__ X1base, const T* __restrict__ H, int GPB,
-                          typename C2<T>::t* X3base, PassTabs tb) {
+__global__ void __launch_bounds__(256) k_rowfold(Geom g, const typename C2<T>::t* __restrict__ X1base,
+                                                 const T* __restrict__ H, int logGPB, typename C2<T>::t* X3base,
+                                                 PassTabs tb) {
   using V = typename C2<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int nrows = GPB * g.Rg;
+  const int GPB = 1 << logGPB;
+  const int lognr = logGPB + g.logRg;
+  const int nrows = 1 << lognr;
   V* s0 = (V*)smem_raw;
   V* s1 = s0 + (size_t)nrows * g.D1;
   const V* X1 = X1base + (int64_t)blockIdx.y * g.L;
   V* X3 = X3base + (int64_t)blockIdx.y * g.N;
   const int G0 = blockIdx.x * GPB;
+  const int D1m = g.D1 - 1, Rgm = g.Rg - 1, N1m = g.N1 - 1;
   // load rows: local row lr = gg*Rg + q  <->  global row (G0+gg) + q*Rstride
-  const int64_t total = (int64_t)nrows * g.D1;
-  for (int64_t t = threadIdx.x; t < total; t += blockDim.x) {
-    int lr = (int)(t / g.D1), i = (int)(t % g.D1);
-    int gg = lr / g.Rg, q = lr % g.Rg;
-    int64_t row = (int64_t)(G0 + gg) + (int64_t)q * g.Rstride;
-    s0[t] = X1[row * g.D1 + i];
+  const int total = nrows << g.logD1;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int lr = t >> g.logD1, i = t & D1m;
+    const int gg = lr >> g.logRg, q = lr & Rgm;
+    const int row = G0 + gg + q * g.Rstride;
+    s0[t] = X1[(row << g.logD1) + i];
   }
   __syncthreads();
-  int cur = fft_lines<V, false>(s0, s1, g.logD1, nrows, g.D1, 1, (const V*)tb.tw, TW_N >> g.logD1);
+  int cur = fft_lines<V, false>(s0, s1, g.logD1, lognr, g.D1, 1, (const V*)tb.tw, TW_N >> g.logD1);
   V* X = cur ? s1 : s0;
   V* F = cur ? s0 : s1;  // fold output lines [gg][N1]
-  const int64_t totF = (int64_t)GPB * g.N1;
-  for (int64_t t = threadIdx.x; t < totF; t += blockDim.x) {
-    int gg = (int)(t / g.N1), k1 = (int)(t % g.N1);
+  const int totF = GPB << g.logN1;
+  for (int t = threadIdx.x; t < totF; t += blockDim.x) {
+    const int gg = t >> g.logN1, k1 = t & N1m;
     T ar = 0, ai = 0;
     for (int q = 0; q < g.Rg; ++q) {
-      int64_t row = (int64_t)(G0 + gg) + (int64_t)q * g.Rstride;
-      const V* xr = X + (int64_t)(gg * g.Rg + q) * g.D1;
+      const int row = G0 + gg + q * g.Rstride;
+      const V* xr = X + ((gg * g.Rg + q) << g.logD1);
+      const T* hr = H + ((int64_t)row << g.logD1);
       for (int p = 0; p < g.Fq; ++p) {
-        int kk = k1 + p * g.N1;
-        T hh = __ldg(H + row * g.D1 + kk);
-        V xv = xr[kk];
+        const int kk = k1 + p * g.N1;
+        const T hh = __ldg(hr + kk);
+        const V xv = xr[kk];
         ar += hh * xv.x; ai += hh * xv.y;
       }
     }
@@ -464,68 +497,71 @@ __global__ void k_rowfold(Geom g, const typename C2<T>::t* __restrict__ X1base, 
     F[t] = o;
   }
   __syncthreads();
-  V* Fo = F;
-  V* Fs = X;
-  int c2 = fft_lines<V, true>(Fo, Fs, g.logN1, GPB, g.N1, 1, (const V*)tb.tw, TW_N >> g.logN1);
-  V* Z = c2 ? Fs : Fo;
-  for (int64_t t = threadIdx.x; t < totF; t += blockDim.x) {
-    int gg = (int)(t / g.N1), n1 = (int)(t % g.N1);
-    int k0 = G0 + gg;
+  int c2 = fft_lines<V, true>(F, X, g.logN1, logGPB, g.N1, 1, (const V*)tb.tw, TW_N >> g.logN1);
+  V* Z = c2 ? X : F;
+  for (int t = threadIdx.x; t < totF; t += blockDim.x) {
+    const int gg = t >> g.logN1, n1 = t & N1m;
+    const int k0 = G0 + gg;
     V v = Z[t];
-    if (g.dim == 1 && k0 != 0 && n1 != 0) v = cmul(v, big_tw<V>((const V*)tb.bigNA, (const V*)tb.bigNB, (int64_t)n1 * k0, true));
-    X3[(int64_t)k0 * g.N1 + n1] = v;
+    if (g.dim == 1 && k0 != 0 && n1 != 0) v = cmul(v, big_tw<V>((const V*)tb.bigNA, (const V*)tb.bigNB, n1 * k0, true));
+    X3[(k0 << g.logN1) + n1] = v;
   }
 }
 template <typename T>
-az_status launch_rowfold(const Geom& g, const typename C2<T>::t* X1, const T* H, int npairs,
+az_status launch_rowfold_v1(const Geom& g, const typename C2<T>::t* X1, const T* H, int npairs,
                          typename C2<T>::t* X3, const PassTabs& tb, cudaStream_t st) {
   using V = typename C2<T>::t;
   int GPB = row_groups_per_cta<V>(g);
   size_t sm = 2 * (size_t)GPB * g.Rg * g.D1 * sizeof(V);
   if (set_smem(k_rowfold<T>, sm) != cudaSuccess) { set_error("smem attribute"); return AZ_ERR_CUDA; }
   dim3 grid(g.G0 / GPB, npairs);
-  k_rowfold<T><<<grid, 256, sm, st>>>(g, X1, H, GPB, X3, tb);
+  ProfScope ps(sizeof(T) == 4 ? "rowfold_f32" : "rowfold_f64", (double)npairs * (g.L + g.N) * sizeof(V) + (double)g.L * sizeof(T), st);
+  k_rowfold<T><<<grid, 256, sm, st>>>(g, X1, H, ilog2i(GPB), X3, tb);
   AZ_LAUNCH_CHECK();
   return AZ_OK;
 }
 
 // ------------------------------------------------------------------ inverse column pass
 template <typename T, typename TO>
-__global__ void k_colinv(Geom g, const typename C2<T>::t* __restrict__ X3base, int pair0, int ncols, int C,
-                         TO* __restrict__ out, int64_t ldo, const uint32_t* __restrict__ bits, int64_t nw,
-                         PassTabs tb) {
+__global__ void __launch_bounds__(256) k_colinv(Geom g, const typename C2<T>::t* __restrict__ X3base, int pair0,
+                                                int ncols, int logC, TO* __restrict__ out, int64_t ldo,
+                                                const uint32_t* __restrict__ bits, int64_t nw, PassTabs tb) {
   using V = typename C2<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int C = 1 << logC, Cm = C - 1;
   V* s0 = (V*)smem_raw;
   V* s1 = s0 + (size_t)g.G0 * C;
   const int c0 = blockIdx.x * C;
   const V* X3 = X3base + (int64_t)blockIdx.y * g.N;
   const int pair = pair0 + blockIdx.y;
   const int colA = 2 * pair, colB = 2 * pair + 1;
-  const int64_t total = (int64_t)g.G0 * C;
-  for (int64_t t = threadIdx.x; t < total; t += blockDim.x) {
-    int c = (int)(t % C), k0 = (int)(t / C);
-    s0[t] = X3[(int64_t)k0 * g.N1 + c0 + c];
+  const bool hasB = colB < ncols;
+  TO* oA = out + (int64_t)colA * ldo;
+  TO* oB = out + (int64_t)colB * ldo;
+  const int total = g.G0 << logC;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int c = t & Cm, k0 = t >> logC;
+    s0[t] = X3[(k0 << g.logN1) + c0 + c];
   }
   __syncthreads();
-  int cur = fft_lines<V, true>(s0, s1, g.logG0, C, 1, C, (const V*)tb.tw, TW_N >> g.logG0);
+  int cur = fft_lines<V, true>(s0, s1, g.logG0, logC, 1, C, (const V*)tb.tw, TW_N >> g.logG0);
   V* res = cur ? s1 : s0;
   const T sc = (T)(1.0 / (double)g.N);
-  for (int64_t t = threadIdx.x; t < total; t += blockDim.x) {
-    int c = (int)(t % C), n0 = (int)(t / C);
-    int64_t j = (int64_t)n0 * g.N1 + c0 + c;
-    V v = res[t];
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int c = t & Cm, n0 = t >> logC;
+    const int j = (n0 << g.logN1) + c0 + c;
+    const V v = res[t];
     T za = v.x * sc, zb = v.y * sc;
     if (bits) {
       za = (T)rad_bit(bits, nw, j, colA) - za;
-      if (colB < ncols) zb = (T)rad_bit(bits, nw, j, colB) - zb;
+      if (hasB) zb = (T)rad_bit(bits, nw, j, colB) - zb;
     }
-    out[(int64_t)colA * ldo + j] = (TO)za;
-    if (colB < ncols) out[(int64_t)colB * ldo + j] = (TO)zb;
+    oA[j] = (TO)za;
+    if (hasB) oB[j] = (TO)zb;
   }
 }
 template <typename T, typename TO>
-az_status launch_colinv(const Geom& g, const typename C2<T>::t* X3, int pair0, int npairs, int ncols,
+az_status launch_colinv_v1(const Geom& g, const typename C2<T>::t* X3, int pair0, int npairs, int ncols,
                         TO* out, int64_t ldo, const uint32_t* bits, int64_t nw, const PassTabs& tb,
                         cudaStream_t st) {
   using V = typename C2<T>::t;
@@ -533,70 +569,189 @@ az_status launch_colinv(const Geom& g, const typename C2<T>::t* X3, int pair0, i
   size_t sm = 2 * (size_t)g.G0 * C * sizeof(V);
   if (set_smem(k_colinv<T, TO>, sm) != cudaSuccess) { set_error("smem attribute"); return AZ_ERR_CUDA; }
   dim3 grid(g.N1 / C, npairs);
-  k_colinv<T, TO><<<grid, 256, sm, st>>>(g, X3, pair0, ncols, C, out, ldo, bits, nw, tb);
+  ProfScope ps(sizeof(T) == 4 ? "colinv_f32" : "colinv_f64", (double)npairs * g.N * sizeof(V) + (double)std::min(ncols - 2 * pair0, 2 * npairs) * g.N * sizeof(TO), st);
+  k_colinv<T, TO><<<grid, 256, sm, st>>>(g, X3, pair0, ncols, ilog2i(C), out, ldo, bits, nw, tb);
   AZ_LAUNCH_CHECK();
   return AZ_OK;
 }
 
 // ------------------------------------------------------------------ stencils
-template <typename T, typename TZ>
-__device__ __forceinline__ T stencil_1d(const Geom& g, const T* __restrict__ tp, int W, int64_t i,
-                                        const TZ* __restrict__ z) {
-  const int s = g.s[0];
-  int64_t jlo = fdiv(i - W + s - 1, s), jhi = fdiv(i + W, s);
-  T acc = 0;
-  for (int64_t j = jlo; j <= jhi; ++j) acc += __ldg(tp + (i - s * j + W)) * (T)z[fmod_pos(j, g.N)];
-  return acc;
-}
-
-template <typename T, typename TZ, typename TB, typename TO>
-__global__ void k_stencil_rows(Geom g, int kind, T inv2e2, const int32_t* __restrict__ idx, int64_t M,
-                               const T* __restrict__ x0, const T* __restrict__ x2, const T* __restrict__ y0,
-                               const T* __restrict__ y2, int Wx, int Wy, const TZ* __restrict__ zb, int64_t ldz,
-                               const TB* __restrict__ bb, int64_t ldb, T alpha, T beta, TO* __restrict__ outb,
-                               int64_t ldo) {
-  int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// Rows of A at the kept grid points: out[m, c] = alpha*b[m, c] + beta*(A z)[m, c].
+// One thread per kept point m and a group of CPT columns (index arithmetic and
+// taps shared across the group).
+template <typename T, typename TZ, typename TB, typename TO, int CPT>
+__global__ void __launch_bounds__(256) k_stencil_rows(Geom g, int kind, T inv2e2, const int32_t* __restrict__ idx, int M,
+                                                      const T* __restrict__ x0, const T* __restrict__ x2,
+                                                      const T* __restrict__ y0, const T* __restrict__ y2, int Wx, int Wy,
+                                                      const TZ* __restrict__ zb, int64_t ldz, const TB* __restrict__ bb,
+                                                      int64_t ldb, T alpha, T beta, TO* __restrict__ outb, int64_t ldo,
+                                                      int ncols) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= M) return;
-  const int c = blockIdx.y;
-  const TZ* z = zb + (int64_t)c * ldz;
-  const int64_t i = idx[m];
-  T az;
+  const int cbase = blockIdx.y * CPT;
+  const int nc = min(CPT, ncols - cbase);
+  const int i = __ldg(idx + m);
+  T acc[CPT];
+#pragma unroll
+  for (int c = 0; c < CPT; ++c) acc[c] = 0;
   if (g.dim == 1) {
-    az = stencil_1d<T, TZ>(g, x0, Wx, i, z);
+    const int ls = g.logs[0], s = g.s[0], Nm = (int)g.N - 1;
+    const int jlo = cdiv_p2(i - Wx, ls), jhi = fdiv_p2(i + Wx, ls);
+    for (int j = jlo; j <= jhi; ++j) {
+      const T tap = __ldg(x0 + (i - s * j + Wx));
+      const int jj = j & Nm;
+#pragma unroll
+      for (int c = 0; c < CPT; ++c)
+        if (c < nc) acc[c] += tap * (T)__ldg(zb + (int64_t)(cbase + c) * ldz + jj);
+    }
   } else {
     const int sx = g.s[0], sy = g.s[1];
-    const int64_t Nx = g.n[0], Ny = g.n[1];
-    const int64_t ix = i / g.D1, iy = i % g.D1;
-    int64_t xlo = fdiv(ix - Wx + sx - 1, sx), xhi = fdiv(ix + Wx, sx);
-    int64_t ylo = fdiv(iy - Wy + sy - 1, sy), yhi = fdiv(iy + Wy, sy);
-    T acc = 0;
-    for (int64_t jx = xlo; jx <= xhi; ++jx) {
-      const TZ* zr = z + fmod_pos(jx, Nx) * Ny;
-      T a0 = 0, a2 = 0;
-      for (int64_t jy = ylo; jy <= yhi; ++jy) {
-        T zv = (T)zr[fmod_pos(jy, Ny)];
-        a0 += __ldg(y0 + (iy - sy * jy + Wy)) * zv;
-        if (kind == 1) a2 += __ldg(y2 + (iy - sy * jy + Wy)) * zv;
+    const int Nxm = (int)g.n[0] - 1, Nym = (int)g.n[1] - 1, lNy = g.logn[1];
+    const int ix = i >> g.logD1, iy = i & (g.D1 - 1);
+    const int xlo = cdiv_p2(ix - Wx, g.logs[0]), xhi = fdiv_p2(ix + Wx, g.logs[0]);
+    const int ylo = cdiv_p2(iy - Wy, g.logs[1]), yhi = fdiv_p2(iy + Wy, g.logs[1]);
+    for (int jx = xlo; jx <= xhi; ++jx) {
+      const int rowoff = (jx & Nxm) << lNy;
+      const T tx0 = __ldg(x0 + (ix - sx * jx + Wx));
+      const T tx2 = kind == 1 ? __ldg(x2 + (ix - sx * jx + Wx)) : (T)0;
+      for (int jy = ylo; jy <= yhi; ++jy) {
+        const T ty0 = __ldg(y0 + (iy - sy * jy + Wy));
+        T w = tx0 * ty0;
+        if (kind == 1) w = -(tx2 * ty0 + tx0 * __ldg(y2 + (iy - sy * jy + Wy))) * inv2e2;
+        const int jj = rowoff + (jy & Nym);
+#pragma unroll
+        for (int c = 0; c < CPT; ++c)
+          if (c < nc) acc[c] += w * (T)__ldg(zb + (int64_t)(cbase + c) * ldz + jj);
       }
-      T tx0 = __ldg(x0 + (ix - sx * jx + Wx));
-      if (kind == 1) acc += __ldg(x2 + (ix - sx * jx + Wx)) * a0 + tx0 * a2;
-      else acc += tx0 * a0;
     }
-    az = kind == 1 ? -acc * inv2e2 : acc;
   }
-  T r = beta * az;
-  if (bb) r += alpha * (T)bb[(int64_t)c * ldb + m];
-  outb[(int64_t)c * ldo + m] = (TO)r;
+#pragma unroll
+  for (int c = 0; c < CPT; ++c) {
+    if (c < nc) {
+      T r = beta * acc[c];
+      if (bb) r += alpha * (T)bb[(int64_t)(cbase + c) * ldb + m];
+      outb[(int64_t)(cbase + c) * ldo + m] = (TO)r;
+    }
+  }
 }
 template <typename T, typename TZ, typename TB, typename TO>
 az_status launch_stencil_rows(const Geom& g, int kind, double eps, const int32_t* idx, int64_t M,
                               const StencilTaps& tp, const TZ* z, int64_t ldz, const TB* b, int64_t ldb,
                               T alpha, T beta, TO* out, int64_t ldo, int ncols, cudaStream_t st) {
   if (M == 0 || ncols == 0) return AZ_OK;
-  dim3 grid((unsigned)((M + 255) / 256), ncols);
-  k_stencil_rows<T, TZ, TB, TO><<<grid, 256, 0, st>>>(g, kind, (T)(1.0 / (2.0 * eps * eps)), idx, M, (const T*)tp.x0,
-                                                      (const T*)tp.x2, (const T*)tp.y0, (const T*)tp.y2, tp.Wx,
-                                                      tp.Wy, z, ldz, b, ldb, alpha, beta, out, ldo);
+  constexpr int CPT = 4;
+  dim3 grid((unsigned)((M + 255) / 256), (ncols + CPT - 1) / CPT);
+  ProfScope ps(sizeof(T) == 4 ? "stencil_rows_f32" : "stencil_rows_f64", (double)g.N * ncols * sizeof(TZ) + (double)M * ncols * ((b ? sizeof(TB) : 0) + sizeof(TO)) + 4.0 * M, st);
+  k_stencil_rows<T, TZ, TB, TO, CPT><<<grid, 256, 0, st>>>(g, kind, (T)(1.0 / (2.0 * eps * eps)), idx, (int)M, (const T*)tp.x0,
+                                                           (const T*)tp.x2, (const T*)tp.y0, (const T*)tp.y2, tp.Wx,
+                                                           tp.Wy, z, ldz, b, ldb, alpha, beta, out, ldo, ncols);
+  AZ_LAUNCH_CHECK();
+  return AZ_OK;
+}
+
+// FP64-accurate residual rows r = b - A x in double-FP32 arithmetic, for
+// coefficients x that are exactly representable in FP32 (the mixed path's
+// first-pass solution is formed in FP32).  Each FP64 tap is split into FP32
+// hi + lo; tap*x = hi*x (exact: product + fma error) + lo*x, accumulated with
+// two-sum; the ~48-bit sum is subtracted from b in FP64.
+struct DFa { float hi, lo; };
+__device__ __forceinline__ void dfa_add(DFa& s, float x, float th, float tl) {
+  const float p = th * x;
+  const float e = fmaf(th, x, -p);
+  const float t = s.hi + p;
+  const float bb = t - s.hi;
+  const float err = (s.hi - (t - bb)) + (p - bb);
+  s.hi = t;
+  s.lo += err + fmaf(tl, x, e);
+}
+// (ah + al) * (bh + bl) as a double-float (hi exact product + cross terms)
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float& ph, float& pl) {
+  ph = ah * bh;
+  pl = fmaf(ah, bh, -ph) + fmaf(ah, bl, al * bh);
+}
+template <int CPT>
+__global__ void __launch_bounds__(256) k_resid_df(Geom g, int kind, double inv2e2, const int32_t* __restrict__ idx, int M,
+                                                  const float* __restrict__ x0h, const float* __restrict__ x0l,
+                                                  const float* __restrict__ x2h, const float* __restrict__ x2l,
+                                                  const float* __restrict__ y0h, const float* __restrict__ y0l,
+                                                  const float* __restrict__ y2h, const float* __restrict__ y2l,
+                                                  int Wx, int Wy, const float* __restrict__ xf, int64_t ldx,
+                                                  const double* __restrict__ bb, int64_t ldb, float* __restrict__ out,
+                                                  int64_t ldo, int ncols) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  const int cbase = blockIdx.y * CPT;
+  const int nc = min(CPT, ncols - cbase);
+  const int i = __ldg(idx + m);
+  DFa acc[CPT];
+#pragma unroll
+  for (int c = 0; c < CPT; ++c) { acc[c].hi = 0.f; acc[c].lo = 0.f; }
+  if (g.dim == 1) {
+    const int ls = g.logs[0], s = g.s[0], Nm = (int)g.N - 1;
+    const int jlo = cdiv_p2(i - Wx, ls), jhi = fdiv_p2(i + Wx, ls);
+    for (int j = jlo; j <= jhi; ++j) {
+      const int ti = i - s * j + Wx;
+      const float th = __ldg(x0h + ti), tl = __ldg(x0l + ti);
+      const int jj = j & Nm;
+#pragma unroll
+      for (int c = 0; c < CPT; ++c)
+        if (c < nc) dfa_add(acc[c], __ldg(xf + (int64_t)(cbase + c) * ldx + jj), th, tl);
+    }
+  } else {
+    const int sx = g.s[0], sy = g.s[1];
+    const int Nxm = (int)g.n[0] - 1, Nym = (int)g.n[1] - 1, lNy = g.logn[1];
+    const int ix = i >> g.logD1, iy = i & (g.D1 - 1);
+    const int xlo = cdiv_p2(ix - Wx, g.logs[0]), xhi = fdiv_p2(ix + Wx, g.logs[0]);
+    const int ylo = cdiv_p2(iy - Wy, g.logs[1]), yhi = fdiv_p2(iy + Wy, g.logs[1]);
+    for (int jx = xlo; jx <= xhi; ++jx) {
+      const int rowoff = (jx & Nxm) << lNy;
+      const int tx = ix - sx * jx + Wx;
+      const float ah = __ldg(x0h + tx), al = __ldg(x0l + tx);
+      const float a2h = kind == 1 ? __ldg(x2h + tx) : 0.f, a2l = kind == 1 ? __ldg(x2l + tx) : 0.f;
+      for (int jy = ylo; jy <= yhi; ++jy) {
+        const int ty = iy - sy * jy + Wy;
+        const float bh = __ldg(y0h + ty), bl = __ldg(y0l + ty);
+        float wh, wl;
+        df_mul(ah, al, bh, bl, wh, wl);
+        if (kind == 1) {
+          float uh, ul, vh, vl;
+          df_mul(a2h, a2l, bh, bl, uh, ul);
+          df_mul(ah, al, __ldg(y2h + ty), __ldg(y2l + ty), vh, vl);
+          // w = -(u + v) * inv2e2 (FP64 scalar applied after the sum below)
+          const float sh = uh + vh;
+          const float bz = sh - uh;
+          const float se = (uh - (sh - bz)) + (vh - bz) + ul + vl;
+          wh = sh; wl = se;
+        }
+        const int jj = rowoff + (jy & Nym);
+#pragma unroll
+        for (int c = 0; c < CPT; ++c)
+          if (c < nc) dfa_add(acc[c], __ldg(xf + (int64_t)(cbase + c) * ldx + jj), wh, wl);
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < CPT; ++c) {
+    if (c < nc) {
+      double ax = (double)acc[c].hi + (double)acc[c].lo;
+      if (g.dim == 2 && kind == 1) ax = -ax * inv2e2;
+      out[(int64_t)(cbase + c) * ldo + m] = (float)(bb[(int64_t)(cbase + c) * ldb + m] - ax);
+    }
+  }
+}
+az_status launch_resid_df(const Geom& g, int kind, double eps, const int32_t* idx, int64_t M, const float* const th[4],
+                          const float* const tl[4], int Wx, int Wy, const float* xf, int64_t ldx, const double* b,
+                          int64_t ldb, float* out, int64_t ldo, int ncols, cudaStream_t st) {
+  if (M == 0 || ncols == 0) return AZ_OK;
+  constexpr int CPT = 4;
+  dim3 grid((unsigned)((M + 255) / 256), (ncols + CPT - 1) / CPT);
+  ProfScope ps("resid_df", (double)g.N * ncols * 4 + (double)M * ncols * (8 + 4) + 4.0 * M, st);
+  const float* y0h = g.dim == 1 ? th[0] : th[1];
+  const float* y0l = g.dim == 1 ? tl[0] : tl[1];
+  const float* y2h = g.dim == 1 ? th[2] : th[3];
+  const float* y2l = g.dim == 1 ? tl[2] : tl[3];
+  k_resid_df<CPT><<<grid, 256, 0, st>>>(g, kind, 1.0 / (2.0 * eps * eps), idx, (int)M, th[0], tl[0], th[2], tl[2], y0h, y0l,
+                                        y2h, y2l, Wx, g.dim == 1 ? Wx : Wy, xf, ldx, b, ldb, out, ldo, ncols);
   AZ_LAUNCH_CHECK();
   return AZ_OK;
 }
@@ -642,6 +797,7 @@ az_status launch_boundary_rows(const Geom& g, double eps, double w, const double
                                TO* out, int64_t ldo, int ncols, cudaStream_t st) {
   if (Mb == 0 || ncols == 0) return AZ_OK;
   dim3 grid((unsigned)((Mb + 127) / 128), ncols);
+  ProfScope ps("boundary_rows", (double)Mb * ncols * ((b ? sizeof(TB) : 0) + sizeof(TO)) + 16.0 * Mb, st);
   k_boundary_rows<T, TZ, TB, TO><<<grid, 128, 0, st>>>(g, (T)eps, (T)w, center_window(g, eps), pts, Mb, z, ldz, b,
                                                        ldb, alpha, beta, out, ldo);
   AZ_LAUNCH_CHECK();
@@ -689,6 +845,7 @@ az_status launch_evaluate(const Geom& g, double eps, int s_test, const double* x
     Wc = (int)std::max<int64_t>(0, std::min<int64_t>(Wc, lim));
   }
   dim3 grid((unsigned)((npts + 255) / 256), nrhs);
+  ProfScope ps("evaluate", 8.0 * npts * nrhs + 8.0 * g.N * nrhs, st);
   k_evaluate<<<grid, 256, 0, st>>>(g, eps, s_test, Wc, x, ldx, out, ldo, npts);
   AZ_LAUNCH_CHECK();
   return AZ_OK;
@@ -706,6 +863,7 @@ __global__ void k_symbol_full(Geom g, int kind, double inv2e2, const double* G0x
 }
 az_status launch_symbol_full(const Geom& g, int kind, double eps, const double* G0x, const double* G0y,
                              const double* G2x, const double* G2y, double* Ghat, cudaStream_t st) {
+  ProfScope ps("symbol", 8.0 * g.L, st);
   k_symbol_full<<<(unsigned)((g.L + 255) / 256), 256, 0, st>>>(g, kind, 1.0 / (2.0 * eps * eps), G0x, G0y, G2x, G2y, Ghat);
   AZ_LAUNCH_CHECK();
   return AZ_OK;
@@ -724,6 +882,7 @@ __global__ void k_fold_S(Geom g, const double* __restrict__ Gh, double* __restri
   S[k] = acc;
 }
 az_status launch_fold_S(const Geom& g, const double* Ghat, double* S, cudaStream_t st) {
+  ProfScope ps("symbol", 8.0 * (g.L + g.N), st);
   k_fold_S<<<(unsigned)((g.N + 255) / 256), 256, 0, st>>>(g, Ghat, S);
   AZ_LAUNCH_CHECK();
   return AZ_OK;
@@ -744,6 +903,7 @@ __global__ void k_H(Geom g, const double* __restrict__ Gh, const double* __restr
 az_status launch_H(const Geom& g, const double* Ghat, const double* S, double thr, double* H64, float* H32,
                    cudaStream_t st) {
   // thr: relative threshold tau_sym^2; the max of S is expected in H64 scratch? no: S max stored at S[g.N]
+  ProfScope ps("symbol", 8.0 * (2 * g.L + g.N) + 4.0 * g.L, st);
   k_H<<<(unsigned)((g.L + 255) / 256), 256, 0, st>>>(g, Ghat, S, S + g.N, thr, H64, H32);
   AZ_LAUNCH_CHECK();
   return AZ_OK;
@@ -762,6 +922,7 @@ __global__ void k_max_abs(const double* v, int64_t n, double* out) {
   }
 }
 az_status launch_max_abs(const double* v, int64_t n, double* out, cudaStream_t st) {
+  ProfScope ps("symbol", 8.0 * n, st);
   k_max_abs<<<1, 1024, 0, st>>>(v, n, out);
   AZ_LAUNCH_CHECK();
   return AZ_OK;
@@ -773,6 +934,7 @@ __global__ void k_spec_to_natural(Geom g, const double2* X, double* out) {
   out[k0 + (int64_t)g.D0 * k1] = X[t].x;
 }
 az_status launch_spec_to_natural(const Geom& g, const double2* X, double* out, cudaStream_t st) {
+  ProfScope ps("symbol", 24.0 * g.L, st);
   k_spec_to_natural<<<(unsigned)((g.L + 255) / 256), 256, 0, st>>>(g, X, out);
   AZ_LAUNCH_CHECK();
   return AZ_OK;
@@ -784,7 +946,7 @@ __global__ void k_line_dft_real(const double* in, int logn, double* out, const d
   double2* s1 = s0 + n;
   for (int i = threadIdx.x; i < n; i += blockDim.x) s0[i] = make_double2(in[i], 0.0);
   __syncthreads();
-  int cur = fft_lines<double2, false>(s0, s1, logn, 1, n, 1, tw, TW_N >> logn);
+  int cur = fft_lines<double2, false>(s0, s1, logn, 0, n, 1, tw, TW_N >> logn);
   double2* r = cur ? s1 : s0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) out[i] = r[i].x;
 }
@@ -793,6 +955,7 @@ az_status launch_line_dft_real(const double* in, int n, double* out, const doubl
   while ((1 << logn) < n) ++logn;
   size_t sm = 2 * (size_t)n * sizeof(double2);
   if (set_smem(k_line_dft_real, sm) != cudaSuccess) { set_error("smem attribute"); return AZ_ERR_CUDA; }
+  ProfScope ps("symbol", 16.0 * n, st);
   k_line_dft_real<<<1, 256, sm, st>>>(in, logn, out, tw);
   AZ_LAUNCH_CHECK();
   return AZ_OK;
@@ -809,6 +972,7 @@ az_status launch_scale_rows(const double* in, int64_t ldi, int64_t rows, int nco
                             int64_t ldo, cudaStream_t st) {
   if (rows == 0 || ncols == 0) return AZ_OK;
   dim3 grid((unsigned)((rows + 255) / 256), ncols);
+  ProfScope ps("scale_rows", 16.0 * rows * ncols, st);
   k_scale_rows<<<grid, 256, 0, st>>>(in, ldi, rows, sc, out, ldo);
   AZ_LAUNCH_CHECK();
   return AZ_OK;
@@ -829,31 +993,333 @@ __global__ void k_sumsq_cols(const double* v, int64_t ld, int64_t rows, double* 
 }
 az_status launch_sumsq_cols(const double* v, int64_t ld, int64_t rows, int ncols, double* out, cudaStream_t st) {
   if (ncols == 0) return AZ_OK;
+  ProfScope ps("sumsq", 8.0 * rows * ncols, st);
   k_sumsq_cols<<<ncols, 1024, 0, st>>>(v, ld, rows, out);
   AZ_LAUNCH_CHECK();
   return AZ_OK;
 }
 
-// ------------------------------------------------------------------ explicit instantiations
-#define INST_T(T)                                                                                           \
+// ================================================================== register-resident passes
+// Same three passes as above, with the FFT held in registers (E values per
+// thread) and one padded shared buffer; used whenever every FFT length of the
+// pass is >= E.  E = 16 (FP32) or 8 (FP64).
+template <typename T> struct EPT { static constexpr int E = sizeof(T) == 4 ? 16 : 8; };
+// CTA size of the register passes: 256 threads and 3 CTAs per SM (80
+// registers) keep the load, compute and store phases of different CTAs
+// overlapped without spilling the 16 values a thread holds.
+#define REG_THREADS 256
+#define REG_MINB 3
+
+template <typename T, int MODE, typename TB>
+__global__ void __launch_bounds__(REG_THREADS, REG_MINB) k_colfwd_r(Geom g, const int32_t* __restrict__ pos2m, const TB* __restrict__ b,
+                                                  int64_t ldb, int ncols, SketchIn<T> in, int pair0, int logC,
+                                                  typename C2<T>::t* X1base, PassTabs tb) {
+  // MODE 0: gather b (E b on the grid); MODE 1: sketch stencil A^c R with the mask
+  using V = typename C2<T>::t;
+  constexpr int E = EPT<T>::E;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* sm = (V*)smem_raw;
+  const int C = 1 << logC;
+  const int line = threadIdx.x & (C - 1), tl = threadIdx.x >> logC;
+  const int c0 = blockIdx.x * C;
+  const int n1 = c0 + line;
+  const int pair = pair0 + blockIdx.y;
+  const int colA = 2 * pair, colB = 2 * pair + 1;
+  V* X1 = X1base + (int64_t)blockIdx.y * g.L;
+  const V* twp = (const V*)tb.tw;
+  // 2D sketch: y-stencil of R into a staging region after the FFT buffer
+  V* stg = sm + padix<5>(g.D0 << logC) + 32;
+  if (MODE == 1 && g.dim == 2) {
+    const int sy = g.s[1];
+    const int Nym = (int)g.n[1] - 1, lNy = g.logn[1];
+    const int tot1 = (int)g.n[0] << logC;
+    const bool hasB = colB < in.k;
+    for (int t = threadIdx.x; t < tot1; t += blockDim.x) {
+      const int c = t & (C - 1), jx = t >> logC;
+      const int iy = c0 + c;
+      const int jlo = cdiv_p2(iy - in.Wy, g.logs[1]), jhi = fdiv_p2(iy + in.Wy, g.logs[1]);
+      T re = 0, im = 0;
+      for (int jy = jlo; jy <= jhi; ++jy) {
+        const T tap = __ldg(in.tapy + (iy - sy * jy + in.Wy));
+        const int j = (jx << lNy) + (jy & Nym);
+        re += tap * (T)rad_bit(in.bits, in.nw, j, colA);
+        if (hasB) im += tap * (T)rad_bit(in.bits, in.nw, j, colB);
+      }
+      V v; v.x = re; v.y = im;
+      stg[t] = v;
+    }
+    __syncthreads();
+  }
+  if (MODE == 1) {
+    // sketch: v = mask * A^c R at every tile point, staged into the FFT
+    // buffer (keeps the stencil out of the unrolled first stage)
+    const int tot = g.D0 << logC;
+    const bool hasB = colB < in.k;
+    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+      const int c = t & (C - 1), p = t >> logC;
+      const int pos = (p << g.logD1) + c0 + c;
+      V v; v.x = 0; v.y = 0;
+      if (__ldg(pos2m + pos) >= 0) {
+        if (g.dim == 1) {
+          const int ls = g.logs[0], s = g.s[0], Nm = (int)g.N - 1, W = in.Wx;
+          const int jlo = cdiv_p2(pos - W, ls), jhi = fdiv_p2(pos + W, ls);
+          for (int j = jlo; j <= jhi; ++j) {
+            const T tap = __ldg(in.tapx + (pos - s * j + W));
+            const int jj = j & Nm;
+            v.x += tap * (T)rad_bit(in.bits, in.nw, jj, colA);
+            if (hasB) v.y += tap * (T)rad_bit(in.bits, in.nw, jj, colB);
+          }
+        } else {
+          const int sx = g.s[0], Nxm = (int)g.n[0] - 1;
+          const int jlo = cdiv_p2(p - in.Wx, g.logs[0]), jhi = fdiv_p2(p + in.Wx, g.logs[0]);
+          for (int jx = jlo; jx <= jhi; ++jx) {
+            const T tap = __ldg(in.tapx + (p - sx * jx + in.Wx));
+            const V u = stg[((jx & Nxm) << logC) + c];
+            v.x += tap * u.x; v.y += tap * u.y;
+          }
+        }
+      }
+      sm[padix<5>(t)] = v;
+    }
+    __syncthreads();
+  }
+  const TB* bA = b ? b + (int64_t)colA * ldb : nullptr;
+  const TB* bB = b ? b + (int64_t)colB * ldb : nullptr;
+  auto pro = [&](int p) -> V {
+    if (MODE == 1) return sm[padix<5>((p << logC) + line)];
+    const int pos = (p << g.logD1) + n1;
+    V v; v.x = 0; v.y = 0;
+    const int m = __ldg(pos2m + pos);
+    if (m < 0) return v;
+    v.x = (T)bA[m];
+    if (colB < ncols) v.y = (T)bB[m];
+    return v;
+  };
+  auto epi = [&](int k0, V v) {
+    if (g.dim == 1 && k0 != 0 && n1 != 0) v = cmul(v, big_tw<V>((const V*)tb.bigA, (const V*)tb.bigB, n1 * k0, false));
+    X1[(k0 << g.logD1) + n1] = v;
+  };
+  fft_reg<V, E, false, 5>(sm, g.logD0, true, line, tl, 1, C, twp, TW_N >> g.logD0, pro, epi, MODE == 1);
+}
+
+template <typename T, int E2>
+__global__ void __launch_bounds__(REG_THREADS, REG_MINB) k_rowfold_r(Geom g, const typename C2<T>::t* __restrict__ X1base,
+                                                   const T* __restrict__ H, int logGPB, typename C2<T>::t* X3base,
+                                                   PassTabs tb) {
+  using V = typename C2<T>::t;
+  constexpr int E = EPT<T>::E;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int GPB = 1 << logGPB;
+  const int lognr = logGPB + g.logRg;
+  V* smX = (V*)smem_raw;                                       // nrows x D1 (padded)
+  V* smF = smX + padix<4>(g.D1 << lognr) + 16;                // GPB x N1 (padded)
+  const V* X1 = X1base + (int64_t)blockIdx.y * g.L;
+  V* X3 = X3base + (int64_t)blockIdx.y * g.N;
+  const int G0 = blockIdx.x * GPB;
+  const V* twp = (const V*)tb.tw;
+  // forward FFT of the rows: P1 = D1/E threads per row
+  {
+    const int logP1 = g.logD1 - (E == 16 ? 4 : 3);
+    const int lr = threadIdx.x >> logP1, tl = threadIdx.x & ((1 << logP1) - 1);
+    const int gg = lr >> g.logRg, q = lr & (g.Rg - 1);
+    const int row = G0 + gg + q * g.Rstride;
+    const V* xr = X1 + ((int64_t)row << g.logD1);
+    auto pro = [&](int p) -> V { return xr[p]; };
+    auto epi = [&](int o, V v) { smX[padix<4>((lr << g.logD1) + o)] = v; };
+    fft_reg<V, E, false, 4>(smX, g.logD1, true, lr, tl, g.D1, 1, twp, TW_N >> g.logD1, pro, epi);
+  }
+  __syncthreads();
+  // fold (prologue of the inverse FFT of length N1, P2 = N1/E2 threads per line)
+  {
+    constexpr int LOGE2 = E2 == 16 ? 4 : (E2 == 8 ? 3 : (E2 == 4 ? 2 : 1));
+    const int logP2 = g.logN1 - LOGE2;
+    const int gg = threadIdx.x >> logP2, tl = threadIdx.x & ((1 << logP2) - 1);
+    const int k0 = G0 + gg;
+    auto pro = [&](int k1) -> V {
+      T ar = 0, ai = 0;
+      for (int q = 0; q < g.Rg; ++q) {
+        const int row = k0 + q * g.Rstride;
+        const int lr = gg * g.Rg + q;
+        const T* hr = H + ((int64_t)row << g.logD1);
+        for (int p = 0; p < g.Fq; ++p) {
+          const int kk = k1 + p * g.N1;
+          const T hh = __ldg(hr + kk);
+          const V xv = smX[padix<4>((lr << g.logD1) + kk)];
+          ar += hh * xv.x; ai += hh * xv.y;
+        }
+      }
+      V o; o.x = ar; o.y = ai;
+      return o;
+    };
+    auto epi = [&](int n1, V v) {
+      if (g.dim == 1 && k0 != 0 && n1 != 0) v = cmul(v, big_tw<V>((const V*)tb.bigNA, (const V*)tb.bigNB, n1 * k0, true));
+      X3[(k0 << g.logN1) + n1] = v;
+    };
+    fft_reg<V, E2, true, 4>(smF, g.logN1, true, gg, tl, g.N1, 1, twp, TW_N >> g.logN1, pro, epi);
+  }
+}
+
+template <typename T, typename TO, bool WMODE>
+__global__ void __launch_bounds__(REG_THREADS, REG_MINB) k_colinv_r(Geom g, const typename C2<T>::t* __restrict__ X3base, int pair0,
+                                                  int ncols, int logC, TO* __restrict__ out, int64_t ldo,
+                                                  const uint32_t* __restrict__ bits, int64_t nw, PassTabs tb) {
+  using V = typename C2<T>::t;
+  constexpr int E = EPT<T>::E;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* sm = (V*)smem_raw;
+  const int C = 1 << logC;
+  const int line = threadIdx.x & (C - 1), tl = threadIdx.x >> logC;
+  const int c0 = blockIdx.x * C;
+  const int n1 = c0 + line;
+  const V* X3 = X3base + (int64_t)blockIdx.y * g.N;
+  const int pair = pair0 + blockIdx.y;
+  const int colA = 2 * pair, colB = 2 * pair + 1;
+  const bool hasB = colB < ncols;
+  TO* oA = out + (int64_t)colA * ldo;
+  TO* oB = out + (int64_t)colB * ldo;
+  const T sc = (T)(1.0 / (double)g.N);
+  auto pro = [&](int k0) -> V { return X3[(k0 << g.logN1) + n1]; };
+  auto epi = [&](int n0, V v) {
+    const int j = (n0 << g.logN1) + n1;
+    T za = v.x * sc, zb = v.y * sc;
+    if (WMODE) {
+      za = (T)rad_bit(bits, nw, j, colA) - za;
+      if (hasB) zb = (T)rad_bit(bits, nw, j, colB) - zb;
+    }
+    oA[j] = (TO)za;
+    if (hasB) oB[j] = (TO)zb;
+  };
+  fft_reg<V, E, true, 5>(sm, g.logG0, true, line, tl, 1, C, (const V*)tb.tw, TW_N >> g.logG0, pro, epi);
+}
+
+// Column count per CTA for the register passes: C * (n / E) threads <= 512.
+template <typename T> static int reg_cols(int n, int ncols) {
+  const int P = n / EPT<T>::E;
+  int C = std::max(1, REG_THREADS / P);
+  C = std::min(C, 16);
+  int p = 1;
+  while (p * 2 <= C) p *= 2;
+  return std::min(p, ncols);
+}
+template <typename T> static bool reg_ok(const Geom& g) {
+  const int E = EPT<T>::E;
+  const int E2 = E / (g.Rg * g.Fq);
+  return g.D0 >= E && g.D1 >= E && g.G0 >= E && E2 >= 2 && g.N1 >= E2 && (g.D1 / E) * g.Rg <= REG_THREADS &&
+         (g.D0 / E) <= REG_THREADS && (g.G0 / E) <= REG_THREADS;
+}
+
+template <typename T>
+az_status launch_colfwd_stencil(const Geom& g, const SketchIn<T>& in, int pair0, int npairs,
+                                typename C2<T>::t* X1, const PassTabs& tb, cudaStream_t st) {
+  using V = typename C2<T>::t;
+  if (!reg_ok<T>(g)) return launch_colfwd_stencil_v1<T>(g, in, pair0, npairs, X1, tb, st);
+  const int C = reg_cols<T>(g.D0, g.D1);
+  const int threads = C * (g.D0 / EPT<T>::E);
+  size_t sm = ((size_t)padix_host(g.D0 * C, 5) + 32 + (g.dim == 2 ? (size_t)g.n[0] * C : 0)) * sizeof(V);
+  auto kern = k_colfwd_r<T, 1, double>;
+  if (set_smem(kern, sm) != cudaSuccess) { set_error("smem attribute"); return AZ_ERR_CUDA; }
+  dim3 grid(g.D1 / C, npairs);
+  ProfScope ps(sizeof(T) == 4 ? "colfwd_sketch_f32" : "colfwd_sketch_f64", (double)npairs * g.L * sizeof(V) + npairs * 2.0 * g.N / 8 + 4.0 * g.L, st);
+  kern<<<grid, threads, sm, st>>>(g, in.pos2m, nullptr, 0, 0, in, pair0, ilog2i(C), X1, tb);
+  AZ_LAUNCH_CHECK();
+  return AZ_OK;
+}
+template <typename T, typename TB>
+az_status launch_colfwd_gather(const Geom& g, const int32_t* pos2m, const TB* b, int64_t ldb, int ncols,
+                               int pair0, int npairs, typename C2<T>::t* X1, const PassTabs& tb,
+                               cudaStream_t st, int64_t M_rows) {
+  using V = typename C2<T>::t;
+  if (!reg_ok<T>(g)) return launch_colfwd_gather_v1<T, TB>(g, pos2m, b, ldb, ncols, pair0, npairs, X1, tb, st, M_rows);
+  const int C = reg_cols<T>(g.D0, g.D1);
+  const int threads = C * (g.D0 / EPT<T>::E);
+  size_t sm = ((size_t)padix_host(g.D0 * C, 5) + 32) * sizeof(V);
+  auto kern = k_colfwd_r<T, 0, TB>;
+  if (set_smem(kern, sm) != cudaSuccess) { set_error("smem attribute"); return AZ_ERR_CUDA; }
+  dim3 grid(g.D1 / C, npairs);
+  SketchIn<T> none{};
+  ProfScope ps(sizeof(T) == 4 ? "colfwd_gather_f32" : "colfwd_gather_f64", (double)npairs * g.L * sizeof(V) + (double)std::min(ncols - 2 * pair0, 2 * npairs) * M_rows * sizeof(TB) + 4.0 * g.L, st);
+  kern<<<grid, threads, sm, st>>>(g, pos2m, b, ldb, ncols, none, pair0, ilog2i(C), X1, tb);
+  AZ_LAUNCH_CHECK();
+  return AZ_OK;
+}
+template <typename T>
+az_status launch_rowfold(const Geom& g, const typename C2<T>::t* X1, const T* H, int npairs,
+                         typename C2<T>::t* X3, const PassTabs& tb, cudaStream_t st) {
+  using V = typename C2<T>::t;
+  if (!reg_ok<T>(g)) return launch_rowfold_v1<T>(g, X1, H, npairs, X3, tb, st);
+  constexpr int E = EPT<T>::E;
+  const int P1 = g.D1 / E;
+  // groups per CTA: threads = GPB * Rg * P1 <= 512
+  int GPB = 1;
+  while (GPB * 2 * g.Rg * P1 <= REG_THREADS && g.G0 % (GPB * 2) == 0 && GPB * 2 <= 8) GPB *= 2;
+  const int threads = GPB * g.Rg * P1;
+  size_t sm = ((size_t)padix_host(g.D1 * GPB * g.Rg, 4) + 16 + padix_host(g.N1 * GPB, 4) + 16) * sizeof(V);
+  const int E2 = E / (g.Rg * g.Fq);
+  dim3 grid(g.G0 / GPB, npairs);
+  ProfScope ps(sizeof(T) == 4 ? "rowfold_f32" : "rowfold_f64", (double)npairs * (g.L + g.N) * sizeof(V) + (double)g.L * sizeof(T), st);
+  if (E2 == 8) {
+    if (set_smem(k_rowfold_r<T, 8>, sm) != cudaSuccess) { set_error("smem attribute"); return AZ_ERR_CUDA; }
+    k_rowfold_r<T, 8><<<grid, threads, sm, st>>>(g, X1, H, ilog2i(GPB), X3, tb);
+  } else if (E2 == 4) {
+    if (set_smem(k_rowfold_r<T, 4>, sm) != cudaSuccess) { set_error("smem attribute"); return AZ_ERR_CUDA; }
+    k_rowfold_r<T, 4><<<grid, threads, sm, st>>>(g, X1, H, ilog2i(GPB), X3, tb);
+  } else if (E2 == 2) {
+    if (set_smem(k_rowfold_r<T, 2>, sm) != cudaSuccess) { set_error("smem attribute"); return AZ_ERR_CUDA; }
+    k_rowfold_r<T, 2><<<grid, threads, sm, st>>>(g, X1, H, ilog2i(GPB), X3, tb);
+  } else {
+    if (set_smem(k_rowfold_r<T, 16>, sm) != cudaSuccess) { set_error("smem attribute"); return AZ_ERR_CUDA; }
+    k_rowfold_r<T, 16><<<grid, threads, sm, st>>>(g, X1, H, ilog2i(GPB), X3, tb);
+  }
+  AZ_LAUNCH_CHECK();
+  return AZ_OK;
+}
+template <typename T, typename TO>
+az_status launch_colinv(const Geom& g, const typename C2<T>::t* X3, int pair0, int npairs, int ncols,
+                        TO* out, int64_t ldo, const uint32_t* bits, int64_t nw, const PassTabs& tb,
+                        cudaStream_t st) {
+  using V = typename C2<T>::t;
+  if (!reg_ok<T>(g)) return launch_colinv_v1<T, TO>(g, X3, pair0, npairs, ncols, out, ldo, bits, nw, tb, st);
+  const int C = reg_cols<T>(g.G0, g.N1);
+  const int threads = C * (g.G0 / EPT<T>::E);
+  size_t sm = ((size_t)padix_host(g.G0 * C, 5) + 32) * sizeof(V);
+  dim3 grid(g.N1 / C, npairs);
+  ProfScope ps(sizeof(T) == 4 ? "colinv_f32" : "colinv_f64", (double)npairs * g.N * sizeof(V) + (double)std::min(ncols - 2 * pair0, 2 * npairs) * g.N * sizeof(TO), st);
+  if (bits) {
+    if (set_smem(k_colinv_r<T, TO, true>, sm) != cudaSuccess) { set_error("smem attribute"); return AZ_ERR_CUDA; }
+    k_colinv_r<T, TO, true><<<grid, threads, sm, st>>>(g, X3, pair0, ncols, ilog2i(C), out, ldo, bits, nw, tb);
+  } else {
+    if (set_smem(k_colinv_r<T, TO, false>, sm) != cudaSuccess) { set_error("smem attribute"); return AZ_ERR_CUDA; }
+    k_colinv_r<T, TO, false><<<grid, threads, sm, st>>>(g, X3, pair0, ncols, ilog2i(C), out, ldo, bits, nw, tb);
+  }
+  AZ_LAUNCH_CHECK();
+  return AZ_OK;
+}
+
+#define INST_R(T)                                                                                           \
   template az_status launch_colfwd_stencil<T>(const Geom&, const SketchIn<T>&, int, int, C2<T>::t*,          \
                                               const PassTabs&, cudaStream_t);                               \
-  template az_status launch_colfwd_load<T>(const Geom&, const C2<T>::t*, int, C2<T>::t*, const PassTabs&,    \
-                                           cudaStream_t);                                                   \
-  template az_status launch_rowfft<T>(const Geom&, const C2<T>::t*, int, C2<T>::t*, const PassTabs&,        \
-                                      cudaStream_t);                                                        \
   template az_status launch_rowfold<T>(const Geom&, const C2<T>::t*, const T*, int, C2<T>::t*,              \
                                        const PassTabs&, cudaStream_t);                                      \
   template az_status launch_colfwd_gather<T, double>(const Geom&, const int32_t*, const double*, int64_t,    \
                                                      int, int, int, C2<T>::t*, const PassTabs&,             \
-                                                     cudaStream_t);                                         \
+                                                     cudaStream_t, int64_t);                                \
   template az_status launch_colfwd_gather<T, float>(const Geom&, const int32_t*, const float*, int64_t, int, \
-                                                    int, int, C2<T>::t*, const PassTabs&, cudaStream_t);    \
+                                                    int, int, C2<T>::t*, const PassTabs&, cudaStream_t,     \
+                                                    int64_t);                                               \
   template az_status launch_colinv<T, float>(const Geom&, const C2<T>::t*, int, int, int, float*, int64_t,  \
                                              const uint32_t*, int64_t, const PassTabs&, cudaStream_t);      \
   template az_status launch_colinv<T, double>(const Geom&, const C2<T>::t*, int, int, int, double*,         \
                                               int64_t, const uint32_t*, int64_t, const PassTabs&,           \
                                               cudaStream_t);
+INST_R(float)
+INST_R(double)
+
+// ------------------------------------------------------------------ explicit instantiations
+#define INST_T(T)                                                                                           \
+  template az_status launch_colfwd_load<T>(const Geom&, const C2<T>::t*, int, C2<T>::t*, const PassTabs&,    \
+                                           cudaStream_t);                                                   \
+  template az_status launch_rowfft<T>(const Geom&, const C2<T>::t*, int, C2<T>::t*, const PassTabs&,        \
+                                      cudaStream_t);
 INST_T(float)
 INST_T(double)
 

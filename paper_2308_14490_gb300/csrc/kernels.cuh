@@ -13,7 +13,13 @@ az_status launch_compact(const uint8_t* mask, int64_t L, int32_t* pos2m, int32_t
 // (f = phi or phi''), FP64, m = 0..L-1.
 az_status launch_samples(double* g, int64_t L, double hL, double eps, int deriv, int pimg, cudaStream_t st);
 // stencil taps t[m + W] = g(m mod L) for |m| <= W, FP64 and FP32 copies
-az_status launch_taps(const double* g, int64_t L, int W, double* t64, float* t32, cudaStream_t st);
+az_status launch_taps(const double* g, int64_t L, int W64, double* t64, int W32, float* t32, cudaStream_t st,
+                      float* th = nullptr, float* tl = nullptr);
+// FP64-accurate residual rows (kept grid rows only): out = b - A x for x exactly
+// representable in FP32 (given as floats), taps split into FP32 hi/lo.
+az_status launch_resid_df(const Geom& g, int kind, double eps, const int32_t* idx, int64_t M, const float* const th[4],
+                          const float* const tl[4], int Wx, int Wy, const float* xf, int64_t ldx, const double* b,
+                          int64_t ldb, float* out, int64_t ldo, int ncols, cudaStream_t st);
 
 // Twiddle tables (host-built, copied): master table of 4096 entries w_4096^m.
 void host_twiddles(int n, std::vector<double>& re, std::vector<double>& im);
@@ -43,7 +49,7 @@ az_status launch_colfwd_stencil(const Geom& g, const SketchIn<T>& in, int pair0,
 template <typename T, typename TB>
 az_status launch_colfwd_gather(const Geom& g, const int32_t* pos2m, const TB* b, int64_t ldb, int ncols,
                                int pair0, int npairs, typename C2<T>::t* X1, const PassTabs& tb,
-                               cudaStream_t st);
+                               cudaStream_t st, int64_t M_rows);
 template <typename T>
 az_status launch_colfwd_load(const Geom& g, const typename C2<T>::t* in, int npairs,
                              typename C2<T>::t* X1, const PassTabs& tb, cudaStream_t st);

@@ -13,6 +13,7 @@
 // Sigma^{-1}, so that u = VS U_tau^T g.
 #include <cmath>
 #include "lowrank.cuh"
+#include "profile.cuh"
 
 namespace az {
 
@@ -22,77 +23,248 @@ namespace az {
     if (_e != cudaSuccess) { set_error(std::string("kernel launch: ") + cudaGetErrorString(_e)); return AZ_ERR_CUDA; } \
   } while (0)
 
-static constexpr int GRAM_ROWS = 2048;  // rows per CTA of the Gram partials
+static constexpr int GRAM_ROWS = 1024;  // rows per CTA of the Gram partials
 static constexpr int GRAM_TILE = 64;    // rows staged per step
 
 int gram_blocks(int64_t M) { return (int)std::max<int64_t>(1, (M + GRAM_ROWS - 1) / GRAM_ROWS); }
 
-// Each CTA: rows [b*GRAM_ROWS, ...), all (a, c) pairs; A and B tiles staged in
-// shared memory as double; per-thread FP64 accumulators.
-template <typename TA, typename TB>
-__global__ void k_gram_partial(const TA* __restrict__ A, int64_t lda, int ka, const TB* __restrict__ B, int64_t ldb,
-                               int kb, int64_t M, double* __restrict__ partial) {
+// Each CTA: rows [b*GRAM_ROWS, ...); each thread owns an RA x RB block of the
+// ka x kb output; tiles of GRAM_TILE rows are staged in shared memory in the
+// staging type TS.  Products within a tile are summed in TS, tiles are summed
+// in FP64 (TS = double gives FP64 products throughout).
+// Exact FP32 product a*b = p + e (e from one fma) and two-sum accumulation into
+// a (hi, lo) pair: the "double-float" arithmetic used where FP32 inputs need an
+// FP64-accurate sum (about 48 significant bits) at FP32 throughput.
+struct DF { float hi, lo; };
+__device__ __forceinline__ void df_add_prod(DF& s, float a, float b) {
+  const float p = a * b;
+  const float e = fmaf(a, b, -p);
+  const float t = s.hi + p;
+  const float bb = t - s.hi;
+  const float err = (s.hi - (t - bb)) + (p - bb);
+  s.hi = t;
+  s.lo += err + e;
+}
+__device__ __forceinline__ void df_add_prod_split(DF& s, float a, float bh, float bl) {
+  df_add_prod(s, a, bh);
+  s.lo = fmaf(a, bl, s.lo);
+}
+
+// Asynchronous global->shared copy of one element (zero-filled when !valid).
+template <int BYTES>
+__device__ __forceinline__ void cp_async_elem(void* sdst, const void* gsrc, bool valid) {
+  const unsigned saddr = (unsigned)__cvta_generic_to_shared(sdst);
+  const int srcsize = valid ? BYTES : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(saddr), "l"(gsrc), "n"(BYTES), "r"(srcsize));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// Staged tiles are double-buffered with cp.async so the next tile's loads are
+// in flight while the current one is multiplied.  TS is the input type (no
+// conversion on the copy).
+template <typename TA, typename TB, typename TS, int RA, int RB, bool DFMODE>
+__global__ void __launch_bounds__(256) k_gram_partial(const TA* __restrict__ A, int64_t lda, int ka, const TB* __restrict__ B,
+                                                      int64_t ldb, int kb, int64_t M, double* __restrict__ partial, int sym) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* sA = (double*)smem_raw;             // GRAM_TILE x ka  [row*ka + a]
-  double* sB = sA + GRAM_TILE * ka;           // GRAM_TILE x kb
-  const int npair = ka * kb;
+  TS* sbuf = (TS*)smem_raw;                       // 2 x GRAM_TILE x (ka + kb)
+  const int tile_elems = GRAM_TILE * (ka + kb);
+  double* red = (double*)(sbuf + 2 * tile_elems);  // nsplit x nblk x RA*RB (reduction)
+  const int nta = (ka + RA - 1) / RA, ntb = (kb + RB - 1) / RB;
+  const int nblkt = nta * ntb;
+  const int nsplit = blockDim.x / nblkt;        // thread groups splitting each tile's rows
+  const int bt = threadIdx.x % nblkt, sp = threadIdx.x / nblkt;
+  const int ta = bt % nta, tb = bt / nta;
+  // symmetric product (B == A): only blocks on or above the block diagonal
+  const bool active = sp < nsplit && (!sym || ta <= tb);
   const int64_t r0 = (int64_t)blockIdx.x * GRAM_ROWS;
   const int64_t r1 = (M < r0 + GRAM_ROWS) ? M : r0 + GRAM_ROWS;
-  constexpr int MAXP = 8;
-  double acc[MAXP];
-#pragma unroll
-  for (int q = 0; q < MAXP; ++q) acc[q] = 0.0;
-  for (int64_t rb = r0; rb < r1; rb += GRAM_TILE) {
+  const int ntiles = (int)((r1 - r0 + GRAM_TILE - 1) / GRAM_TILE);
+  auto issue = [&](int tix) {
+    TS* sA = sbuf + (tix & 1) * tile_elems;
+    TS* sB = sA + GRAM_TILE * ka;
+    const int64_t rb = r0 + (int64_t)tix * GRAM_TILE;
     const int nr = (int)((r1 - rb) < GRAM_TILE ? (r1 - rb) : GRAM_TILE);
-    __syncthreads();
     for (int t = threadIdx.x; t < GRAM_TILE * ka; t += blockDim.x) {
-      int a = t / GRAM_TILE, rr = t % GRAM_TILE;
-      sA[rr * ka + a] = rr < nr ? (double)A[(int64_t)a * lda + rb + rr] : 0.0;
+      const int a = t / GRAM_TILE, rr = t % GRAM_TILE;
+      const bool v = rr < nr;
+      cp_async_elem<sizeof(TS)>(sA + rr * ka + a, A + (int64_t)a * lda + (v ? rb + rr : r0), v);
     }
     for (int t = threadIdx.x; t < GRAM_TILE * kb; t += blockDim.x) {
-      int c = t / GRAM_TILE, rr = t % GRAM_TILE;
-      sB[rr * kb + c] = rr < nr ? (double)B[(int64_t)c * ldb + rb + rr] : 0.0;
+      const int c = t / GRAM_TILE, rr = t % GRAM_TILE;
+      const bool v = rr < nr;
+      cp_async_elem<sizeof(TS)>(sB + rr * kb + c, B + (int64_t)c * ldb + (v ? rb + rr : r0), v);
     }
-    __syncthreads();
+    cp_async_commit();
+  };
+  // accumulators live across all tiles of this CTA (FP64, FP32 or
+  // double-float); converted to FP64 once at the end
+  TS sacc[RA][RB];
+  DF dacc[RA][RB];
 #pragma unroll
-    for (int q = 0; q < MAXP; ++q) {
-      int p = threadIdx.x + q * blockDim.x;
-      if (p < npair) {
-        int a = p % ka, c = p / ka;
-        double s = 0.0;
-        for (int rr = 0; rr < nr; ++rr) s = fma(sA[rr * ka + a], sB[rr * kb + c], s);
-        acc[q] += s;
+  for (int i = 0; i < RA; ++i)
+#pragma unroll
+    for (int j = 0; j < RB; ++j) { sacc[i][j] = (TS)0; dacc[i][j].hi = 0.f; dacc[i][j].lo = 0.f; }
+  if (ntiles > 0) issue(0);
+  for (int tix = 0; tix < ntiles; ++tix) {
+    if (tix + 1 < ntiles) { issue(tix + 1); cp_async_wait<1>(); }
+    else cp_async_wait<0>();
+    __syncthreads();
+    const TS* sA = sbuf + (tix & 1) * tile_elems;
+    const TS* sB = sA + GRAM_TILE * ka;
+    const int64_t rb = r0 + (int64_t)tix * GRAM_TILE;
+    const int nr = (int)((r1 - rb) < GRAM_TILE ? (r1 - rb) : GRAM_TILE);
+    if (active) {
+      for (int rr = sp; rr < nr; rr += nsplit) {
+        TS av[RA], bv[RB];
+#pragma unroll
+        for (int i = 0; i < RA; ++i) { int a = ta * RA + i; av[i] = a < ka ? sA[rr * ka + a] : (TS)0; }
+#pragma unroll
+        for (int j = 0; j < RB; ++j) { int c = tb * RB + j; bv[j] = c < kb ? sB[rr * kb + c] : (TS)0; }
+        if (DFMODE) {
+#pragma unroll
+          for (int i = 0; i < RA; ++i)
+#pragma unroll
+            for (int j = 0; j < RB; ++j) df_add_prod(dacc[i][j], (float)av[i], (float)bv[j]);
+        } else {
+#pragma unroll
+          for (int i = 0; i < RA; ++i)
+#pragma unroll
+            for (int j = 0; j < RB; ++j) sacc[i][j] = fma(av[i], bv[j], sacc[i][j]);
+        }
       }
     }
+    __syncthreads();   // buffer (tix & 1) is refilled by the issue of tile tix + 2
   }
+  double acc[RA][RB];
 #pragma unroll
-  for (int q = 0; q < MAXP; ++q) {
-    int p = threadIdx.x + q * blockDim.x;
-    if (p < npair) partial[(int64_t)blockIdx.x * npair + p] = acc[q];
+  for (int i = 0; i < RA; ++i)
+#pragma unroll
+    for (int j = 0; j < RB; ++j)
+      acc[i][j] = DFMODE ? (double)dacc[i][j].hi + (double)dacc[i][j].lo : (double)sacc[i][j];
+  // reduce the split groups in a fixed order
+  __syncthreads();
+  if (active) {
+#pragma unroll
+    for (int i = 0; i < RA; ++i)
+#pragma unroll
+      for (int j = 0; j < RB; ++j) red[((size_t)sp * nblkt + bt) * (RA * RB) + i * RB + j] = acc[i][j];
+  }
+  __syncthreads();
+  const int npair = ka * kb;
+  for (int t = threadIdx.x; t < nblkt * RA * RB; t += blockDim.x) {
+    const int b2 = t / (RA * RB), e = t % (RA * RB);
+    const int i = e / RB, j = e % RB;
+    const int ta2 = b2 % nta, tb2 = b2 / nta;
+    if (sym && ta2 > tb2) continue;
+    const int a = ta2 * RA + i, c = tb2 * RB + j;
+    if (a >= ka || c >= kb) continue;
+    double sacc2 = 0.0;
+    for (int q = 0; q < nsplit; ++q) sacc2 += red[((size_t)q * nblkt + b2) * (RA * RB) + e];
+    partial[(int64_t)blockIdx.x * npair + a + (int64_t)c * ka] = sacc2;
   }
 }
-__global__ void k_gram_reduce(const double* __restrict__ partial, int nblk, int npair, double* __restrict__ G) {
+__global__ void k_gram_reduce(const double* __restrict__ partial, int nblk, int npair, int ka, int sym, int RA,
+                              double* __restrict__ G) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= npair) return;
+  int a = p % ka, c = p / ka;
+  // symmetric case: entries in blocks below the block diagonal were not
+  // computed; read the mirrored entry
+  int src = p;
+  if (sym && (a / RA) > (c / RA)) src = c + a * ka;
   double s = 0.0;
-  for (int b = 0; b < nblk; ++b) s += partial[(int64_t)b * npair + p];
+  for (int b = 0; b < nblk; ++b) s += partial[(int64_t)b * npair + src];
   G[p] = s;  // column-major ka x kb: p = a + c*ka
 }
+// mode: products summed in FP32 within a tile ("fast", FP32 inputs only),
+// else double-float for FP32 inputs, else FP64.
 template <typename TA, typename TB>
 az_status launch_gram(const TA* A, int64_t lda, int ka, const TB* B, int64_t ldb, int kb, int64_t M,
-                      double* partial, double* G, cudaStream_t st) {
+                      double* partial, double* G, cudaStream_t st, bool fast) {
+  constexpr int RA = 4, RB = 4;
   const int npair = ka * kb;
-  int threads = 256;
-  while (threads * 8 < npair && threads < 1024) threads *= 2;
-  if (threads * 8 < npair) { set_error("gram: too many columns for this kernel"); return AZ_ERR_ARG; }
+  const int nthr = ((ka + RA - 1) / RA) * ((kb + RB - 1) / RB);
+  if (nthr > 1024) { set_error("gram: too many columns for this kernel"); return AZ_ERR_ARG; }
+  const int nsplit = std::max(1, 256 / nthr);
+  const int threads = nsplit * nthr;
   const int nblk = gram_blocks(M);
-  size_t sm = (size_t)GRAM_TILE * (ka + kb) * sizeof(double);
-  if (sm > 48 * 1024) cudaFuncSetAttribute(k_gram_partial<TA, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_gram_partial<TA, TB><<<nblk, threads, sm, st>>>(A, lda, ka, B, ldb, kb, M, partial);
-  k_gram_reduce<<<(npair + 255) / 256, 256, 0, st>>>(partial, nblk, npair, G);
+  const bool in32 = sizeof(TA) == 4 && sizeof(TB) == 4;
+  const int sym = ((const void*)A == (const void*)B && ka == kb && lda == ldb) ? 1 : 0;
+  const size_t ts = in32 ? sizeof(float) : sizeof(double);
+  size_t sm = 2 * (size_t)GRAM_TILE * (ka + kb) * ts;
+  sm = (sm + 15) / 16 * 16 + (size_t)nsplit * nthr * RA * RB * sizeof(double);
+  ProfScope ps(in32 ? (fast ? "proj_f32" : "gram_df32") : "gram_f64", (double)M * (ka * sizeof(TA) + kb * sizeof(TB)), st, 2);
+  if (in32 && fast) {
+    auto k = k_gram_partial<TA, TB, float, RA, RB, false>;
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k<<<nblk, threads, sm, st>>>(A, lda, ka, B, ldb, kb, M, partial, sym);
+  } else if (in32) {
+    auto k = k_gram_partial<TA, TB, float, RA, RB, true>;
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k<<<nblk, threads, sm, st>>>(A, lda, ka, B, ldb, kb, M, partial, sym);
+  } else {
+    auto k = k_gram_partial<TA, TB, double, RA, RB, false>;
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k<<<nblk, threads, sm, st>>>(A, lda, ka, B, ldb, kb, M, partial, sym);
+  }
+  k_gram_reduce<<<(npair + 255) / 256, 256, 0, st>>>(partial, nblk, npair, ka, sym, RA, G);
   AZ_LCHECK();
   return AZ_OK;
 }
+
+// out[M x r] = A[M x k] * S[k x r] with A FP32 and S FP64 split into FP32
+// (hi, lo): each product a*S = a*hi (exact, two-product) + a*lo, summed in
+// double-float; the result is rounded to TO.  Used for Q1 = Y B1, whose small
+// directions cancel by up to sigma_1/sigma_r.
+template <typename TO, int KB>
+__global__ void __launch_bounds__(128) k_tsprod_df(const float* __restrict__ A, int64_t lda, int k,
+                                                   const double* __restrict__ S, int r, int64_t M, TO* __restrict__ out,
+                                                   int64_t ldo) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* sh = (float*)smem_raw;      // [a*KB + c]
+  float* sl = sh + k * KB;
+  for (int t = threadIdx.x; t < k * KB; t += blockDim.x) {
+    const int a = t / KB, c = t % KB;
+    const double v = c < r ? S[a + (int64_t)c * k] : 0.0;
+    const float h = (float)v;
+    sh[t] = h;
+    sl[t] = (float)(v - (double)h);
+  }
+  __syncthreads();
+  const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  DF acc[KB];
+#pragma unroll
+  for (int c = 0; c < KB; ++c) { acc[c].hi = 0.f; acc[c].lo = 0.f; }
+  for (int a = 0; a < k; ++a) {
+    const float v = A[(int64_t)a * lda + m];
+#pragma unroll
+    for (int c = 0; c < KB; ++c) df_add_prod_split(acc[c], v, sh[a * KB + c], sl[a * KB + c]);
+  }
+#pragma unroll
+  for (int c = 0; c < KB; ++c)
+    if (c < r) out[(int64_t)c * ldo + m] = (TO)((double)acc[c].hi + (double)acc[c].lo);
+}
+template <typename TO>
+az_status launch_tsprod_df(const float* A, int64_t lda, int k, const double* S, int r, int64_t M, TO* out, int64_t ldo,
+                           cudaStream_t st) {
+  ProfScope ps("tsprod_df32", (double)M * (k * 4 + r * sizeof(TO)), st);
+  const unsigned grid = (unsigned)((M + 127) / 128);
+  if (r <= 16) {
+    size_t sm = 2 * (size_t)k * 16 * sizeof(float);
+    k_tsprod_df<TO, 16><<<grid, 128, sm, st>>>(A, lda, k, S, r, M, out, ldo);
+  } else if (r <= 32) {
+    size_t sm = 2 * (size_t)k * 32 * sizeof(float);
+    k_tsprod_df<TO, 32><<<grid, 128, sm, st>>>(A, lda, k, S, r, M, out, ldo);
+  } else {
+    set_error("tsprod_df: r > 32 not supported by this kernel");
+    return AZ_ERR_ARG;
+  }
+  AZ_LCHECK();
+  return AZ_OK;
+}
+template az_status launch_tsprod_df<float>(const float*, int64_t, int, const double*, int, int64_t, float*, int64_t, cudaStream_t);
 
 // out = A * S : thread per (row, output column), S in shared memory.
 template <typename TA, typename TO>
@@ -119,6 +291,7 @@ az_status launch_tsprod(const TA* A, int64_t lda, int k, const double* S, int r,
   if (r > 64) { set_error("tsprod: r > 64 not supported by this kernel"); return AZ_ERR_ARG; }
   size_t sm = (size_t)k * r * sizeof(double);
   if (sm > 48 * 1024) cudaFuncSetAttribute(k_tsprod<TA, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  ProfScope ps("tsprod", (double)M * (k * sizeof(TA) + r * sizeof(TO)), st);
   k_tsprod<TA, TO><<<(unsigned)((M + 127) / 128), 128, sm, st>>>(A, lda, k, S, r, M, out, ldo);
   AZ_LCHECK();
   return AZ_OK;
@@ -130,13 +303,28 @@ az_status launch_tsprod(const TA* A, int64_t lda, int k, const double* S, int r,
 // orthogonal; V (n x n) accumulates the rotations.  Round-robin pair order, one
 // warp per pair.  After convergence column j has norm sigma_j and
 // a[:, j] / sigma_j is the left singular vector.
-__device__ void jacobi_onesided(double* a, int m, int n, double* V, int* flag) {
+__device__ int jacobi_onesided(double* a, int m, int n, double* V, int* flag, double floor_rel) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  // identity V
+  __shared__ double fro2;
+  // identity V; ||a||_F^2 is invariant under the rotations and sets the level
+  // below which column pairs are rounding noise and are left alone
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) V[t] = (t % n == t / n) ? 1.0 : 0.0;
+  if (threadIdx.x == 0) {
+    double f = 0;
+    for (int t = 0; t < m * n; ++t) f += a[t] * a[t];
+    fro2 = f;
+  }
   __syncthreads();
+  // a pair is orthogonal to working precision once |gamma| is below the
+  // rounding level of the larger column against the whole matrix (floor_rel;
+  // 0 = plain relative criterion)
+  const double fro = sqrt(fro2);
+  // relative orthogonality reachable by an m-term FP64 dot product
+  const double reltol = fmax(1e-15, 2.3e-16 * m);
   const int nn = (n + 1) & ~1;  // even count for round-robin (a dummy column if n odd)
-  for (int sweep = 0; sweep < 60; ++sweep) {
+  int sweeps = 0;
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    sweeps = sweep + 1;
     if (threadIdx.x == 0) *flag = 0;
     __syncthreads();
     for (int step = 0; step < nn - 1; ++step) {
@@ -157,7 +345,7 @@ __device__ void jacobi_onesided(double* a, int m, int n, double* V, int* flag) {
           be += __shfl_xor_sync(0xffffffffu, be, o);
           ga += __shfl_xor_sync(0xffffffffu, ga, o);
         }
-        if (fabs(ga) > 1e-15 * sqrt(al * be) && ga != 0.0) {
+        if (fabs(ga) > floor_rel * fro * sqrt(fmax(al, be)) && fabs(ga) > reltol * sqrt(al * be)) {
           double zeta = (be - al) / (2.0 * ga);
           double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
           double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
@@ -180,78 +368,113 @@ __device__ void jacobi_onesided(double* a, int m, int n, double* V, int* flag) {
     if (*flag == 0) break;
     __syncthreads();
   }
+  return sweeps;
 }
 
-// sort columns of (a, V) by decreasing norm; norms into sig
-__device__ void sort_by_norm(double* a, int m, int n, double* V, double* sig, double* tmp) {
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    double s = 0;
-    for (int r = 0; r < m; ++r) s += a[j * m + r] * a[j * m + r];
-    sig[j] = sqrt(s);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    // selection sort on indices (n <= 64)
-    for (int i = 0; i < n; ++i) {
-      int best = i;
-      for (int j = i + 1; j < n; ++j) if (sig[j] > sig[best]) best = j;
-      if (best != i) {
-        double t = sig[i]; sig[i] = sig[best]; sig[best] = t;
-        for (int r = 0; r < m; ++r) { double u = a[i * m + r]; a[i * m + r] = a[best * m + r]; a[best * m + r] = u; }
-        for (int r = 0; r < n; ++r) { double u = V[i * n + r]; V[i * n + r] = V[best * n + r]; V[best * n + r] = u; }
-      }
-    }
-  }
-  __syncthreads();
-  (void)tmp;
-}
-
-__global__ void k_factor1(const double* __restrict__ G1, int k, double taug, double floor2, double* V, double* lam,
+// Pass 1 (rank-revealing): Cholesky of G1 = Y^T Y with symmetric diagonal
+// pivoting, stopped when the largest remaining pivot is <= tol * the largest
+// initial diagonal.  Y P = Q1 R1 with R1 = [R11 R12] (r1 x k, upper
+// trapezoidal in pivoted order).  Writes B1 = P[:, :r1] R11^{-1} (k x k, zero
+// columns beyond r1), R1P = R1 P^T (r1 x k, ld k; the small factor of Y in the
+// original column order) and r1.
+__global__ void k_factor1(const double* __restrict__ G1, int k, double tol, double floor2, double* R1P, double* lam,
                           double* B1, FactorInfo* info) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* a = (double*)smem_raw;   // k x k
-  double* sV = a + k * k;          // k x k
-  double* sg = sV + k * k;         // k
-  __shared__ int flag;
-  for (int t = threadIdx.x; t < k * k; t += blockDim.x) a[t] = G1[t];
+  double* G = (double*)smem_raw;   // k x k working copy, column-major
+  double* R = G + k * k;           // r1 x k rows (ld k): R[i*k + c]
+  __shared__ int perm[64];
+  __shared__ int piv, r1s, stop;
+  __shared__ double dmax;
+  for (int t = threadIdx.x; t < k * k; t += blockDim.x) { G[t] = G1[t]; R[t] = 0.0; }
+  for (int t = threadIdx.x; t < k; t += blockDim.x) perm[t] = t;
+  if (threadIdx.x == 0) { r1s = 0; stop = 0; }
   __syncthreads();
-  jacobi_onesided(a, k, k, sV, &flag);
-  sort_by_norm(a, k, k, sV, sg, nullptr);
-  // G1 SPD: the column norms of G1 V are the eigenvalues lambda
-  __shared__ int r1s;
-  if (threadIdx.x == 0) {
-    int r1 = 0;
-    double l1 = sg[0];
-    bool finite = isfinite(l1);
-    for (int j = 0; j < k; ++j) if (sg[j] > taug * taug * l1 && sg[j] > floor2 && isfinite(sg[j])) ++r1;
-    r1s = r1;
-    info->r1 = r1;
-    info->status = finite ? 0 : 2;
+  for (int j = 0; j < k; ++j) {
+    if (threadIdx.x == 0) {
+      int p = j;
+      double best = G[j * k + j];
+      for (int i = j + 1; i < k; ++i) if (G[i * k + i] > best) { best = G[i * k + i]; p = i; }
+      if (j == 0) dmax = best;
+      if (!(best > tol * dmax) || !(best > floor2) || !isfinite(best)) stop = 1;
+      piv = p;
+    }
+    __syncthreads();
+    if (stop) break;
+    const int p = piv;
+    if (p != j) {  // symmetric swap of rows/columns j and p, and of R's columns
+      for (int t = threadIdx.x; t < k; t += blockDim.x) {
+        double u = G[t * k + j]; G[t * k + j] = G[t * k + p]; G[t * k + p] = u;
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < k; t += blockDim.x) {
+        double u = G[j * k + t]; G[j * k + t] = G[p * k + t]; G[p * k + t] = u;
+      }
+      for (int t = threadIdx.x; t < j; t += blockDim.x) {
+        double u = R[t * k + j]; R[t * k + j] = R[t * k + p]; R[t * k + p] = u;
+      }
+      if (threadIdx.x == 0) { int u = perm[j]; perm[j] = perm[p]; perm[p] = u; }
+      __syncthreads();
+    }
+    const double d = sqrt(G[j * k + j]);
+    for (int c = j + threadIdx.x; c < k; c += blockDim.x) R[j * k + c] = (c == j) ? d : G[c * k + j] / d;
+    __syncthreads();
+    for (int t = threadIdx.x; t < (k - j - 1) * (k - j - 1); t += blockDim.x) {
+      const int i = j + 1 + t % (k - j - 1), c = j + 1 + t / (k - j - 1);
+      G[c * k + i] -= R[j * k + i] * R[j * k + c];
+    }
+    if (threadIdx.x == 0) r1s = j + 1;
+    __syncthreads();
   }
-  __syncthreads();
+  const int r1 = r1s;
+  if (threadIdx.x == 0) { info->r1 = r1; info->status = isfinite(dmax) ? 0 : 2; info->pad = 0; }
+  // B1 = P[:, :r1] R11^{-1}: column c solves R11 y = e_c by back substitution
+  for (int c = threadIdx.x; c < k; c += blockDim.x) {
+    for (int i = 0; i < k; ++i) B1[(int64_t)c * k + i] = 0.0;
+    if (c < r1) {
+      double y[64];
+      for (int i = r1 - 1; i >= 0; --i) {
+        double sacc = (i == c) ? 1.0 : 0.0;
+        for (int l = i + 1; l < r1; ++l) sacc -= R[i * k + l] * y[l];
+        y[i] = sacc / R[i * k + i];
+      }
+      for (int i = 0; i < r1; ++i) B1[(int64_t)c * k + perm[i]] = y[i];
+    }
+  }
+  // R1P = R1 P^T (rows i < r1, original column order), ld k
   for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
-    int row = t % k, col = t / k;
-    V[t] = sV[t];
-    B1[t] = col < r1s ? sV[col * k + row] / sqrt(sg[col]) : 0.0;
+    const int i = t % k, c = t / k;
+    R1P[(int64_t)c * k + i] = 0.0;
   }
-  for (int t = threadIdx.x; t < k; t += blockDim.x) lam[t] = sg[t];
+  __syncthreads();
+  for (int t = threadIdx.x; t < r1 * k; t += blockDim.x) {
+    const int i = t % r1, c = t / r1;   // pivoted column c
+    R1P[(int64_t)perm[c] * k + i] = c >= i ? R[i * k + c] : 0.0;
+  }
+  for (int t = threadIdx.x; t < k; t += blockDim.x) lam[t] = t < r1 ? R[t * k + t] : 0.0;
 }
 az_status launch_factor1(const double* G1, int k, double taug, double floor2, double* V, double* lam, double* B1,
                          FactorInfo* info, cudaStream_t st) {
   if (k > 64) { set_error("factor: k > 64 not supported by the one-CTA factorisation"); return AZ_ERR_ARG; }
-  size_t sm = (2 * (size_t)k * k + k) * sizeof(double);
+  size_t sm = (2 * (size_t)k * k) * sizeof(double);
   if (sm > 48 * 1024) cudaFuncSetAttribute(k_factor1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_factor1<<<1, 1024, sm, st>>>(G1, k, taug, floor2, V, lam, B1, info);
+  ProfScope ps("factor1", 0.0, st);
+  const double tol = fmax(taug * taug, 1e-15);
+  k_factor1<<<1, 256, sm, st>>>(G1, k, tol, floor2, V, lam, B1, info);
   AZ_LCHECK();
   return AZ_OK;
 }
 
-__global__ void k_factor2(const double* __restrict__ G2, int k, const double* __restrict__ V, const double* __restrict__ lam,
+// Pass 2: R2 = chol(G2[:r1, :r1]) with G2 = Q1^T Q1, Q1 = Y B1; the small
+// factor of Y is Rs = R2 R1P (r1 x k), so Y = (Q1 R2^{-1}) Rs.  One-sided
+// Jacobi on Rs^T (k x r1) gives Rs^T = V_R Sigma U_R^T; rank r = #(sigma >
+// tau sigma_1, > floor); T = R2^{-1} U_R[:, :r] (so U_tau = Q1 T) and
+// VS = V_R[:, :r] Sigma^{-1}; both k x k with zero columns beyond r.
+__global__ void k_factor2(const double* __restrict__ G2, int k, const double* __restrict__ R1P,
                           double tau, double floor, double* T, double* VS, double* sig, FactorInfo* info) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* R = (double*)smem_raw;   // r1 x r1 (column-major ld k), Cholesky factor, upper
-  double* A = R + k * k;           // Rs, then rotated
-  double* VR = A + k * k;          // k x k
+  double* R = (double*)smem_raw;   // r1 x r1 Cholesky factor (upper), column-major ld k
+  double* A = R + k * k;           // Rs^T: k x r1, column-major ld k
+  double* VR = A + k * k;          // r1 x r1 rotations
   double* sg = VR + k * k;
   __shared__ int flag;
   __shared__ int fail;
@@ -259,13 +482,11 @@ __global__ void k_factor2(const double* __restrict__ G2, int k, const double* __
   for (int t = threadIdx.x; t < k * k; t += blockDim.x) { R[t] = 0.0; A[t] = 0.0; }
   if (threadIdx.x == 0) fail = 0;
   __syncthreads();
-  // copy upper part of G2[:r1,:r1] into R (column-major, ld k)
   for (int t = threadIdx.x; t < r1 * r1; t += blockDim.x) {
     int i = t % r1, j = t / r1;
     if (i <= j) R[j * k + i] = G2[(int64_t)j * k + i];
   }
   __syncthreads();
-  // right-looking Cholesky, upper: G2 = R^T R
   for (int j = 0; j < r1; ++j) {
     if (threadIdx.x == 0) {
       double d = R[j * k + j];
@@ -273,7 +494,7 @@ __global__ void k_factor2(const double* __restrict__ G2, int k, const double* __
       R[j * k + j] = sqrt(d);
     }
     __syncthreads();
-    double djj = R[j * k + j];
+    const double djj = R[j * k + j];
     for (int c = j + 1 + threadIdx.x; c < r1; c += blockDim.x) R[c * k + j] /= djj;
     __syncthreads();
     for (int t = threadIdx.x; t < r1 * r1; t += blockDim.x) {
@@ -282,18 +503,39 @@ __global__ void k_factor2(const double* __restrict__ G2, int k, const double* __
     }
     __syncthreads();
   }
-  // Rs = R diag(sqrt(lam)) (r1 x r1, column-major ld r1 in A)
-  for (int t = threadIdx.x; t < r1 * r1; t += blockDim.x) {
-    int i = t % r1, j = t / r1;
-    A[j * r1 + i] = (i <= j ? R[j * k + i] : 0.0) * sqrt(lam[j]);
+  // A = Rs^T = R1P^T R2^T : A[c, i] = sum_l R1P[l, c] R2[i, l]  (l <= i)
+  for (int t = threadIdx.x; t < k * r1; t += blockDim.x) {
+    const int c = t % k, i = t / k;
+    double sacc = 0.0;
+    for (int l = 0; l <= i; ++l) sacc += R1P[(int64_t)c * k + l] * R[i * k + l];
+    A[i * k + c] = sacc;
   }
   __syncthreads();
-  jacobi_onesided(A, r1, r1, VR, &flag);
-  sort_by_norm(A, r1, r1, VR, sg, nullptr);
+  const int sw = jacobi_onesided(A, k, r1, VR, &flag, 1e-14);
+  if (threadIdx.x == 0) info->pad = sw;
+  // sort by decreasing norm (columns of A of length k, rotations VR of length r1)
+  for (int j = threadIdx.x; j < r1; j += blockDim.x) {
+    double sacc = 0;
+    for (int rr = 0; rr < k; ++rr) sacc += A[j * k + rr] * A[j * k + rr];
+    sg[j] = sqrt(sacc);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < r1; ++i) {
+      int best = i;
+      for (int j = i + 1; j < r1; ++j) if (sg[j] > sg[best]) best = j;
+      if (best != i) {
+        double u = sg[i]; sg[i] = sg[best]; sg[best] = u;
+        for (int rr = 0; rr < k; ++rr) { u = A[i * k + rr]; A[i * k + rr] = A[best * k + rr]; A[best * k + rr] = u; }
+        for (int rr = 0; rr < r1; ++rr) { u = VR[i * r1 + rr]; VR[i * r1 + rr] = VR[best * r1 + rr]; VR[best * r1 + rr] = u; }
+      }
+    }
+  }
+  __syncthreads();
   __shared__ int rs;
   if (threadIdx.x == 0) {
     int r = 0;
-    double s1 = r1 > 0 ? sg[0] : 0.0;
+    const double s1 = r1 > 0 ? sg[0] : 0.0;
     for (int j = 0; j < r1; ++j) if (sg[j] > tau * s1 && sg[j] > floor) ++r;
     rs = r;
     info->r = r;
@@ -303,26 +545,21 @@ __global__ void k_factor2(const double* __restrict__ G2, int k, const double* __
   }
   __syncthreads();
   const int r = rs;
-  // U_R[:, c] = A[:, c] / sg[c]  (in A, ld r1); T = R^{-1} U_R[:, :r]  (back substitution, thread per column)
+  // U_R = VR (r1 x r1, column c); T = R2^{-1} U_R[:, :r] by back substitution
   for (int c = threadIdx.x; c < k; c += blockDim.x) {
     for (int i = 0; i < k; ++i) T[(int64_t)c * k + i] = 0.0;
     if (c < r) {
       for (int i = r1 - 1; i >= 0; --i) {
-        double s = A[c * r1 + i] / sg[c];
-        for (int l = i + 1; l < r1; ++l) s -= R[l * k + i] * T[(int64_t)c * k + l];
-        T[(int64_t)c * k + i] = s / R[i * k + i];
+        double sacc = VR[c * r1 + i];
+        for (int l = i + 1; l < r1; ++l) sacc -= R[l * k + i] * T[(int64_t)c * k + l];
+        T[(int64_t)c * k + i] = sacc / R[i * k + i];
       }
     }
   }
-  // VS = V[:, :r1] VR[:, :r] Sigma^{-1}  (k x k, zero beyond r)
+  // VS = V_R[:, :r] Sigma^{-1} = A[:, c] / sigma_c^2
   for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
-    int i = t % k, c = t / k;
-    double s = 0.0;
-    if (c < r) {
-      for (int l = 0; l < r1; ++l) s += V[(int64_t)l * k + i] * VR[c * r1 + l];
-      s /= sg[c];
-    }
-    VS[t] = s;
+    const int i = t % k, c = t / k;
+    VS[t] = c < r ? A[c * k + i] / (sg[c] * sg[c]) : 0.0;
   }
   for (int t = threadIdx.x; t < k; t += blockDim.x) sig[t] = t < r1 ? sg[t] : 0.0;
 }
@@ -331,7 +568,9 @@ az_status launch_factor2(const double* G2, int k, const double* V, const double*
   if (k > 64) { set_error("factor: k > 64 not supported by the one-CTA factorisation"); return AZ_ERR_ARG; }
   size_t sm = (3 * (size_t)k * k + k) * sizeof(double);
   if (sm > 48 * 1024) cudaFuncSetAttribute(k_factor2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_factor2<<<1, 1024, sm, st>>>(G2, k, V, lam, tau, floor, T, VS, sig, info);
+  ProfScope ps("factor2", 0.0, st);
+  (void)lam;
+  k_factor2<<<1, 32 * std::max(1, std::min(32, (k + 1) / 2)), sm, st>>>(G2, k, V, tau, floor, T, VS, sig, info);
   AZ_LCHECK();
   return AZ_OK;
 }
@@ -345,43 +584,60 @@ __global__ void k_small_mm(const double* VS, int k, const double* c, int n, doub
   u[t] = s;
 }
 az_status launch_small_mm(const double* VS, int k, const double* c, int n, double* u, cudaStream_t st) {
+  ProfScope ps("small_mm", 0.0, st);
   k_small_mm<<<(k * n + 255) / 256, 256, 0, st>>>(VS, k, c, n, u);
   AZ_LCHECK();
   return AZ_OK;
 }
 
-template <typename TW, typename TZ>
-__global__ void k_update_x(const TW* __restrict__ W, int64_t ldw, int k, const double* __restrict__ u,
-                           const TZ* __restrict__ z, int64_t ldz, int64_t N, double* __restrict__ x, int64_t ldx,
-                           int accumulate) {
+// x[:, c] = (accumulate ? x : 0) + z[:, c] + W u[:, c]: one thread per
+// coefficient j, its W row held in registers, all right-hand sides in a loop;
+// arithmetic in the precision of W (FP32 in the mixed path), result stored FP64.
+template <typename TW, typename TZ, int KB>
+__global__ void __launch_bounds__(256) k_update_x(const TW* __restrict__ W, int64_t ldw, int k, const double* __restrict__ u,
+                                                  const TZ* z, int64_t ldz, int64_t N, int nrhs,
+                                                  double* __restrict__ x, int64_t ldx, int accumulate, float* xf) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* su = (double*)smem_raw;
-  const int c = blockIdx.y;
-  for (int t = threadIdx.x; t < k; t += blockDim.x) su[t] = u[(int64_t)c * k + t];
+  TW* su = (TW*)smem_raw;   // [c*k + a]
+  for (int t = threadIdx.x; t < k * nrhs; t += blockDim.x) su[t] = (TW)u[t];
   __syncthreads();
-  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= N) return;
-  double s = (double)z[(int64_t)c * ldz + j];
-  for (int a = 0; a < k; ++a) s = fma((double)W[(int64_t)a * ldw + j], su[a], s);
-  double* xp = x + (int64_t)c * ldx + j;
-  *xp = accumulate ? *xp + s : s;
+  TW w[KB];
+#pragma unroll
+  for (int a = 0; a < KB; ++a) w[a] = a < k ? W[(int64_t)a * ldw + j] : (TW)0;
+  for (int c = 0; c < nrhs; ++c) {
+    TW s = (TW)z[(int64_t)c * ldz + j];
+    const TW* uc = su + c * k;
+#pragma unroll
+    for (int a = 0; a < KB; ++a) if (a < k) s = fma(w[a], uc[a], s);
+    double* xp = x + (int64_t)c * ldx + j;
+    *xp = accumulate ? *xp + (double)s : (double)s;
+    if (xf) xf[(int64_t)c * ldz + j] = (float)s;   // exact FP32 copy (may alias z)
+  }
 }
 template <typename TW, typename TZ>
 az_status launch_update_x(const TW* W, int64_t ldw, int k, const double* u, const TZ* z, int64_t ldz, int64_t N,
-                          int nrhs, double* x, int64_t ldx, bool accumulate, cudaStream_t st) {
-  dim3 grid((unsigned)((N + 255) / 256), nrhs);
-  k_update_x<TW, TZ><<<grid, 256, k * sizeof(double), st>>>(W, ldw, k, u, z, ldz, N, x, ldx, accumulate ? 1 : 0);
+                          int nrhs, double* x, int64_t ldx, bool accumulate, cudaStream_t st, float* xf) {
+  ProfScope ps("update_x", (double)N * (k * sizeof(TW) + nrhs * (sizeof(TZ) + 8.0 * (accumulate ? 2 : 1))), st);
+  size_t sm = (size_t)k * nrhs * sizeof(TW);
+  unsigned grid = (unsigned)((N + 255) / 256);
+  if (k <= 8) k_update_x<TW, TZ, 8><<<grid, 256, sm, st>>>(W, ldw, k, u, z, ldz, N, nrhs, x, ldx, accumulate ? 1 : 0, xf);
+  else if (k <= 16) k_update_x<TW, TZ, 16><<<grid, 256, sm, st>>>(W, ldw, k, u, z, ldz, N, nrhs, x, ldx, accumulate ? 1 : 0, xf);
+  else if (k <= 32) k_update_x<TW, TZ, 32><<<grid, 256, sm, st>>>(W, ldw, k, u, z, ldz, N, nrhs, x, ldx, accumulate ? 1 : 0, xf);
+  else k_update_x<TW, TZ, 64><<<grid, 256, sm, st>>>(W, ldw, k, u, z, ldz, N, nrhs, x, ldx, accumulate ? 1 : 0, xf);
   AZ_LCHECK();
   return AZ_OK;
 }
 
-template az_status launch_gram<float, float>(const float*, int64_t, int, const float*, int64_t, int, int64_t, double*, double*, cudaStream_t);
-template az_status launch_gram<double, double>(const double*, int64_t, int, const double*, int64_t, int, int64_t, double*, double*, cudaStream_t);
-template az_status launch_gram<float, double>(const float*, int64_t, int, const double*, int64_t, int, int64_t, double*, double*, cudaStream_t);
+template az_status launch_gram<float, float>(const float*, int64_t, int, const float*, int64_t, int, int64_t, double*, double*, cudaStream_t, bool);
+template az_status launch_gram<double, double>(const double*, int64_t, int, const double*, int64_t, int, int64_t, double*, double*, cudaStream_t, bool);
+template az_status launch_gram<float, double>(const float*, int64_t, int, const double*, int64_t, int, int64_t, double*, double*, cudaStream_t, bool);
 template az_status launch_tsprod<float, double>(const float*, int64_t, int, const double*, int, int64_t, double*, int64_t, cudaStream_t);
 template az_status launch_tsprod<double, double>(const double*, int64_t, int, const double*, int, int64_t, double*, int64_t, cudaStream_t);
 template az_status launch_tsprod<double, float>(const double*, int64_t, int, const double*, int, int64_t, float*, int64_t, cudaStream_t);
-template az_status launch_update_x<float, float>(const float*, int64_t, int, const double*, const float*, int64_t, int64_t, int, double*, int64_t, bool, cudaStream_t);
-template az_status launch_update_x<double, double>(const double*, int64_t, int, const double*, const double*, int64_t, int64_t, int, double*, int64_t, bool, cudaStream_t);
+template az_status launch_tsprod<float, float>(const float*, int64_t, int, const double*, int, int64_t, float*, int64_t, cudaStream_t);
+template az_status launch_update_x<float, float>(const float*, int64_t, int, const double*, const float*, int64_t, int64_t, int, double*, int64_t, bool, cudaStream_t, float*);
+template az_status launch_update_x<double, double>(const double*, int64_t, int, const double*, const double*, int64_t, int64_t, int, double*, int64_t, bool, cudaStream_t, float*);
 
 }  // namespace az

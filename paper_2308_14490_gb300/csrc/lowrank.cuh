@@ -22,11 +22,15 @@ struct FactorInfo {
 int gram_blocks(int64_t M);
 template <typename TA, typename TB>
 az_status launch_gram(const TA* A, int64_t lda, int ka, const TB* B, int64_t ldb, int kb, int64_t M,
-                      double* partial, double* G, cudaStream_t st);
+                      double* partial, double* G, cudaStream_t st, bool fast = false);
 // out[M x r] = A[M x k] * S[k x r] (S FP64, column-major ld k), FP64 accumulation.
 template <typename TA, typename TO>
 az_status launch_tsprod(const TA* A, int64_t lda, int k, const double* S, int r, int64_t M, TO* out, int64_t ldo,
                         cudaStream_t st);
+// out[M x r] = A[M x k] S (A FP32, S FP64) with double-float accumulation (r <= 32)
+template <typename TO>
+az_status launch_tsprod_df(const float* A, int64_t lda, int k, const double* S, int r, int64_t M, TO* out, int64_t ldo,
+                           cudaStream_t st);
 // First pass: eigen-decomposition of G1 (k x k) by one-sided Jacobi; keeps
 // lambda_i > taug^2 lambda_1 (and above the rounding floor); writes
 // B1 = V_keep Lambda^{-1/2} (k x k, zero columns beyond r1) and V, lambda.
@@ -42,6 +46,6 @@ az_status launch_small_mm(const double* VS, int k, const double* c, int n, doubl
 // x[:, c] = (accumulate ? x : 0) + z[:, c] + W u[:, c]  (N rows)
 template <typename TW, typename TZ>
 az_status launch_update_x(const TW* W, int64_t ldw, int k, const double* u, const TZ* z, int64_t ldz, int64_t N,
-                          int nrhs, double* x, int64_t ldx, bool accumulate, cudaStream_t st);
+                          int nrhs, double* x, int64_t ldx, bool accumulate, cudaStream_t st, float* xf = nullptr);
 
 }  // namespace az
