@@ -86,6 +86,7 @@ typedef struct {
   double sigma_max;     /* largest singular value of the sketch Y */
   double sigma_min_kept;/* smallest kept singular value */
   size_t device_bytes;  /* bytes held by the handle */
+  int32_t jacobi_sweeps;/* sweeps taken by the small factor's one-sided Jacobi SVD */
 } az_info_t;
 
 /* Build a solver for one problem.  (Sec. 3.2.3 "Step 0" and step 1's sketch.)

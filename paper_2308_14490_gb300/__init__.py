@@ -37,7 +37,8 @@ class az_info_t(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64), ("L", ctypes.c_int64), ("M", ctypes.c_int64), ("Mb", ctypes.c_int64),
                 ("k", ctypes.c_int32), ("rank", ctypes.c_int32), ("rank_gram", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("sigma_max", ctypes.c_double),
-                ("sigma_min_kept", ctypes.c_double), ("device_bytes", ctypes.c_size_t)]
+                ("sigma_min_kept", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
+                ("jacobi_sweeps", ctypes.c_int32)]
 
 
 _P = ctypes.c_void_p

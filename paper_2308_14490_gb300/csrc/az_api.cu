@@ -408,7 +408,7 @@ az_status sketch_and_factor(az_setup_t* h, cudaStream_t st) {
     float* Q1f = (float*)h->Q1;
     AZ_TRY(launch_tsprod_df<float>((const float*)Y, h->Mtot, k, h->B1, k, h->Mtot, Q1f, h->Mtot, st));
     AZ_TRY((launch_gram<float, float>(Q1f, h->Mtot, k, Q1f, h->Mtot, k, h->Mtot, h->partial, h->G, st, true)));
-    AZ_TRY(launch_factor2(h->G, k, h->V, h->lam, h->tau_svd, h->floor, h->Tm, h->VS, h->sig, h->info, st));
+    AZ_TRY(launch_factor2(h->G, k, h->V, h->lam, h->tau_svd, h->floor, h->Tm, h->VS, h->sig, h->info, st, true));
     AZ_TRY((launch_tsprod<float, float>(Q1f, h->Mtot, k, h->Tm, k, h->Mtot, (float*)h->Ut, h->Mtot, st)));
   }
   return AZ_OK;
@@ -742,6 +742,7 @@ az_status az_get_info(az_handle h, az_info_t* info) {
   info->rank = fi.r; info->rank_gram = fi.r1; info->precision = h->precision;
   info->sigma_max = fi.sigma_max; info->sigma_min_kept = fi.sigma_min_kept;
   info->device_bytes = h->bytes;
+  info->jacobi_sweeps = fi.pad;
   return AZ_OK;
 }
 

@@ -12,6 +12,7 @@
 // (formed as Q1 T with T = R2^{-1} U_R[:, :r]) and VS = V_r1 V_R[:, :r]
 // Sigma^{-1}, so that u = VS U_tau^T g.
 #include <cmath>
+#include <type_traits>
 #include "lowrank.cuh"
 #include "profile.cuh"
 
@@ -266,33 +267,46 @@ az_status launch_tsprod_df(const float* A, int64_t lda, int k, const double* S, 
 }
 template az_status launch_tsprod_df<float>(const float*, int64_t, int, const double*, int, int64_t, float*, int64_t, cudaStream_t);
 
-// out = A * S : thread per (row, output column), S in shared memory.
-template <typename TA, typename TO>
-__global__ void k_tsprod(const TA* __restrict__ A, int64_t lda, int k, const double* __restrict__ S, int r, int64_t M,
-                         TO* __restrict__ out, int64_t ldo) {
+// out = A * S : thread per row, S (k x r) in shared memory, r <= KB outputs
+// accumulated in registers (FP64 for FP64 inputs, else FP32).
+template <typename TA, typename TO, int KB>
+__global__ void __launch_bounds__(128) k_tsprod(const TA* __restrict__ A, int64_t lda, int k, const double* __restrict__ S,
+                                                int r, int64_t M, TO* __restrict__ out, int64_t ldo) {
+  using TC = typename std::conditional<sizeof(TA) == 8, double, float>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* sS = (double*)smem_raw;
-  for (int t = threadIdx.x; t < k * r; t += blockDim.x) sS[t] = S[(t / r) + (int64_t)(t % r) * k] ;  // sS[a*r + c] = S[a, c]
-  __syncthreads();
-  int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= M) return;
-  double acc[64];
-  const int rr = min(r, 64);
-  for (int c = 0; c < rr; ++c) acc[c] = 0.0;
-  for (int a = 0; a < k; ++a) {
-    double v = (double)A[(int64_t)a * lda + m];
-    for (int c = 0; c < rr; ++c) acc[c] = fma(v, sS[a * r + c], acc[c]);
+  TC* sS = (TC*)smem_raw;   // sS[a*KB + c] = S[a, c]
+  for (int t = threadIdx.x; t < k * KB; t += blockDim.x) {
+    const int a = t / KB, c = t % KB;
+    sS[t] = c < r ? (TC)S[a + (int64_t)c * k] : (TC)0;
   }
-  for (int c = 0; c < rr; ++c) out[(int64_t)c * ldo + m] = (TO)acc[c];
+  __syncthreads();
+  const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  TC acc[KB];
+#pragma unroll
+  for (int c = 0; c < KB; ++c) acc[c] = 0;
+  for (int a = 0; a < k; ++a) {
+    const TC v = (TC)A[(int64_t)a * lda + m];
+#pragma unroll
+    for (int c = 0; c < KB; ++c) acc[c] = fma(v, sS[a * KB + c], acc[c]);
+  }
+#pragma unroll
+  for (int c = 0; c < KB; ++c)
+    if (c < r) out[(int64_t)c * ldo + m] = (TO)acc[c];
 }
 template <typename TA, typename TO>
 az_status launch_tsprod(const TA* A, int64_t lda, int k, const double* S, int r, int64_t M, TO* out, int64_t ldo,
                         cudaStream_t st) {
-  if (r > 64) { set_error("tsprod: r > 64 not supported by this kernel"); return AZ_ERR_ARG; }
-  size_t sm = (size_t)k * r * sizeof(double);
-  if (sm > 48 * 1024) cudaFuncSetAttribute(k_tsprod<TA, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  using TC = typename std::conditional<sizeof(TA) == 8, double, float>::type;
   ProfScope ps("tsprod", (double)M * (k * sizeof(TA) + r * sizeof(TO)), st);
-  k_tsprod<TA, TO><<<(unsigned)((M + 127) / 128), 128, sm, st>>>(A, lda, k, S, r, M, out, ldo);
+  const unsigned grid = (unsigned)((M + 127) / 128);
+  if (r <= 16) k_tsprod<TA, TO, 16><<<grid, 128, (size_t)k * 16 * sizeof(TC), st>>>(A, lda, k, S, r, M, out, ldo);
+  else if (r <= 32) k_tsprod<TA, TO, 32><<<grid, 128, (size_t)k * 32 * sizeof(TC), st>>>(A, lda, k, S, r, M, out, ldo);
+  else if (r <= 64) {
+    size_t sm = (size_t)k * 64 * sizeof(TC);
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_tsprod<TA, TO, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_tsprod<TA, TO, 64><<<grid, 128, sm, st>>>(A, lda, k, S, r, M, out, ldo);
+  } else { set_error("tsprod: r > 64 not supported by this kernel"); return AZ_ERR_ARG; }
   AZ_LCHECK();
   return AZ_OK;
 }
@@ -303,14 +317,15 @@ az_status launch_tsprod(const TA* A, int64_t lda, int k, const double* S, int r,
 // orthogonal; V (n x n) accumulates the rotations.  Round-robin pair order, one
 // warp per pair.  After convergence column j has norm sigma_j and
 // a[:, j] / sigma_j is the left singular vector.
-__device__ int jacobi_onesided(double* a, int m, int n, double* V, int* flag, double floor_rel) {
+template <typename TJ>
+__device__ int jacobi_onesided(TJ* a, int m, int n, TJ* V, int* flag, double floor_rel) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  __shared__ double fro2;
+  __shared__ TJ fro2;
   // identity V; ||a||_F^2 is invariant under the rotations and sets the level
   // below which column pairs are rounding noise and are left alone
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) V[t] = (t % n == t / n) ? 1.0 : 0.0;
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) V[t] = (t % n == t / n) ? (TJ)1 : (TJ)0;
   if (threadIdx.x == 0) {
-    double f = 0;
+    TJ f = 0;
     for (int t = 0; t < m * n; ++t) f += a[t] * a[t];
     fro2 = f;
   }
@@ -318,9 +333,11 @@ __device__ int jacobi_onesided(double* a, int m, int n, double* V, int* flag, do
   // a pair is orthogonal to working precision once |gamma| is below the
   // rounding level of the larger column against the whole matrix (floor_rel;
   // 0 = plain relative criterion)
-  const double fro = sqrt(fro2);
-  // relative orthogonality reachable by an m-term FP64 dot product
-  const double reltol = fmax(1e-15, 2.3e-16 * m);
+  const TJ fro = sqrt(fro2);
+  // relative orthogonality reachable by an m-term dot product in TJ
+  const TJ ueps = sizeof(TJ) == 8 ? (TJ)1.1e-16 : (TJ)6e-8;
+  const TJ reltol = fmax((TJ)(10 * ueps), (TJ)(2 * m) * ueps);
+  const TJ flr = (TJ)floor_rel;
   const int nn = (n + 1) & ~1;  // even count for round-robin (a dummy column if n odd)
   int sweeps = 0;
   for (int sweep = 0; sweep < 30; ++sweep) {
@@ -335,9 +352,9 @@ __device__ int jacobi_onesided(double* a, int m, int n, double* V, int* flag, do
         int i = idx(p0), j = idx(p1);
         if (i > j) { int tt = i; i = j; j = tt; }
         if (j >= n) continue;
-        double al = 0, be = 0, ga = 0;
+        TJ al = 0, be = 0, ga = 0;
         for (int r = lane; r < m; r += 32) {
-          double x = a[i * m + r], y = a[j * m + r];
+          TJ x = a[i * m + r], y = a[j * m + r];
           al += x * x; be += y * y; ga += x * y;
         }
         for (int o = 16; o > 0; o >>= 1) {
@@ -345,17 +362,17 @@ __device__ int jacobi_onesided(double* a, int m, int n, double* V, int* flag, do
           be += __shfl_xor_sync(0xffffffffu, be, o);
           ga += __shfl_xor_sync(0xffffffffu, ga, o);
         }
-        if (fabs(ga) > floor_rel * fro * sqrt(fmax(al, be)) && fabs(ga) > reltol * sqrt(al * be)) {
-          double zeta = (be - al) / (2.0 * ga);
-          double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+        if (fabs(ga) > flr * fro * sqrt(fmax(al, be)) && fabs(ga) > reltol * sqrt(al * be)) {
+          TJ zeta = (be - al) / ((TJ)2 * ga);
+          TJ t = (zeta >= 0 ? (TJ)1 : (TJ)-1) / (fabs(zeta) + sqrt((TJ)1 + zeta * zeta));
+          TJ c = (TJ)1 / sqrt((TJ)1 + t * t), s = c * t;
           for (int r = lane; r < m; r += 32) {
-            double x = a[i * m + r], y = a[j * m + r];
+            TJ x = a[i * m + r], y = a[j * m + r];
             a[i * m + r] = c * x - s * y;
             a[j * m + r] = s * x + c * y;
           }
           for (int r = lane; r < n; r += 32) {
-            double x = V[i * n + r], y = V[j * n + r];
+            TJ x = V[i * n + r], y = V[j * n + r];
             V[i * n + r] = c * x - s * y;
             V[j * n + r] = s * x + c * y;
           }
@@ -470,7 +487,7 @@ az_status launch_factor1(const double* G1, int k, double taug, double floor2, do
 // tau sigma_1, > floor); T = R2^{-1} U_R[:, :r] (so U_tau = Q1 T) and
 // VS = V_R[:, :r] Sigma^{-1}; both k x k with zero columns beyond r.
 __global__ void k_factor2(const double* __restrict__ G2, int k, const double* __restrict__ R1P,
-                          double tau, double floor, double* T, double* VS, double* sig, FactorInfo* info) {
+                          double tau, double floor, double* T, double* VS, double* sig, FactorInfo* info, int f32jac) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* R = (double*)smem_raw;   // r1 x r1 Cholesky factor (upper), column-major ld k
   double* A = R + k * k;           // Rs^T: k x r1, column-major ld k
@@ -503,15 +520,29 @@ __global__ void k_factor2(const double* __restrict__ G2, int k, const double* __
     }
     __syncthreads();
   }
-  // A = Rs^T = R1P^T R2^T : A[c, i] = sum_l R1P[l, c] R2[i, l]  (l <= i)
+  // A = Rs^T = R1P^T R2^T : A[c, i] = sum_{l >= i} R1P[l, c] R2[i, l]  (R2 upper)
   for (int t = threadIdx.x; t < k * r1; t += blockDim.x) {
     const int c = t % k, i = t / k;
     double sacc = 0.0;
-    for (int l = 0; l <= i; ++l) sacc += R1P[(int64_t)c * k + l] * R[i * k + l];
+    for (int l = i; l < r1; ++l) sacc += R1P[(int64_t)c * k + l] * R[l * k + i];
     A[i * k + c] = sacc;
   }
   __syncthreads();
-  const int sw = jacobi_onesided(A, k, r1, VR, &flag, 1e-14);
+  int sw;
+  if (f32jac) {
+    // mixed path: Rs is only FP32-accurate (its inputs are), so its SVD is
+    // taken in FP32 and widened back
+    float* Af = (float*)(sg + k);
+    float* Vf = Af + k * k;
+    for (int t = threadIdx.x; t < k * r1; t += blockDim.x) Af[t] = (float)A[t];
+    __syncthreads();
+    sw = jacobi_onesided<float>(Af, k, r1, Vf, &flag, 0.0);
+    for (int t = threadIdx.x; t < k * r1; t += blockDim.x) A[t] = (double)Af[t];
+    for (int t = threadIdx.x; t < r1 * r1; t += blockDim.x) VR[t] = (double)Vf[t];
+    __syncthreads();
+  } else {
+    sw = jacobi_onesided<double>(A, k, r1, VR, &flag, 0.0);
+  }
   if (threadIdx.x == 0) info->pad = sw;
   // sort by decreasing norm (columns of A of length k, rotations VR of length r1)
   for (int j = threadIdx.x; j < r1; j += blockDim.x) {
@@ -564,13 +595,13 @@ __global__ void k_factor2(const double* __restrict__ G2, int k, const double* __
   for (int t = threadIdx.x; t < k; t += blockDim.x) sig[t] = t < r1 ? sg[t] : 0.0;
 }
 az_status launch_factor2(const double* G2, int k, const double* V, const double* lam, double tau, double floor,
-                         double* T, double* VS, double* sig, FactorInfo* info, cudaStream_t st) {
+                         double* T, double* VS, double* sig, FactorInfo* info, cudaStream_t st, bool f32jac) {
   if (k > 64) { set_error("factor: k > 64 not supported by the one-CTA factorisation"); return AZ_ERR_ARG; }
-  size_t sm = (3 * (size_t)k * k + k) * sizeof(double);
+  size_t sm = (3 * (size_t)k * k + k) * sizeof(double) + 2 * (size_t)k * k * sizeof(float);
   if (sm > 48 * 1024) cudaFuncSetAttribute(k_factor2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   ProfScope ps("factor2", 0.0, st);
   (void)lam;
-  k_factor2<<<1, 32 * std::max(1, std::min(32, (k + 1) / 2)), sm, st>>>(G2, k, V, tau, floor, T, VS, sig, info);
+  k_factor2<<<1, 32 * std::max(1, std::min(32, (k + 1) / 2)), sm, st>>>(G2, k, V, tau, floor, T, VS, sig, info, f32jac ? 1 : 0);
   AZ_LCHECK();
   return AZ_OK;
 }

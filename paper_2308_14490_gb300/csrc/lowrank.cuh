@@ -40,7 +40,7 @@ az_status launch_factor1(const double* G1, int k, double taug, double floor2, do
 // rank r = #(sigma > tau sigma_1, > floor); T = R2^{-1} U_R[:, :r] (k x k, zero
 // beyond r), VS = V_keep V_R[:, :r] Sigma^{-1} (k x k, zero beyond r), sigma.
 az_status launch_factor2(const double* G2, int k, const double* V, const double* lam, double tau, double floor,
-                         double* T, double* VS, double* sig, FactorInfo* info, cudaStream_t st);
+                         double* T, double* VS, double* sig, FactorInfo* info, cudaStream_t st, bool f32jac = false);
 // u[k x n] = VS[k x k] c[k x n]
 az_status launch_small_mm(const double* VS, int k, const double* c, int n, double* u, cudaStream_t st);
 // x[:, c] = (accumulate ? x : 0) + z[:, c] + W u[:, c]  (N rows)

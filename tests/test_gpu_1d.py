@@ -117,7 +117,7 @@ def test_solve_fp64_relres_parity(az, p):
     ref = AZ(op, p.k, 7, 1e-8)
     r_o = relres(op, ref.solve(b), b)
     r_g = relres(op, xg, b)
-    assert np.all(np.abs(r_g - r_o) <= 1e-10), (r_g, r_o)
+    assert np.all(np.abs(r_g - r_o) <= 1e-10), (r_g.tolist(), r_o.tolist(), (r_g - r_o).tolist())
     assert np.allclose(rr, r_g, rtol=1e-9, atol=1e-15)
 
 
