@@ -168,6 +168,22 @@ const char* az_last_error(void);
  * seed high), bit (row % 32) of word ((row % 128)/32), set = +1. */
 az_status az_rademacher(int64_t N, int32_t k, uint64_t seed, double* R_dev, void* stream);
 
+/* az_rademacher without any device allocation, for callers that cannot call
+ * cudaMalloc: for example a serving process whose caching allocator already
+ * holds the free device memory (a fresh cudaMalloc would fail or force the
+ * cache to be released), or code on a latency-critical path where cudaMalloc
+ * and cudaFree may synchronise the device.  The paper has no counterpart; it is
+ * a deployment variant of az_rademacher with identical output.
+ *   Scratch: a fixed 4 MiB device array inside the library (kept by every GPU
+ *   that loads it until the process exits).  Limit: k * ceil(N/32) <= 2^20,
+ *   i.e. at most 2^25 entries of R; larger sizes return AZ_ERR_ARG.
+ *   The first call on each device (with that device current) looks up the
+ *   array's device address once; make that first call before any stream
+ *   capture.  All calls share the one array, so calls that overlap on the GPU
+ *   (different streams or threads without ordering) race on it and must be
+ *   serialised by the caller.  Stream-ordered, no synchronisation. */
+az_status az_rademacher_noalloc(int64_t N, int32_t k, uint64_t seed, double* R_dev, void* stream);
+
 /* Recompute every setup step (index map, symbol, test matrix with a new
  * seed, sketch, factorisation) on an existing handle, on `stream`, without
  * allocating and without synchronising.  A factorisation breakdown is reported

@@ -61,6 +61,7 @@ _SIGS = {
     "az_last_error": [],
     "az_rademacher": [_I64, _I32, ctypes.c_uint64, _P, _P],
     "az_refactor": [_P, ctypes.c_uint64, _P],
+    "az_rademacher_noalloc": [_I64, _I32, ctypes.c_uint64, _P, _P],
     "az_launch_count": [],
     "az_profile_begin": [],
     "az_profile_end": [],
@@ -177,6 +178,12 @@ def az_destroy(h):
 def az_rademacher(N, k, seed, R, stream=None):
     """R: (k, N) float64 CUDA tensor (column j of the matrix is row j of the tensor)."""
     _check(_lib.az_rademacher(int(N), int(k), int(seed), _ptr(R), _stream(stream)), "az_rademacher")
+
+
+def az_rademacher_noalloc(N, k, seed, R, stream=None):
+    """Same output as az_rademacher, but uses the library's fixed device scratch
+    instead of allocating (for callers that cannot allocate device memory)."""
+    _check(_lib.az_rademacher_noalloc(int(N), int(k), int(seed), _ptr(R), _stream(stream)), "az_rademacher_noalloc")
 
 
 def az_last_error():

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libaz.so")
-SOURCES = ["kernels.cu", "lowrank.cu", "az_api.cu", "profile.cu"]
+SOURCES = ["kernels.cu", "lowrank.cu", "az_api.cu", "profile.cu", "noalloc.cu"]
 HEADERS = ["az_internal.cuh", "fft.cuh", "kernels.cuh", "lowrank.cuh", "profile.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
