@@ -252,15 +252,16 @@ az_status launch_tsprod_df(const float* A, int64_t lda, int k, const double* S, 
                            cudaStream_t st) {
   ProfScope ps("tsprod_df32", (double)M * (k * 4 + r * sizeof(TO)), st);
   const unsigned grid = (unsigned)((M + 127) / 128);
-  if (r <= 16) {
-    size_t sm = 2 * (size_t)k * 16 * sizeof(float);
-    k_tsprod_df<TO, 16><<<grid, 128, sm, st>>>(A, lda, k, S, r, M, out, ldo);
-  } else if (r <= 32) {
-    size_t sm = 2 * (size_t)k * 32 * sizeof(float);
-    k_tsprod_df<TO, 32><<<grid, 128, sm, st>>>(A, lda, k, S, r, M, out, ldo);
-  } else {
-    set_error("tsprod_df: r > 32 not supported by this kernel");
-    return AZ_ERR_ARG;
+  // output columns in chunks of at most 32 (double-float accumulators in registers)
+  for (int c0 = 0; c0 < r; c0 += 32) {
+    const int rc = std::min(32, r - c0);
+    const double* Sc = S + (int64_t)c0 * k;
+    TO* oc = out + (int64_t)c0 * ldo;
+    if (rc <= 16) {
+      k_tsprod_df<TO, 16><<<grid, 128, 2 * (size_t)k * 16 * sizeof(float), st>>>(A, lda, k, Sc, rc, M, oc, ldo);
+    } else {
+      k_tsprod_df<TO, 32><<<grid, 128, 2 * (size_t)k * 32 * sizeof(float), st>>>(A, lda, k, Sc, rc, M, oc, ldo);
+    }
   }
   AZ_LCHECK();
   return AZ_OK;
