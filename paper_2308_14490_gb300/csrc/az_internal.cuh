@@ -42,6 +42,58 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
   return c;
 }
 
+// ---------------------------------------------------------------- FP64 <-> FP32 on the integer pipe
+// GB300 runs FP64 arithmetic and FP64 conversions at a small fraction of the
+// FP32 rate; the mixed path converts its FP64 inputs/outputs with integer bit
+// manipulation instead.  Values outside the FP32 normal range fall back to the
+// hardware conversion.
+__device__ __forceinline__ float d2f_int(double d) {   // round to nearest even
+  const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+  const unsigned sign = (unsigned)(u >> 63);
+  const int e = (int)((u >> 52) & 0x7ff);
+  const unsigned long long m = u & 0xFFFFFFFFFFFFFull;
+  if (e == 0) return sign ? -0.0f : 0.0f;
+  int fe = e - 1023 + 127;
+  if (fe <= 0 || fe >= 254) return (float)d;
+  unsigned mant = (unsigned)(m >> 29);
+  const unsigned rem = (unsigned)(m & 0x1FFFFFFFull);
+  if (rem > 0x10000000u || (rem == 0x10000000u && (mant & 1u))) {
+    if (++mant == 0x800000u) { mant = 0; ++fe; }
+  }
+  return __uint_as_float((sign << 31) | ((unsigned)fe << 23) | mant);
+}
+__device__ __forceinline__ double f2d_int(float f) {   // exact
+  const unsigned u = __float_as_uint(f);
+  const unsigned fe = (u >> 23) & 0xff;
+  if (fe == 0 || fe == 0xff) return (double)f;   // zero, subnormal, inf, nan
+  const unsigned long long e = (unsigned long long)(fe - 127 + 1023);
+  return __longlong_as_double((long long)(((unsigned long long)(u >> 31) << 63) | (e << 52) |
+                                          ((unsigned long long)(u & 0x7fffff) << 29)));
+}
+// d = hi + lo with hi = d2f_int(d) and lo = the FP32-rounded remainder (exact
+// split up to 2^-48 relative), integer pipe only
+__device__ __forceinline__ void d2ff_int(double d, float& hi, float& lo) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+  const int e = (int)((u >> 52) & 0x7ff);
+  if (e == 0 || e - 1023 + 127 <= 52 || e - 1023 + 127 >= 254) {
+    hi = (float)d;
+    lo = (float)(d - (double)hi);
+    return;
+  }
+  // hi: truncated to 24 significant bits; lo: the remaining 29 bits, rounded
+  const unsigned sign = (unsigned)(u >> 63);
+  const unsigned long long m = u & 0xFFFFFFFFFFFFFull;
+  const int fe = e - 1023 + 127;
+  hi = __uint_as_float((sign << 31) | ((unsigned)fe << 23) | (unsigned)(m >> 29));
+  const unsigned rem = (unsigned)(m & 0x1FFFFFFFull);   // value rem * 2^(e - 1023 - 52)
+  const float lf = (float)rem;                           // exact up to rounding to 24 bits
+  lo = __fmul_rn(sign ? -lf : lf, __uint_as_float((unsigned)(fe - 52) << 23));
+}
+
+template <typename TO, typename TI> __device__ __forceinline__ TO cvt(TI v) { return (TO)v; }
+template <> __device__ __forceinline__ float cvt<float, double>(double v) { return d2f_int(v); }
+template <> __device__ __forceinline__ double cvt<double, float>(float v) { return f2d_int(v); }
+
 // floor division for possibly negative numerators (positive divisor)
 __host__ __device__ __forceinline__ int64_t fdiv(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 __host__ __device__ __forceinline__ int64_t fmod_pos(int64_t a, int64_t b) { int64_t r = a % b; return r < 0 ? r + b : r; }

@@ -127,7 +127,9 @@ __global__ void k_samples(double* g, int64_t L, double hL, double eps, int deriv
   double e2 = eps * eps, acc = 0.0;
   for (int p = -pimg; p <= pimg; ++p) {
     double r = (mm + (double)p * (double)L) * hL;
-    double ex = exp(-e2 * r * r);
+    const double q = e2 * r * r;
+    if (q > 760.0) continue;   // exp(-q) underflows to zero in FP64
+    double ex = exp(-q);
     acc += deriv == 0 ? ex : -2.0 * e2 * ex * (1.0 - 2.0 * e2 * r * r);
   }
   g[m] = acc;
@@ -629,8 +631,8 @@ __global__ void __launch_bounds__(256) k_stencil_rows(Geom g, int kind, T inv2e2
   for (int c = 0; c < CPT; ++c) {
     if (c < nc) {
       T r = beta * acc[c];
-      if (bb) r += alpha * (T)bb[(int64_t)(cbase + c) * ldb + m];
-      outb[(int64_t)(cbase + c) * ldo + m] = (TO)r;
+      if (bb) r += alpha * cvt<T>(bb[(int64_t)(cbase + c) * ldb + m]);
+      outb[(int64_t)(cbase + c) * ldo + m] = cvt<TO>(r);
     }
   }
 }
@@ -733,9 +735,19 @@ __global__ void __launch_bounds__(256) k_resid_df(Geom g, int kind, double inv2e
 #pragma unroll
   for (int c = 0; c < CPT; ++c) {
     if (c < nc) {
-      double ax = (double)acc[c].hi + (double)acc[c].lo;
-      if (g.dim == 2 && kind == 1) ax = -ax * inv2e2;
-      out[(int64_t)(cbase + c) * ldo + m] = (float)(bb[(int64_t)(cbase + c) * ldb + m] - ax);
+      const double bv = bb[(int64_t)(cbase + c) * ldb + m];
+      if (g.dim == 2 && kind == 1) {
+        double ax = -((double)acc[c].hi + (double)acc[c].lo) * inv2e2;
+        out[(int64_t)(cbase + c) * ldo + m] = (float)(bv - ax);
+      } else {
+        // r = (bh + bl) - (hi + lo) with a two-difference on the leading terms
+        float bh, bl;
+        d2ff_int(bv, bh, bl);
+        const float sd = bh - acc[c].hi;
+        const float bz = sd - bh;
+        const float er = (bh - (sd - bz)) + (-acc[c].hi - bz);
+        out[(int64_t)(cbase + c) * ldo + m] = sd + (er + (bl - acc[c].lo));
+      }
     }
   }
 }
@@ -1003,12 +1015,20 @@ az_status launch_sumsq_cols(const double* v, int64_t ld, int64_t rows, int ncols
 // Same three passes as above, with the FFT held in registers (E values per
 // thread) and one padded shared buffer; used whenever every FFT length of the
 // pass is >= E.  E = 16 (FP32) or 8 (FP64).
-template <typename T> struct EPT { static constexpr int E = sizeof(T) == 4 ? 16 : 8; };
-// CTA size of the register passes: 256 threads and 3 CTAs per SM (80
-// registers) keep the load, compute and store phases of different CTAs
-// overlapped without spilling the 16 values a thread holds.
+// Values per thread (FP32 / FP64) and CTA shape of the register passes:
+// 256 threads and 3 CTAs per SM (80 registers) keep the load, compute and
+// store phases of different CTAs overlapped without spilling.
+#ifndef AZ_REG_E32
+#define AZ_REG_E32 16
+#endif
+#ifndef REG_THREADS
 #define REG_THREADS 256
+#endif
+#ifndef REG_MINB
 #define REG_MINB 3
+#endif
+#define PADC 4   // shared-memory padding: one element every 16 (column and row layouts)
+template <typename T> struct EPT { static constexpr int E = sizeof(T) == 4 ? AZ_REG_E32 : 8; };
 
 template <typename T, int MODE, typename TB>
 __global__ void __launch_bounds__(REG_THREADS, REG_MINB) k_colfwd_r(Geom g, const int32_t* __restrict__ pos2m, const TB* __restrict__ b,
@@ -1028,7 +1048,7 @@ __global__ void __launch_bounds__(REG_THREADS, REG_MINB) k_colfwd_r(Geom g, cons
   V* X1 = X1base + (int64_t)blockIdx.y * g.L;
   const V* twp = (const V*)tb.tw;
   // 2D sketch: y-stencil of R into a staging region after the FFT buffer
-  V* stg = sm + padix<5>(g.D0 << logC) + 32;
+  V* stg = sm + padix<PADC>(g.D0 << logC) + 32;
   if (MODE == 1 && g.dim == 2) {
     const int sy = g.s[1];
     const int Nym = (int)g.n[1] - 1, lNy = g.logn[1];
@@ -1079,27 +1099,27 @@ __global__ void __launch_bounds__(REG_THREADS, REG_MINB) k_colfwd_r(Geom g, cons
           }
         }
       }
-      sm[padix<5>(t)] = v;
+      sm[padix<PADC>(t)] = v;
     }
     __syncthreads();
   }
   const TB* bA = b ? b + (int64_t)colA * ldb : nullptr;
   const TB* bB = b ? b + (int64_t)colB * ldb : nullptr;
   auto pro = [&](int p) -> V {
-    if (MODE == 1) return sm[padix<5>((p << logC) + line)];
+    if (MODE == 1) return sm[padix<PADC>((p << logC) + line)];
     const int pos = (p << g.logD1) + n1;
     V v; v.x = 0; v.y = 0;
     const int m = __ldg(pos2m + pos);
     if (m < 0) return v;
-    v.x = (T)bA[m];
-    if (colB < ncols) v.y = (T)bB[m];
+    v.x = cvt<T>(bA[m]);
+    if (colB < ncols) v.y = cvt<T>(bB[m]);
     return v;
   };
   auto epi = [&](int k0, V v) {
     if (g.dim == 1 && k0 != 0 && n1 != 0) v = cmul(v, big_tw<V>((const V*)tb.bigA, (const V*)tb.bigB, n1 * k0, false));
     X1[(k0 << g.logD1) + n1] = v;
   };
-  fft_reg<V, E, false, 5>(sm, g.logD0, true, line, tl, 1, C, twp, TW_N >> g.logD0, pro, epi, MODE == 1);
+  fft_reg<V, E, false, PADC>(sm, g.logD0, true, line, tl, 1, C, twp, TW_N >> g.logD0, pro, epi, MODE == 1);
 }
 
 template <typename T, int E2>
@@ -1112,21 +1132,21 @@ __global__ void __launch_bounds__(REG_THREADS, REG_MINB) k_rowfold_r(Geom g, con
   const int GPB = 1 << logGPB;
   const int lognr = logGPB + g.logRg;
   V* smX = (V*)smem_raw;                                       // nrows x D1 (padded)
-  V* smF = smX + padix<4>(g.D1 << lognr) + 16;                // GPB x N1 (padded)
+  V* smF = smX + padix<PADC>(g.D1 << lognr) + 16;             // GPB x N1 (padded)
   const V* X1 = X1base + (int64_t)blockIdx.y * g.L;
   V* X3 = X3base + (int64_t)blockIdx.y * g.N;
   const int G0 = blockIdx.x * GPB;
   const V* twp = (const V*)tb.tw;
   // forward FFT of the rows: P1 = D1/E threads per row
   {
-    const int logP1 = g.logD1 - (E == 16 ? 4 : 3);
+    const int logP1 = g.logD1 - (E == 16 ? 4 : (E == 8 ? 3 : 2));
     const int lr = threadIdx.x >> logP1, tl = threadIdx.x & ((1 << logP1) - 1);
     const int gg = lr >> g.logRg, q = lr & (g.Rg - 1);
     const int row = G0 + gg + q * g.Rstride;
     const V* xr = X1 + ((int64_t)row << g.logD1);
     auto pro = [&](int p) -> V { return xr[p]; };
-    auto epi = [&](int o, V v) { smX[padix<4>((lr << g.logD1) + o)] = v; };
-    fft_reg<V, E, false, 4>(smX, g.logD1, true, lr, tl, g.D1, 1, twp, TW_N >> g.logD1, pro, epi);
+    auto epi = [&](int o, V v) { smX[padix<PADC>((lr << g.logD1) + o)] = v; };
+    fft_reg<V, E, false, PADC>(smX, g.logD1, true, lr, tl, g.D1, 1, twp, TW_N >> g.logD1, pro, epi);
   }
   __syncthreads();
   // fold (prologue of the inverse FFT of length N1, P2 = N1/E2 threads per line)
@@ -1144,7 +1164,7 @@ __global__ void __launch_bounds__(REG_THREADS, REG_MINB) k_rowfold_r(Geom g, con
         for (int p = 0; p < g.Fq; ++p) {
           const int kk = k1 + p * g.N1;
           const T hh = __ldg(hr + kk);
-          const V xv = smX[padix<4>((lr << g.logD1) + kk)];
+          const V xv = smX[padix<PADC>((lr << g.logD1) + kk)];
           ar += hh * xv.x; ai += hh * xv.y;
         }
       }
@@ -1155,7 +1175,7 @@ __global__ void __launch_bounds__(REG_THREADS, REG_MINB) k_rowfold_r(Geom g, con
       if (g.dim == 1 && k0 != 0 && n1 != 0) v = cmul(v, big_tw<V>((const V*)tb.bigNA, (const V*)tb.bigNB, n1 * k0, true));
       X3[(k0 << g.logN1) + n1] = v;
     };
-    fft_reg<V, E2, true, 4>(smF, g.logN1, true, gg, tl, g.N1, 1, twp, TW_N >> g.logN1, pro, epi);
+    fft_reg<V, E2, true, PADC>(smF, g.logN1, true, gg, tl, g.N1, 1, twp, TW_N >> g.logN1, pro, epi);
   }
 }
 
@@ -1189,7 +1209,7 @@ __global__ void __launch_bounds__(REG_THREADS, REG_MINB) k_colinv_r(Geom g, cons
     oA[j] = (TO)za;
     if (hasB) oB[j] = (TO)zb;
   };
-  fft_reg<V, E, true, 5>(sm, g.logG0, true, line, tl, 1, C, (const V*)tb.tw, TW_N >> g.logG0, pro, epi);
+  fft_reg<V, E, true, PADC>(sm, g.logG0, true, line, tl, 1, C, (const V*)tb.tw, TW_N >> g.logG0, pro, epi);
 }
 
 // Column count per CTA for the register passes: C * (n / E) threads <= 512.
@@ -1215,7 +1235,7 @@ az_status launch_colfwd_stencil(const Geom& g, const SketchIn<T>& in, int pair0,
   if (!reg_ok<T>(g)) return launch_colfwd_stencil_v1<T>(g, in, pair0, npairs, X1, tb, st);
   const int C = reg_cols<T>(g.D0, g.D1);
   const int threads = C * (g.D0 / EPT<T>::E);
-  size_t sm = ((size_t)padix_host(g.D0 * C, 5) + 32 + (g.dim == 2 ? (size_t)g.n[0] * C : 0)) * sizeof(V);
+  size_t sm = ((size_t)padix_host(g.D0 * C, PADC) + 32 + (g.dim == 2 ? (size_t)g.n[0] * C : 0)) * sizeof(V);
   auto kern = k_colfwd_r<T, 1, double>;
   if (set_smem(kern, sm) != cudaSuccess) { set_error("smem attribute"); return AZ_ERR_CUDA; }
   dim3 grid(g.D1 / C, npairs);
@@ -1232,7 +1252,7 @@ az_status launch_colfwd_gather(const Geom& g, const int32_t* pos2m, const TB* b,
   if (!reg_ok<T>(g)) return launch_colfwd_gather_v1<T, TB>(g, pos2m, b, ldb, ncols, pair0, npairs, X1, tb, st, M_rows);
   const int C = reg_cols<T>(g.D0, g.D1);
   const int threads = C * (g.D0 / EPT<T>::E);
-  size_t sm = ((size_t)padix_host(g.D0 * C, 5) + 32) * sizeof(V);
+  size_t sm = ((size_t)padix_host(g.D0 * C, PADC) + 32) * sizeof(V);
   auto kern = k_colfwd_r<T, 0, TB>;
   if (set_smem(kern, sm) != cudaSuccess) { set_error("smem attribute"); return AZ_ERR_CUDA; }
   dim3 grid(g.D1 / C, npairs);
@@ -1253,7 +1273,7 @@ az_status launch_rowfold(const Geom& g, const typename C2<T>::t* X1, const T* H,
   int GPB = 1;
   while (GPB * 2 * g.Rg * P1 <= REG_THREADS && g.G0 % (GPB * 2) == 0 && GPB * 2 <= 8) GPB *= 2;
   const int threads = GPB * g.Rg * P1;
-  size_t sm = ((size_t)padix_host(g.D1 * GPB * g.Rg, 4) + 16 + padix_host(g.N1 * GPB, 4) + 16) * sizeof(V);
+  size_t sm = ((size_t)padix_host(g.D1 * GPB * g.Rg, PADC) + 16 + padix_host(g.N1 * GPB, PADC) + 16) * sizeof(V);
   const int E2 = E / (g.Rg * g.Fq);
   dim3 grid(g.G0 / GPB, npairs);
   ProfScope ps(sizeof(T) == 4 ? "rowfold_f32" : "rowfold_f64", (double)npairs * (g.L + g.N) * sizeof(V) + (double)g.L * sizeof(T), st);
@@ -1281,7 +1301,7 @@ az_status launch_colinv(const Geom& g, const typename C2<T>::t* X3, int pair0, i
   if (!reg_ok<T>(g)) return launch_colinv_v1<T, TO>(g, X3, pair0, npairs, ncols, out, ldo, bits, nw, tb, st);
   const int C = reg_cols<T>(g.G0, g.N1);
   const int threads = C * (g.G0 / EPT<T>::E);
-  size_t sm = ((size_t)padix_host(g.G0 * C, 5) + 32) * sizeof(V);
+  size_t sm = ((size_t)padix_host(g.G0 * C, PADC) + 32) * sizeof(V);
   dim3 grid(g.N1 / C, npairs);
   ProfScope ps(sizeof(T) == 4 ? "colinv_f32" : "colinv_f64", (double)npairs * g.N * sizeof(V) + (double)std::min(ncols - 2 * pair0, 2 * npairs) * g.N * sizeof(TO), st);
   if (bits) {

@@ -65,12 +65,12 @@ template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile(
 // in flight while the current one is multiplied.  TS is the input type (no
 // conversion on the copy).
 template <typename TA, typename TB, typename TS, int RA, int RB, bool DFMODE>
-__global__ void __launch_bounds__(256) k_gram_partial(const TA* __restrict__ A, int64_t lda, int ka, const TB* __restrict__ B,
+__global__ void __launch_bounds__(512) k_gram_partial(const TA* __restrict__ A, int64_t lda, int ka, const TB* __restrict__ B,
                                                       int64_t ldb, int kb, int64_t M, double* __restrict__ partial, int sym) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TS* sbuf = (TS*)smem_raw;                       // 2 x GRAM_TILE x (ka + kb)
   const int tile_elems = GRAM_TILE * (ka + kb);
-  double* red = (double*)(sbuf + 2 * tile_elems);  // nsplit x nblk x RA*RB (reduction)
+  double* red = (double*)smem_raw;                 // nsplit x nblk x RA*RB (reduction; aliases the tiles)
   const int nta = (ka + RA - 1) / RA, ntb = (kb + RB - 1) / RB;
   const int nblkt = nta * ntb;
   const int nsplit = blockDim.x / nblkt;        // thread groups splitting each tile's rows
@@ -187,14 +187,14 @@ az_status launch_gram(const TA* A, int64_t lda, int ka, const TB* B, int64_t ldb
   const int npair = ka * kb;
   const int nthr = ((ka + RA - 1) / RA) * ((kb + RB - 1) / RB);
   if (nthr > 1024) { set_error("gram: too many columns for this kernel"); return AZ_ERR_ARG; }
-  const int nsplit = std::max(1, 256 / nthr);
+  const int nsplit = std::max(1, 512 / nthr);
   const int threads = nsplit * nthr;
   const int nblk = gram_blocks(M);
   const bool in32 = sizeof(TA) == 4 && sizeof(TB) == 4;
   const int sym = ((const void*)A == (const void*)B && ka == kb && lda == ldb) ? 1 : 0;
   const size_t ts = in32 ? sizeof(float) : sizeof(double);
   size_t sm = 2 * (size_t)GRAM_TILE * (ka + kb) * ts;
-  sm = (sm + 15) / 16 * 16 + (size_t)nsplit * nthr * RA * RB * sizeof(double);
+  sm = std::max(sm, (size_t)nsplit * nthr * RA * RB * sizeof(double));
   ProfScope ps(in32 ? (fast ? "proj_f32" : "gram_df32") : "gram_f64", (double)M * (ka * sizeof(TA) + kb * sizeof(TB)), st, 2);
   if (in32 && fast) {
     auto k = k_gram_partial<TA, TB, float, RA, RB, false>;
@@ -644,7 +644,8 @@ __global__ void __launch_bounds__(256) k_update_x(const TW* __restrict__ W, int6
 #pragma unroll
     for (int a = 0; a < KB; ++a) if (a < k) s = fma(w[a], uc[a], s);
     double* xp = x + (int64_t)c * ldx + j;
-    *xp = accumulate ? *xp + (double)s : (double)s;
+    const double sd = cvt<double>(s);
+    *xp = accumulate ? *xp + sd : sd;
     if (xf) xf[(int64_t)c * ldz + j] = (float)s;   // exact FP32 copy (may alias z)
   }
 }
