@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparator", action="store_true")
     ap.add_argument("--nrhs", type=int, default=NRHS, help="right-hand sides per step (default: the workload's 64)")
+    ap.add_argument("--serving-seconds", type=float, default=5.0,
+                    help="length of the serving-stream sample (Poisson arrivals, 200 req/s); 0 skips it")
     ap.add_argument("--lite", action="store_true",
                     help="timed steps only (no e2e, parity, comparator or CPU legs): the small case for profiler captures")
     return ap.parse_args()
@@ -227,6 +229,22 @@ def fp64_torch_comparator(p, b_dev, steps=2, warmup=1):
             "what": "same step (setup + 64 RHS) written in plain torch FP64 (torch.fft + torch.linalg.svd), no refinement"}, rel
 
 
+# --------------------------------------------------------------------------- serving sample
+def serving_leg(seconds):
+    """The mixed request stream: Poisson arrivals at 200/s of 1D / 2D approximations
+    and 2D Poisson collocations drawn from a seeded pool of 32 setups, 1..32 RHS
+    each, continuous batching over 4 streams with CUDA-graph replay."""
+    import paper_2308_14490_gb300.serving as S
+    pool = S.setup_pool(230814490, 32)
+    reqs = S.poisson_stream(230814490, 200.0, seconds, pool)
+    srv = S.Server(64 << 30, nslots=4)
+    out = srv.run(reqs, realtime=True)
+    srv.close()
+    out["stream"] = f"{len(reqs)} requests over {seconds:.0f} s (Poisson 200/s), pool of 32 setups; " \
+                    "2D setups use k <= 64 in this build"
+    return out
+
+
 # --------------------------------------------------------------------------- our arm
 def load_traffic():
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
@@ -373,6 +391,8 @@ def run_ours(args):
         except Exception as ex:  # the comparator is context, never the headline
             line["fp64_gpu_torch"] = {"error": str(ex)[:200]}
     az.az_destroy(h)
+    if rank == 0 and world == 1 and args.serving_seconds > 0:
+        line["serving"] = serving_leg(args.serving_seconds)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_leg()
     if rank == 0:

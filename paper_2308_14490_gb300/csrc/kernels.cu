@@ -3,6 +3,8 @@
 // local A-apply stencils (S4, S8, S11) and boundary rows (Sec. 6.2).
 #include <cmath>
 #include <algorithm>
+#include <mutex>
+#include <unordered_map>
 #include "kernels.cuh"
 #include "profile.cuh"
 #include "fft_reg.cuh"
@@ -13,10 +15,20 @@ static constexpr int TW_N = 4096;  // master twiddle table length
 static inline size_t padix_host(size_t e, int sh) { return e + (e >> sh); }
 
 // ------------------------------------------------------------------ utilities
+// Raise a kernel's dynamic shared-memory limit once per (kernel, size) so that
+// steady-state launches issue no attribute calls (solves can be captured into
+// CUDA graphs).
 template <typename K>
 static cudaError_t set_smem(K kernel, size_t bytes) {
   if (bytes <= 48 * 1024) return cudaSuccess;
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  static std::mutex mu;
+  static std::unordered_map<const void*, size_t> done;
+  std::lock_guard<std::mutex> g(mu);
+  auto it = done.find((const void*)kernel);
+  if (it != done.end() && it->second >= bytes) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) done[(const void*)kernel] = bytes;
+  return e;
 }
 #define AZ_LAUNCH_CHECK()                                               \
   do {                                                                  \

@@ -15,6 +15,22 @@
 #include <type_traits>
 #include "lowrank.cuh"
 #include "profile.cuh"
+#include <mutex>
+#include <unordered_map>
+
+namespace az {
+// once per (kernel, size): keeps steady-state launches free of attribute calls
+template <typename K> static void smem_once(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return;
+  static std::mutex mu;
+  static std::unordered_map<const void*, size_t> done;
+  std::lock_guard<std::mutex> g(mu);
+  auto it = done.find((const void*)kernel);
+  if (it != done.end() && it->second >= bytes) return;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess)
+    done[(const void*)kernel] = bytes;
+}
+}  // namespace az
 
 namespace az {
 
@@ -198,15 +214,15 @@ az_status launch_gram(const TA* A, int64_t lda, int ka, const TB* B, int64_t ldb
   ProfScope ps(in32 ? (fast ? "proj_f32" : "gram_df32") : "gram_f64", (double)M * (ka * sizeof(TA) + kb * sizeof(TB)), st, 2);
   if (in32 && fast) {
     auto k = k_gram_partial<TA, TB, float, RA, RB, false>;
-    if (sm > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    smem_once(k, sm);
     k<<<nblk, threads, sm, st>>>(A, lda, ka, B, ldb, kb, M, partial, sym);
   } else if (in32) {
     auto k = k_gram_partial<TA, TB, float, RA, RB, true>;
-    if (sm > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    smem_once(k, sm);
     k<<<nblk, threads, sm, st>>>(A, lda, ka, B, ldb, kb, M, partial, sym);
   } else {
     auto k = k_gram_partial<TA, TB, double, RA, RB, false>;
-    if (sm > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    smem_once(k, sm);
     k<<<nblk, threads, sm, st>>>(A, lda, ka, B, ldb, kb, M, partial, sym);
   }
   k_gram_reduce<<<(npair + 255) / 256, 256, 0, st>>>(partial, nblk, npair, ka, sym, RA, G);
@@ -305,7 +321,7 @@ az_status launch_tsprod(const TA* A, int64_t lda, int k, const double* S, int r,
   else if (r <= 32) k_tsprod<TA, TO, 32><<<grid, 128, (size_t)k * 32 * sizeof(TC), st>>>(A, lda, k, S, r, M, out, ldo);
   else if (r <= 64) {
     size_t sm = (size_t)k * 64 * sizeof(TC);
-    if (sm > 48 * 1024) cudaFuncSetAttribute(k_tsprod<TA, TO, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    smem_once(k_tsprod<TA, TO, 64>, sm);
     k_tsprod<TA, TO, 64><<<grid, 128, sm, st>>>(A, lda, k, S, r, M, out, ldo);
   } else { set_error("tsprod: r > 64 not supported by this kernel"); return AZ_ERR_ARG; }
   AZ_LCHECK();
@@ -474,7 +490,7 @@ az_status launch_factor1(const double* G1, int k, double taug, double floor2, do
                          FactorInfo* info, cudaStream_t st) {
   if (k > 64) { set_error("factor: k > 64 not supported by the one-CTA factorisation"); return AZ_ERR_ARG; }
   size_t sm = (2 * (size_t)k * k) * sizeof(double);
-  if (sm > 48 * 1024) cudaFuncSetAttribute(k_factor1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  smem_once(k_factor1, sm);
   ProfScope ps("factor1", 0.0, st);
   const double tol = fmax(taug * taug, 1e-15);
   k_factor1<<<1, 256, sm, st>>>(G1, k, tol, floor2, V, lam, B1, info);
@@ -599,7 +615,7 @@ az_status launch_factor2(const double* G2, int k, const double* V, const double*
                          double* T, double* VS, double* sig, FactorInfo* info, cudaStream_t st, bool f32jac) {
   if (k > 64) { set_error("factor: k > 64 not supported by the one-CTA factorisation"); return AZ_ERR_ARG; }
   size_t sm = (3 * (size_t)k * k + k) * sizeof(double) + 2 * (size_t)k * k * sizeof(float);
-  if (sm > 48 * 1024) cudaFuncSetAttribute(k_factor2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  smem_once(k_factor2, sm);
   ProfScope ps("factor2", 0.0, st);
   (void)lam;
   k_factor2<<<1, 32 * std::max(1, std::min(32, (k + 1) / 2)), sm, st>>>(G2, k, V, tau, floor, T, VS, sig, info, f32jac ? 1 : 0);

@@ -1,0 +1,332 @@
+"""Continuous-batching request loop for AZ solves (approximation and collocation).
+
+* Setups (grid, domain, kernel) are created on first use and kept resident
+  on the device -- symbols, index maps, sketch factors and workspace -- so
+  repeated right-hand sides only pay for az_solve / az_collocate.
+* Admission by device footprint: before a new setup is built its bytes are
+  estimated with az_query_footprint; least-recently-used idle setups are
+  evicted to fit the budget, and a setup that cannot fit is rejected
+  (AZ_ERR_ADMISSION semantics; the request is counted as rejected).
+* Continuous batching: queued requests for the same setup are merged into
+  one solve (their right-hand-side columns concatenated, padded to a bucket of
+  2/4/8/16/32/64 columns) and dispatched to a free slot as soon as one frees
+  up; each slot is its own CUDA stream, so batches of different setups overlap
+  on the device while new requests keep arriving.
+* Each (setup, bucket) solve is captured once into a CUDA graph and replayed.
+
+Right-hand sides are generated on the device from each request's seeded
+parameters (workload inputs, not solver arithmetic).
+"""
+from __future__ import annotations
+
+import collections
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import (AZ_ERR_ADMISSION, AZ_GAUSS, AZ_MIXED, AZ_NEG_LAPLACE_GAUSS, AZError, az_destroy, az_get_info,
+               az_query_footprint, az_setup, az_solve, make_grid, make_options)
+
+BUCKETS = (2, 4, 8, 16, 32, 64)
+
+
+@dataclass
+class SetupSpec:
+    """One problem: dim, centers per dim, oversampling, half-widths, domain."""
+    key: tuple
+    dim: int
+    n: tuple
+    s: tuple
+    T: tuple
+    kind: str                  # "approx" | "poisson"
+    mask_fn: object            # callable(grid coordinate arrays) -> bool mask
+    boundary: np.ndarray | None = None
+    weight: float = 10.0
+    k: int = 24
+    epsh: float = 1.0
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float             # seconds since the start of the run
+    spec: SetupSpec
+    nrhs: int
+    seed: int
+    t_done: float = -1.0
+    rejected: bool = False
+
+
+class _Setup:
+    def __init__(self, spec: SetupSpec, handle, info, device, coords, bnd):
+        self.spec = spec
+        self.h = handle
+        self.info = info
+        self.bytes = info["device_bytes"]
+        self.coords = coords       # (M, dim) kept points on the device
+        self.bnd = bnd             # (Mb, 2) boundary points or None
+        self.last_use = time.perf_counter()
+        self.inflight = 0
+        self.graphs = {}           # bucket -> (graph, b_buf, x_buf)
+
+
+class Server:
+    def __init__(self, budget_bytes: int, nslots: int = 4, use_graphs: bool = True, device=None,
+                 keep_results: bool = False):
+        self.dev = device or torch.device("cuda", torch.cuda.current_device())
+        self.setup_stream = torch.cuda.Stream(device=self.dev)
+        self.keep_results = keep_results
+        self.results = {}                  # rid -> (nrhs, N) solution columns (keep_results)
+        self.budget = int(budget_bytes)
+        self.used = 0
+        self.setups: dict = {}
+        self.queue: collections.OrderedDict = collections.OrderedDict()   # key -> deque of requests
+        self.slots = [torch.cuda.Stream(device=self.dev) for _ in range(nslots)]
+        self.slot_busy = [None] * nslots   # (event, setup, requests, x_buf, ncols) or None
+        self.use_graphs = use_graphs
+        self.rejections = 0
+        self.setup_builds = 0
+        self.evictions = 0
+        self.high_water = 0
+
+    # ------------------------------------------------------------------ setups
+    def _grid_coords(self, spec):
+        cs = []
+        for d in range(spec.dim):
+            L = spec.n[d] * spec.s[d]
+            cs.append(-spec.T[d] + np.arange(L) * (2 * spec.T[d] / L))
+        return cs
+
+    def _build(self, spec: SetupSpec):
+        opts = make_options(AZ_MIXED, spec.k, 1e-8, 0.0, 1, 1)
+        grid = make_grid(spec.dim, spec.n, spec.s, spec.T)
+        cs = self._grid_coords(spec)
+        if spec.dim == 1:
+            mask = spec.mask_fn(cs[0]).astype(np.uint8)
+            pts = cs[0][mask.astype(bool)][:, None]
+        else:
+            X, Y = np.meshgrid(cs[0], cs[1], indexing="ij")
+            mask = spec.mask_fn(X, Y).astype(np.uint8).reshape(-1)
+            sel = mask.astype(bool)
+            pts = np.stack([X.reshape(-1)[sel], Y.reshape(-1)[sel]], 1)
+        M = int(mask.sum())
+        nb = 0 if spec.boundary is None else len(spec.boundary)
+        need = az_query_footprint(grid, M, nb, opts, 64)
+        if need > self.budget:
+            return None
+        # evict least-recently-used idle setups until the new one fits
+        while self.used + need > self.budget:
+            idle = [s for s in self.setups.values() if s.inflight == 0]
+            if not idle:
+                return None
+            victim = min(idle, key=lambda s: s.last_use)
+            self._evict(victim)
+        mt = torch.from_numpy(mask).to(self.dev)
+        bnd = None
+        kernel = AZ_GAUSS
+        if spec.kind == "poisson":
+            kernel = AZ_NEG_LAPLACE_GAUSS
+            bnd = torch.from_numpy(np.ascontiguousarray(spec.boundary)).to(self.dev)
+        self.setup_stream.wait_stream(torch.cuda.current_stream(self.dev))
+        h = az_setup(grid, mt, spec.epsh / (2 * spec.T[0] / spec.n[0]), kernel, bnd, spec.weight, opts,
+                     self.setup_stream)
+        info = az_get_info(h)
+        st = _Setup(spec, h, info, self.dev, torch.from_numpy(pts).to(self.dev), bnd)
+        self.setups[spec.key] = st
+        self.used += st.bytes
+        self.setup_builds += 1
+        self.high_water = max(self.high_water, self.used)
+        return st
+
+    def _evict(self, st: _Setup):
+        st.graphs.clear()
+        az_destroy(st.h)
+        self.used -= st.bytes
+        del self.setups[st.spec.key]
+        self.evictions += 1
+
+    def close(self):
+        torch.cuda.synchronize(self.dev)
+        for st in list(self.setups.values()):
+            self._evict(st)
+
+    # ------------------------------------------------------------------ solves
+    def _rhs(self, st: _Setup, reqs, out):
+        """Fill out[:ncols] with each request's right-hand sides (cos(w.x + phi))."""
+        col = 0
+        for r in reqs:
+            g = np.random.default_rng(r.seed)
+            w = torch.from_numpy(g.uniform(1.0, 20.0, (r.nrhs, st.spec.dim))).to(self.dev)
+            ph = torch.from_numpy(g.uniform(0.0, 2 * math.pi, r.nrhs)).to(self.dev)
+            vals = torch.cos(st.coords @ w.T + ph[None, :])            # (M, nrhs)
+            if st.spec.kind == "poisson":
+                eps = st.spec.epsh / (2 * st.spec.T[0] / st.spec.n[0])
+                lap = (w * w).sum(1)                                     # -Lap cos = |w|^2 cos
+                interior = vals * lap[None, :] / (2 * eps * eps)
+                bvals = torch.cos(st.bnd @ w.T + ph[None, :]) * st.spec.weight
+                vals = torch.cat([interior, bvals], 0)
+            out[col:col + r.nrhs, :vals.shape[0]] = vals.T
+            col += r.nrhs
+        return col
+
+    def _solve_fn(self, st, b_buf, x_buf, stream):
+        az_solve(st.h, b_buf, x_buf, stream)
+
+    def _graph(self, st: _Setup, bucket: int, stream):
+        if bucket in st.graphs:
+            return st.graphs[bucket]
+        rows = st.info["M"] + st.info["Mb"]
+        b_buf = torch.zeros((bucket, rows), dtype=torch.float64, device=self.dev)
+        x_buf = torch.zeros((bucket, st.info["N"]), dtype=torch.float64, device=self.dev)
+        graph = None
+        if self.use_graphs:
+            with torch.cuda.stream(stream):
+                self._solve_fn(st, b_buf, x_buf, stream)           # warm up (attribute set-up)
+            stream.synchronize()
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=stream):
+                self._solve_fn(st, b_buf, x_buf, torch.cuda.current_stream())
+        st.graphs[bucket] = (graph, b_buf, x_buf)
+        return st.graphs[bucket]
+
+    def _dispatch(self, slot: int, key, now_fn):
+        q = self.queue[key]
+        st = self.setups.get(key)
+        if st is None:
+            st = self._build(q[0].spec)
+            if st is None:
+                while q:
+                    r = q.popleft()
+                    r.rejected = True
+                    r.t_done = now_fn()
+                    self.rejections += 1
+                del self.queue[key]
+                return
+        reqs, ncols = [], 0
+        while q and ncols + q[0].nrhs <= BUCKETS[-1]:
+            r = q.popleft()
+            reqs.append(r)
+            ncols += r.nrhs
+        if not q:
+            del self.queue[key]
+        bucket = next(b for b in BUCKETS if b >= ncols)
+        stream = self.slots[slot]
+        graph, b_buf, x_buf = self._graph(st, bucket, stream)
+        with torch.cuda.stream(stream):
+            b_buf.zero_()
+            self._rhs(st, reqs, b_buf)
+            if graph is not None:
+                graph.replay()
+            else:
+                self._solve_fn(st, b_buf, x_buf, stream)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+        st.inflight += 1
+        st.last_use = time.perf_counter()
+        self.slot_busy[slot] = (ev, st, reqs, x_buf, ncols)
+
+    def _poll(self, now_fn):
+        for i, busy in enumerate(self.slot_busy):
+            if busy is not None and busy[0].query():
+                ev, st, reqs, x_buf, ncols = busy
+                t = now_fn()
+                col = 0
+                for r in reqs:
+                    r.t_done = t
+                    if self.keep_results:
+                        self.results[r.rid] = x_buf[col:col + r.nrhs].clone()
+                    col += r.nrhs
+                st.inflight -= 1
+                self.slot_busy[i] = None
+
+    def run(self, requests, realtime: bool = True):
+        """Serve the requests (sorted by arrival).  Returns the summary dict."""
+        reqs = sorted(requests, key=lambda r: r.arrival)
+        t0 = time.perf_counter()
+        now = lambda: time.perf_counter() - t0
+        i = 0
+        n = len(reqs)
+        while True:
+            t = now()
+            while i < n and (reqs[i].arrival <= t or not realtime):
+                r = reqs[i]
+                self.queue.setdefault(r.spec.key, collections.deque()).append(r)
+                i += 1
+                if not realtime and len(self.queue) > 64:
+                    break
+            self._poll(now)
+            for s in range(len(self.slots)):
+                if self.slot_busy[s] is None and self.queue:
+                    # oldest waiting setup first; a setup already running on
+                    # another slot is skipped so its batch can keep growing
+                    keys = [k for k in self.queue
+                            if not any(b is not None and b[1].spec.key == k for b in self.slot_busy)]
+                    if keys:
+                        self._dispatch(s, keys[0], now)
+            idle = all(b is None for b in self.slot_busy)
+            if i >= n and not self.queue and idle:
+                break
+            if realtime and i < n and not self.queue and idle:
+                time.sleep(max(0.0, min(0.001, reqs[i].arrival - now())))
+        elapsed = now()
+        done = [r for r in reqs if not r.rejected]
+        lat = sorted(1000.0 * (r.t_done - r.arrival) for r in done)
+        solves = sum(r.nrhs for r in done)
+
+        def pct(q):
+            return lat[min(len(lat) - 1, int(q * len(lat)))] if lat else None
+        return {"requests": n, "served": len(done), "rejected": self.rejections, "rhs_solved": solves,
+                "elapsed_s": elapsed, "solves_per_s": solves / elapsed if elapsed > 0 else None,
+                "latency_ms": {"p50": pct(0.50), "p99": pct(0.99), "max": lat[-1] if lat else None},
+                "setup_builds": self.setup_builds, "evictions": self.evictions,
+                "device_bytes_high_water": self.high_water}
+
+
+# --------------------------------------------------------------------------- the mixed workload
+def star_fn(r0, a, k):
+    return lambda X, Y: np.sqrt(X * X + Y * Y) <= r0 + a * np.cos(k * np.arctan2(Y, X))
+
+
+def setup_pool(seed: int, count: int = 32, max2d: int = 512):
+    """A seeded pool of setups with the stream's mix of problem kinds."""
+    rng = np.random.default_rng(seed)
+    pool = []
+    for i in range(count):
+        u = rng.random()
+        if u < 0.4:
+            N = 1 << int(rng.integers(12, 19))
+            a = float(rng.uniform(-1.0, 0.0))
+            spec = SetupSpec(("1d", N, round(a, 6)), 1, (N,), (2,), (1.0,), "approx",
+                             (lambda a: (lambda x: (x >= a) & (x <= a + 1.0)))(a), k=24)
+        elif u < 0.8:
+            n = int(rng.choice([64, 128, 256, 512]))
+            n = min(n, max2d)
+            a, kk = float(rng.uniform(0.0, 0.2)), int(rng.integers(3, 8))
+            spec = SetupSpec(("2d", n, round(a, 6), kk), 2, (n, n), (2, 2), (1.0, 1.0), "approx",
+                             star_fn(0.5, a, kk), k=64)
+        else:
+            n = int(rng.choice([64, 128, 256]))
+            a, kk = float(rng.uniform(0.0, 0.2)), int(rng.integers(3, 8))
+            th = 2 * np.pi * np.arange(512) / 512
+            r = 0.5 + a * np.cos(kk * th)
+            spec = SetupSpec(("poisson", n, round(a, 6), kk), 2, (n, n), (2, 2), (1.0, 1.0), "poisson",
+                             star_fn(0.5, a, kk), np.stack([r * np.cos(th), r * np.sin(th)], 1), 10.0, k=64)
+        pool.append(spec)
+    return pool
+
+
+def poisson_stream(seed: int, rate: float, duration: float, pool):
+    """Poisson arrivals at `rate` per second for `duration` seconds, 1..32 RHS each."""
+    rng = np.random.default_rng(seed + 1)
+    t, rid, out = 0.0, 0, []
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t > duration:
+            break
+        spec = pool[int(rng.integers(0, len(pool)))]
+        out.append(Request(rid, t, spec, int(rng.integers(1, 33)), int(rng.integers(0, 2 ** 31))))
+        rid += 1
+    return out
