@@ -245,6 +245,18 @@ def serving_leg(seconds):
     return out
 
 
+# --------------------------------------------------------------------------- replicas
+def replica_rate(local_ms: float, nrhs: int, steps: int, world: int, dist=None, device=None):
+    """Whole-job rate of independent replicas: the slowest rank's time bounds the
+    job; every rank solved nrhs * steps right-hand sides."""
+    import torch
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    if world > 1 and dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    return world * nrhs * steps / (total_ms / 1000.0), total_ms
+
+
 # --------------------------------------------------------------------------- our arm
 def load_traffic():
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
@@ -313,12 +325,7 @@ def run_ours(args):
     barrier()
     clk = clocks.stop()
     per = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
-    total_ms = evs[0].elapsed_time(evs[-1])
-    t = torch.tensor([total_ms], device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    value = world * NRHS * args.steps / (total_ms / 1000.0)
+    value, total_ms = replica_rate(evs[0].elapsed_time(evs[-1]), NRHS, args.steps, world, dist, dev)
     if args.lite:
         if rank == 0:
             print(json.dumps({"lite": True, "value": value, "ms_per_step": total_ms / args.steps,
@@ -336,11 +343,8 @@ def run_ours(args):
         x_pin.copy_(x_dev, non_blocking=True)
     e_evs[1].record(stream)
     torch.cuda.synchronize(dev)
-    e_ms = e_evs[0].elapsed_time(e_evs[1])
-    te = torch.tensor([e_ms], device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e = {"value": world * NRHS * args.steps / (float(te.item()) / 1000.0), "unit": "RHS/s",
+    e_val, _ = replica_rate(e_evs[0].elapsed_time(e_evs[1]), NRHS, args.steps, world, dist, dev)
+    e2e = {"value": e_val, "unit": "RHS/s",
            "h2d_bytes_per_step": int(b_host.nbytes), "d2h_bytes_per_step": int(x_pin.numel() * 8)}
 
     # parity: relres of the mixed result vs the library's all-FP64 path on the same batch
