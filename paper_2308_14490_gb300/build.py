@@ -14,8 +14,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libaz.so")
-SOURCES = ["kernels.cu", "lowrank.cu", "az_api.cu", "profile.cu", "noalloc.cu"]
-HEADERS = ["az_internal.cuh", "fft.cuh", "kernels.cuh", "lowrank.cuh", "profile.cuh"]
+SOURCES = ["kernels.cu", "lowrank.cu", "lowrank_large.cu", "az_api.cu", "profile.cu", "noalloc.cu"]
+HEADERS = ["az_internal.cuh", "fft.cuh", "fft_reg.cuh", "kernels.cuh", "lowrank.cuh", "lowrank_large.cuh", "profile.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]
@@ -57,7 +57,9 @@ def build(verbose: bool = False, force: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 1))) as ex:
         list(ex.map(run, jobs))
     if jobs or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
-        run([nvcc, *ARCH, "-shared", "-o", LIB, *objs, "-cudart", "static"])
+        libdir = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "lib64")
+        run([nvcc, *ARCH, "-shared", "-o", LIB, *objs, "-cudart", "static", "-L" + libdir, "-lcublas", "-lcusolver",
+             "-Xlinker", "-rpath," + libdir])
     return LIB
 
 

@@ -8,6 +8,7 @@
 
 #include "kernels.cuh"
 #include "lowrank.cuh"
+#include "lowrank_large.cuh"
 #include "profile.cuh"
 
 namespace az {
@@ -16,6 +17,10 @@ void set_error(const std::string& msg) { g_last_error = msg; }
 }  // namespace az
 
 using namespace az;
+
+// Sketch widths up to this use the one-CTA factorisation and register-blocked
+// tall products; wider sketches use the Householder QR + GEMM path.
+static constexpr int kNarrowK = 64;
 
 struct az_setup_t {
   Geom g{};
@@ -74,6 +79,7 @@ struct az_setup_t {
   double* Rd = nullptr;     // N x k (collocation sketch)
   double* r64 = nullptr;    // Mtot x cols (relres residual), lazily
   double* bcoll = nullptr;  // Mtot x cols (scaled collocation data), lazily
+  LargeK* wide = nullptr;   // k > 64: Householder QR + FP64 SVD + GEMM path
 };
 
 namespace {
@@ -391,6 +397,10 @@ az_status sketch_and_factor(az_setup_t* h, cudaStream_t st) {
   }
   // Y = A W on all rows (kept grid rows, then weighted boundary rows)
   AZ_TRY((apply_rows<T, T, double, T>(h, W, g.N, nullptr, 0, (T)0, (T)1, Y, h->Mtot, k, st)));
+  if (h->wide) {
+    // wide sketch: Householder QR of Y (Q into the Q1 scratch), SVD of R
+    return large_factor(h->wide, Y, h->Mtot, h->Q1, h->Ut, h->tau_svd, h->floor, h->VS, h->sig, h->info, st);
+  }
   // pass 1: G1 = Y^T Y, SVQB
   AZ_TRY((launch_gram<T, T>(Y, h->Mtot, k, Y, h->Mtot, k, h->Mtot, h->partial, h->G, st)));
   const double taug = Prec<T>::fp64 ? 1e-8 : 1e-7;
@@ -429,6 +439,12 @@ az_status az_once(az_setup_t* h, const TB* b, int64_t ldb, int ncols, double* x,
   T* gg = (T*)h->gb;
   AZ_TRY((zstar_chain<T, TB>(h, 0, b, ldb, ncols, z, g.N, st)));
   AZ_TRY((apply_rows<T, T, TB, T>(h, z, g.N, b, ldb, (T)1, (T)-1, gg, h->Mtot, ncols, st)));
+  if (h->wide) {
+    AZ_TRY(large_project(h->wide, h->Ut, h->Mtot, gg, h->Mtot, ncols, h->cb, st));
+    AZ_TRY(launch_small_mm(h->VS, h->k, h->cb, ncols, h->ub, st));
+    AZ_TRY(large_update(h->wide, h->W, g.N, h->ub, z, g.N, g.N, ncols, x, ldx, accumulate, st));
+    return AZ_OK;
+  }
   AZ_TRY((launch_gram<T, T>((const T*)h->Ut, h->Mtot, h->k, gg, h->Mtot, ncols, h->Mtot, h->partial, h->cb, st, true)));
   AZ_TRY(launch_small_mm(h->VS, h->k, h->cb, ncols, h->ub, st));
   // the mixed path also leaves the (exactly FP32) first-pass solution in the z buffer
@@ -512,6 +528,7 @@ void destroy(az_setup_t* h) {
   if (h->X3d) cudaFree(h->X3d);
   if (h->r64) cudaFree(h->r64);
   if (h->bcoll) cudaFree(h->bcoll);
+  if (h->wide) large_destroy(h->wide);
   delete h;
 }
 
@@ -555,7 +572,8 @@ az_status az_query_footprint(const az_grid* gr, int64_t M, int64_t n_boundary, c
   b += (size_t)pm * (g.L + g.N) * vsz;              // X1, X3
   const int cols = std::max(2 * pm, k);
   b += (size_t)g.N * cols * tsz + 2 * (size_t)Mt * cols * tsz;
-  b += (size_t)gram_blocks(Mt) * k * std::max(k, cols) * 8;
+  if (k <= 64) b += (size_t)gram_blocks(Mt) * k * std::max(k, cols) * 8;
+  else b += (size_t)k * k * 8 * 5 + (size_t)Mt * k * 4 + (32u << 20);   // small FP64 factors, QR workspace, cuBLAS workspace
   b += (size_t)Mt * k * 8;                          // transient Q1 during setup
   *bytes = b;
   return AZ_OK;
@@ -573,7 +591,7 @@ az_status az_setup(const az_grid* gr, const uint8_t* mask, const double* bpts, i
   if (opt) o = *opt;
   else { o.precision = AZ_MIXED; o.k = 24; o.tau_svd = 0; o.tau_sym = 0; o.seed = 1; o.refine_steps = -1; }
   if (o.precision != AZ_FP64 && o.precision != AZ_MIXED) { set_error("az_setup: precision"); return AZ_ERR_ARG; }
-  if (o.k < 1 || o.k > 64) { set_error("az_setup: k must be in [1, 64] for this build"); return AZ_ERR_ARG; }
+  if (o.k < 1 || o.k > 4096) { set_error("az_setup: k must be in [1, 4096]"); return AZ_ERR_ARG; }
   if (kernel == AZ_NEG_LAPLACE_GAUSS && (!gr || gr->dim != 2)) { set_error("az_setup: collocation needs dim = 2"); return AZ_ERR_ARG; }
   az_setup_t* h = new az_setup_t();
   az_status rc = make_geom(gr, h->g);
@@ -639,7 +657,14 @@ az_status az_setup(const az_grid* gr, const uint8_t* mask, const double* bpts, i
     rc = dalloc_t(h, &h->sig, h->k); if (rc) break;
     rc = dalloc_t(h, &h->info, 1); if (rc) break;
     rc = alloc_workspace(h); if (rc) break;
-    rc = dalloc_t(h, &h->partial, (size_t)gram_blocks(h->Mtot) * h->k * std::max(h->k, 2 * h->pairs_max)); if (rc) break;
+    if (h->k > kNarrowK) {
+      size_t wb = 0;
+      rc = large_create(&h->wide, h->Mtot, h->k, h->precision == AZ_FP64, h->Q1, &wb);
+      h->bytes += wb;
+      if (rc) break;
+    } else {
+      rc = dalloc_t(h, &h->partial, (size_t)gram_blocks(h->Mtot) * h->k * std::max(h->k, 2 * h->pairs_max)); if (rc) break;
+    }
     // rounding floor of the sketch's singular values: 1e-13 * ||A R||_F, with
     // ||A R||_F^2 ~ k (Mtot/L) sum_k S_k / s (estimate from the symbol's peak)
     rc = build_symbol(h, st); if (rc) break;

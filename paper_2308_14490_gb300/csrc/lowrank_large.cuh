@@ -1,0 +1,18 @@
+// Wide-sketch (k > 64) low-rank step: Householder QR + FP64 SVD of R + GEMMs.
+#pragma once
+#include "lowrank.cuh"
+
+namespace az {
+struct LargeK;
+// A_probe: a device array of at least M x k elements of the working precision
+// (only used to size the solver workspace).  *bytes receives the device bytes held.
+az_status large_create(LargeK** out, int64_t M, int k, bool fp64, void* A_probe, size_t* bytes);
+void large_destroy(LargeK* L);
+// From the sketch Y (M x k): U_tau (M x k, zero beyond rank), VS (k x k), sigma, info.  A: M x k scratch.
+az_status large_factor(LargeK* L, const void* Y, int64_t ldy, void* A, void* Ut, double tau, double floor, double* VS,
+                       double* sig, FactorInfo* info, cudaStream_t st);
+az_status large_project(LargeK* L, const void* Ut, int64_t ldu, const void* g, int64_t ldg, int n, double* c,
+                        cudaStream_t st);
+az_status large_update(LargeK* L, const void* W, int64_t ldw, const double* u, void* z, int64_t ldz, int64_t N, int n,
+                       double* x, int64_t ldx, bool accumulate, cudaStream_t st);
+}  // namespace az
