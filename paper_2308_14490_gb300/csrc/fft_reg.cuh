@@ -45,12 +45,25 @@ __device__ __forceinline__ void fft_stage(V (&v)[E], V* __restrict__ sm, int log
       const int j = tl + g * P;
       const int k = j & (Ns - 1);
       if (Ns > 1) {
+        // w^u for u < R: the power-of-two exponents come from the table (one
+        // gather each), the rest are products of those (at most LR - 1
+        // products, so a few rounding units), which keeps the scattered
+        // table reads per butterfly at LR instead of R - 1.
+        V w[R];
 #pragma unroll
-        for (int u = 1; u < R; ++u) {
-          V w = __ldg(tw + ((u * k * step) & (n - 1)) * tws);
-          if (INV) w.y = -w.y;
-          v[g * R + u] = cmul(v[g * R + u], w);
+        for (int b = 1; b < R; b <<= 1) {
+          w[b] = __ldg(tw + ((b * k * step) & (n - 1)) * tws);
+          if (INV) w[b].y = -w[b].y;
         }
+#pragma unroll
+        for (int u = 3; u < R; ++u) {
+          if (u & (u - 1)) {
+            const int hb = u >= 8 ? 8 : (u >= 4 ? 4 : 2);
+            w[u] = cmul(w[hb], w[u - hb]);
+          }
+        }
+#pragma unroll
+        for (int u = 1; u < R; ++u) v[g * R + u] = cmul(v[g * R + u], w[u]);
       }
       dftR<V, R, INV>(v + g * R);
     }
