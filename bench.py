@@ -258,12 +258,28 @@ def replica_rate(local_ms: float, nrhs: int, steps: int, world: int, dist=None, 
 
 
 # --------------------------------------------------------------------------- our arm
+def csrc_digest():
+    """SHA-1 over the CUDA sources: DRAM counters taken on other sources are stale."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_2308_14490_gb300", "csrc")
+    h = hashlib.sha1()
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(f.encode())
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()
+
+
 def load_traffic():
+    """Per-kernel DRAM bytes from one ncu pass, or {} when the kernels changed since."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
-        return json.load(open(path))
+        t = json.load(open(path))
     except Exception:
         return {}
+    if t.get("csrc_sha1") != csrc_digest():
+        return {}
+    return t.get("kernels", {})
 
 
 def run_ours(args):
@@ -372,7 +388,8 @@ def run_ours(args):
              sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:8]}
     roofline = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(achieved / hbm, 4), "peak_source": peak_src,
-                "traffic": tr.get("traffic_per_launch") if tr else None,
+                "traffic": (tr["dram_bytes_per_step"] / tr["launches_per_step"]) if tr else None,
+                "traffic_source": tr.get("source") if tr else None,
                 "algorithmic_bytes_per_launch": ent["bytes"] / max(1, ent["launches"]),
                 "avg_launch_ms": ent["ms"] / max(1, ent["launches"]), "time_share": share}
 

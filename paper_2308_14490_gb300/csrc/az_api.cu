@@ -9,6 +9,7 @@
 #include "kernels.cuh"
 #include "lowrank.cuh"
 #include "lowrank_large.cuh"
+#include "tc_tsgram.cuh"
 #include "profile.cuh"
 
 namespace az {
@@ -28,6 +29,7 @@ struct az_setup_t {
   double eps = 0, tau_svd = 1e-8, tau_sym = 0, bweight = 1.0, floor = 0;
   uint64_t seed = 0;
   int64_t M = 0, Mb = 0, Mtot = 0;
+  int64_t ldm = 0;        // leading dimension of Ut and gb: Mtot rounded up to 32 (16-byte TMA strides)
   std::vector<void*> allocs;
   size_t bytes = 0;
   int32_t* pos2m = nullptr;
@@ -50,7 +52,7 @@ struct az_setup_t {
   int64_t nw = 0;
   void* W = nullptr;    // N x k   (T)
   void* Y = nullptr;    // Mtot x k (T)
-  void* Ut = nullptr;   // Mtot x k (T), zero beyond rank
+  void* Ut = nullptr;   // Mtot x k (T, ld ldm), zero beyond rank
   double *G = nullptr, *V = nullptr, *lam = nullptr, *B1 = nullptr, *Tm = nullptr, *VS = nullptr, *sig = nullptr;
   double* partial = nullptr;
   FactorInfo* info = nullptr;
@@ -59,7 +61,7 @@ struct az_setup_t {
   void* X1 = nullptr;   // pairs_max x L complex
   void* X3 = nullptr;   // pairs_max x N complex
   void* zb = nullptr;   // N x 2 pairs_max (T)
-  void* gb = nullptr;   // Mtot x 2 pairs_max (T)
+  void* gb = nullptr;   // Mtot x 2 pairs_max (T, ld ldm)
   void* rb = nullptr;   // Mtot x 2 pairs_max (T) residual
   double* cb = nullptr; // k x 2 pairs_max
   double* ub = nullptr;
@@ -80,6 +82,7 @@ struct az_setup_t {
   double* r64 = nullptr;    // Mtot x cols (relres residual), lazily
   double* bcoll = nullptr;  // Mtot x cols (scaled collocation data), lazily
   LargeK* wide = nullptr;   // k > 64: Householder QR + FP64 SVD + GEMM path
+  int* tc_err = nullptr;    // set by a tensor-core pipeline wait that timed out
 };
 
 namespace {
@@ -102,6 +105,16 @@ az_status dalloc(az_setup_t* h, void** p, size_t bytes) {
 }
 template <typename P> az_status dalloc_t(az_setup_t* h, P** p, size_t count) {
   return dalloc(h, (void**)p, count * sizeof(P));
+}
+
+// per-CTA partial sums of the tall products: the SIMT Gram kernel or the
+// tensor-core kernel, whichever launches more CTAs
+int partial_blocks(int64_t M) {
+  return std::max(gram_blocks(M), (int)std::min<int64_t>(tc_tsgram_blocks(), (M + 31) / 32));
+}
+
+std::string tc_wait_message(int code) {
+  return "tensor-core tall product: pipeline wait timed out (role " + std::to_string(code) + "); results invalid";
 }
 
 bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
@@ -392,14 +405,14 @@ az_status sketch_and_factor(az_setup_t* h, cudaStream_t st) {
     // for the boundary rows).
     T* v = (T*)h->gb;    // Mtot x k scratch (gb holds >= k columns)
     AZ_TRY(launch_bits_to_R(h->bits, g.N, k, h->Rd, st));
-    AZ_TRY((apply_rows<T, double, double, T>(h, h->Rd, g.N, nullptr, 0, (T)0, (T)1, v, h->Mtot, k, st)));
-    AZ_TRY((zstar_chain<T, T>(h, 2, v, h->Mtot, k, W, g.N, st)));
+    AZ_TRY((apply_rows<T, double, double, T>(h, h->Rd, g.N, nullptr, 0, (T)0, (T)1, v, h->ldm, k, st)));
+    AZ_TRY((zstar_chain<T, T>(h, 2, v, h->ldm, k, W, g.N, st)));
   }
   // Y = A W on all rows (kept grid rows, then weighted boundary rows)
   AZ_TRY((apply_rows<T, T, double, T>(h, W, g.N, nullptr, 0, (T)0, (T)1, Y, h->Mtot, k, st)));
   if (h->wide) {
     // wide sketch: Householder QR of Y (Q into the Q1 scratch), SVD of R
-    return large_factor(h->wide, Y, h->Mtot, h->Q1, h->Ut, h->tau_svd, h->floor, h->VS, h->sig, h->info, st);
+    return large_factor(h->wide, Y, h->Mtot, h->Q1, h->Ut, h->ldm, h->tau_svd, h->floor, h->VS, h->sig, h->info, st);
   }
   // pass 1: G1 = Y^T Y, SVQB
   AZ_TRY((launch_gram<T, T>(Y, h->Mtot, k, Y, h->Mtot, k, h->Mtot, h->partial, h->G, st)));
@@ -410,7 +423,7 @@ az_status sketch_and_factor(az_setup_t* h, cudaStream_t st) {
     AZ_TRY((launch_tsprod<T, double>(Y, h->Mtot, k, h->B1, k, h->Mtot, h->Q1, h->Mtot, st)));
     AZ_TRY((launch_gram<double, double>(h->Q1, h->Mtot, k, h->Q1, h->Mtot, k, h->Mtot, h->partial, h->G, st)));
     AZ_TRY(launch_factor2(h->G, k, h->V, h->lam, h->tau_svd, h->floor, h->Tm, h->VS, h->sig, h->info, st));
-    AZ_TRY((launch_tsprod<double, T>(h->Q1, h->Mtot, k, h->Tm, k, h->Mtot, (T*)h->Ut, h->Mtot, st)));
+    AZ_TRY((launch_tsprod<double, T>(h->Q1, h->Mtot, k, h->Tm, k, h->Mtot, (T*)h->Ut, h->ldm, st)));
   } else {
     // mixed: Q1 = Y B1 needs extended precision (its small directions cancel
     // by up to sigma_1 / sigma_r1), computed in double-float and rounded to
@@ -419,7 +432,7 @@ az_status sketch_and_factor(az_setup_t* h, cudaStream_t st) {
     AZ_TRY(launch_tsprod_df<float>((const float*)Y, h->Mtot, k, h->B1, k, h->Mtot, Q1f, h->Mtot, st));
     AZ_TRY((launch_gram<float, float>(Q1f, h->Mtot, k, Q1f, h->Mtot, k, h->Mtot, h->partial, h->G, st, true)));
     AZ_TRY(launch_factor2(h->G, k, h->V, h->lam, h->tau_svd, h->floor, h->Tm, h->VS, h->sig, h->info, st, true));
-    AZ_TRY((launch_tsprod<float, float>(Q1f, h->Mtot, k, h->Tm, k, h->Mtot, (float*)h->Ut, h->Mtot, st)));
+    AZ_TRY((launch_tsprod<float, float>(Q1f, h->Mtot, k, h->Tm, k, h->Mtot, (float*)h->Ut, h->ldm, st)));
   }
   return AZ_OK;
 }
@@ -438,14 +451,20 @@ az_status az_once(az_setup_t* h, const TB* b, int64_t ldb, int ncols, double* x,
   T* z = (T*)h->zb;
   T* gg = (T*)h->gb;
   AZ_TRY((zstar_chain<T, TB>(h, 0, b, ldb, ncols, z, g.N, st)));
-  AZ_TRY((apply_rows<T, T, TB, T>(h, z, g.N, b, ldb, (T)1, (T)-1, gg, h->Mtot, ncols, st)));
+  AZ_TRY((apply_rows<T, T, TB, T>(h, z, g.N, b, ldb, (T)1, (T)-1, gg, h->ldm, ncols, st)));
   if (h->wide) {
-    AZ_TRY(large_project(h->wide, h->Ut, h->Mtot, gg, h->Mtot, ncols, h->cb, st));
+    AZ_TRY(large_project(h->wide, h->Ut, h->ldm, gg, h->ldm, ncols, h->cb, st));
     AZ_TRY(launch_small_mm(h->VS, h->k, h->cb, ncols, h->ub, st));
     AZ_TRY(large_update(h->wide, h->W, g.N, h->ub, z, g.N, g.N, ncols, x, ldx, accumulate, st));
     return AZ_OK;
   }
-  AZ_TRY((launch_gram<T, T>((const T*)h->Ut, h->Mtot, h->k, gg, h->Mtot, ncols, h->Mtot, h->partial, h->cb, st, true)));
+  if (!Prec<T>::fp64 && tc_tsgram_ok(h->Ut, h->ldm, h->k, gg, h->ldm, ncols)) {
+    // c = U_tau^T g on the tensor cores (split TF32, FP32-level accuracy)
+    AZ_TRY(launch_tc_tsgram((const float*)h->Ut, h->ldm, h->k, (const float*)gg, h->ldm, ncols, h->Mtot, h->partial,
+                            h->cb, h->tc_err, st));
+  } else {
+    AZ_TRY((launch_gram<T, T>((const T*)h->Ut, h->ldm, h->k, gg, h->ldm, ncols, h->Mtot, h->partial, h->cb, st, true)));
+  }
   AZ_TRY(launch_small_mm(h->VS, h->k, h->cb, ncols, h->ub, st));
   // the mixed path also leaves the (exactly FP32) first-pass solution in the z buffer
   float* xf = (want_xf && !Prec<T>::fp64) ? (float*)z : nullptr;
@@ -492,10 +511,13 @@ az_status solve_impl(az_setup_t* h, const double* b, int64_t ldb, int64_t nrhs, 
       if (rc == AZ_OK) rc = launch_sumsq_cols(r64, h->Mtot, h->Mtot, nc, h->normb, st);
       if (rc == AZ_OK) rc = launch_sumsq_cols(bc, ldb, h->Mtot, nc, h->normb + nc, st);
       std::vector<double> hv(2 * nc);
+      int tcerr = 0;
       cudaError_t e = cudaMemcpyAsync(hv.data(), h->normb, 2 * nc * sizeof(double), cudaMemcpyDeviceToHost, st);
+      cudaError_t e1 = cudaMemcpyAsync(&tcerr, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, st);
       cudaError_t e2 = cudaStreamSynchronize(st);
       if (rc) return rc;
-      if (e != cudaSuccess || e2 != cudaSuccess) { set_error("relres readback failed"); return AZ_ERR_CUDA; }
+      if (e != cudaSuccess || e1 != cudaSuccess || e2 != cudaSuccess) { set_error("relres readback failed"); return AZ_ERR_CUDA; }
+      if (tcerr) { set_error(tc_wait_message(tcerr)); return AZ_ERR_CUDA; }
       for (int c = 0; c < nc; ++c) relres[c0 + c] = hv[nc + c] > 0 ? std::sqrt(hv[c] / hv[nc + c]) : 0.0;
     }
   }
@@ -513,7 +535,7 @@ az_status alloc_workspace(az_setup_t* h) {
   AZ_TRY(dalloc(h, &h->X1, per_pair * pm / (g.L + g.N) * g.L));
   AZ_TRY(dalloc(h, &h->X3, per_pair * pm / (g.L + g.N) * g.N));
   AZ_TRY(dalloc(h, &h->zb, (size_t)g.N * cols * tsz));
-  AZ_TRY(dalloc(h, &h->gb, (size_t)h->Mtot * cols * tsz));
+  AZ_TRY(dalloc(h, &h->gb, (size_t)h->ldm * cols * tsz));
   AZ_TRY(dalloc(h, &h->rb, (size_t)h->Mtot * cols * tsz));
   AZ_TRY(dalloc_t(h, &h->cb, (size_t)h->k * cols));
   AZ_TRY(dalloc_t(h, &h->ub, (size_t)h->k * cols));
@@ -568,11 +590,12 @@ az_status az_query_footprint(const az_grid* gr, int64_t M, int64_t n_boundary, c
   b += (size_t)g.L * (4 + 8 + 8 + 4);              // pos2m, Ghat, H64, H32
   b += (size_t)M * 4 + (size_t)g.N * 8;             // idx, S
   b += (size_t)((g.N + 31) / 32) * 4 * k;           // bits
-  b += (size_t)g.N * k * tsz + 2 * (size_t)Mt * k * tsz;  // W, Y, Ut
+  const int64_t ldm = (Mt + 31) / 32 * 32;
+  b += (size_t)g.N * k * tsz + (size_t)(Mt + ldm) * k * tsz;  // W, Y, Ut
   b += (size_t)pm * (g.L + g.N) * vsz;              // X1, X3
   const int cols = std::max(2 * pm, k);
-  b += (size_t)g.N * cols * tsz + 2 * (size_t)Mt * cols * tsz;
-  if (k <= 64) b += (size_t)gram_blocks(Mt) * k * std::max(k, cols) * 8;
+  b += (size_t)g.N * cols * tsz + (size_t)(Mt + ldm) * cols * tsz;
+  if (k <= 64) b += (size_t)partial_blocks(Mt) * k * std::max(k, cols) * 8;
   else b += (size_t)k * k * 8 * 5 + (size_t)Mt * k * 4 + (32u << 20);   // small FP64 factors, QR workspace, cuBLAS workspace
   b += (size_t)Mt * k * 8;                          // transient Q1 during setup
   *bytes = b;
@@ -622,6 +645,7 @@ az_status az_setup(const az_grid* gr, const uint8_t* mask, const double* bpts, i
         cudaStreamSynchronize(st) != cudaSuccess) { set_error("az_setup: reading M failed"); rc = AZ_ERR_CUDA; break; }
     h->M = M;
     h->Mtot = M + h->Mb;
+    h->ldm = (h->Mtot + 31) / 32 * 32;
     if (h->Mtot < 1) { set_error("az_setup: Omega contains no grid point"); rc = AZ_ERR_ARG; break; }
     if (h->Mb) {
       rc = dalloc_t(h, &h->bpts, 2 * h->Mb); if (rc) break;
@@ -648,7 +672,9 @@ az_status az_setup(const az_grid* gr, const uint8_t* mask, const double* bpts, i
     const size_t tsz = h->precision == AZ_FP64 ? 8 : 4;
     rc = dalloc(h, &h->W, (size_t)g.N * h->k * tsz); if (rc) break;
     rc = dalloc(h, &h->Y, (size_t)h->Mtot * h->k * tsz); if (rc) break;
-    rc = dalloc(h, &h->Ut, (size_t)h->Mtot * h->k * tsz); if (rc) break;
+    rc = dalloc(h, &h->Ut, (size_t)h->ldm * h->k * tsz); if (rc) break;
+    rc = dalloc_t(h, &h->tc_err, 1); if (rc) break;
+    if (cudaMemsetAsync(h->tc_err, 0, sizeof(int), st) != cudaSuccess) { cudaGetLastError(); set_error("memset"); rc = AZ_ERR_CUDA; break; }
     rc = dalloc_t(h, &h->Q1, (size_t)h->Mtot * h->k); if (rc) break;
     if (h->kind == 1) { rc = dalloc_t(h, &h->Rd, (size_t)g.N * h->k); if (rc) break; }
     for (double** p : {&h->G, &h->V, &h->B1, &h->Tm, &h->VS}) { rc = dalloc_t(h, p, (size_t)h->k * h->k); if (rc) break; }
@@ -663,7 +689,7 @@ az_status az_setup(const az_grid* gr, const uint8_t* mask, const double* bpts, i
       h->bytes += wb;
       if (rc) break;
     } else {
-      rc = dalloc_t(h, &h->partial, (size_t)gram_blocks(h->Mtot) * h->k * std::max(h->k, 2 * h->pairs_max)); if (rc) break;
+      rc = dalloc_t(h, &h->partial, (size_t)partial_blocks(h->Mtot) * h->k * std::max(h->k, 2 * h->pairs_max)); if (rc) break;
     }
     // rounding floor of the sketch's singular values: 1e-13 * ||A R||_F, with
     // ||A R||_F^2 ~ k (Mtot/L) sum_k S_k / s (estimate from the symbol's peak)
@@ -761,8 +787,11 @@ az_status az_apply_Zstar(az_handle h, const double* y, int64_t ldy, int64_t nrhs
 az_status az_get_info(az_handle h, az_info_t* info) {
   if (!h || !info) { set_error("az_get_info: bad arguments"); return AZ_ERR_ARG; }
   FactorInfo fi;
+  int tcerr = 0;
   AZ_CUDA(cudaDeviceSynchronize());
   AZ_CUDA(cudaMemcpy(&fi, h->info, sizeof(fi), cudaMemcpyDeviceToHost));
+  AZ_CUDA(cudaMemcpy(&tcerr, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (tcerr) { set_error(tc_wait_message(tcerr)); return AZ_ERR_CUDA; }
   info->N = h->g.N; info->L = h->g.L; info->M = h->M; info->Mb = h->Mb; info->k = h->k;
   info->rank = fi.r; info->rank_gram = fi.r1; info->precision = h->precision;
   info->sigma_max = fi.sigma_max; info->sigma_min_kept = fi.sigma_min_kept;
@@ -791,8 +820,8 @@ az_status az_get_array(az_handle h, int32_t which, double* dst, void* stream) {
       FactorInfo fi;
       AZ_CUDA(cudaStreamSynchronize(st));
       AZ_CUDA(cudaMemcpy(&fi, h->info, sizeof(fi), cudaMemcpyDeviceToHost));
-      return f64 ? to_double<double>((double*)h->Ut, h->Mtot, h->Mtot, fi.r, dst, h->Mtot, st)
-                 : to_double<float>((float*)h->Ut, h->Mtot, h->Mtot, fi.r, dst, h->Mtot, st);
+      return f64 ? to_double<double>((double*)h->Ut, h->ldm, h->Mtot, fi.r, dst, h->Mtot, st)
+                 : to_double<float>((float*)h->Ut, h->ldm, h->Mtot, fi.r, dst, h->Mtot, st);
     }
     case AZ_ARRAY_SIGMA: {
       FactorInfo fi;

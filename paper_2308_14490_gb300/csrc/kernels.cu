@@ -932,22 +932,29 @@ az_status launch_H(const Geom& g, const double* Ghat, const double* S, double th
   AZ_LAUNCH_CHECK();
   return AZ_OK;
 }
-__global__ void k_max_abs(const double* v, int64_t n, double* out) {
+// max |v_i| over all blocks: block maxima combined by an integer atomicMax on
+// the IEEE bit patterns (for non-negative doubles their order is the numeric
+// order); *out must hold +0.0 before the launch.
+__global__ void k_max_abs(const double* __restrict__ v, int64_t n, unsigned long long* out) {
   __shared__ double sm[32];
   double m = 0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, fabs(v[i]));
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    m = fmax(m, fabs(v[i]));
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
   __syncthreads();
   if (threadIdx.x == 0) {
     double r = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmax(r, sm[w]);
-    *out = r;
+    atomicMax(out, (unsigned long long)__double_as_longlong(r));
   }
 }
 az_status launch_max_abs(const double* v, int64_t n, double* out, cudaStream_t st) {
   ProfScope ps("symbol", 8.0 * n, st);
-  k_max_abs<<<1, 1024, 0, st>>>(v, n, out);
+  AZ_CUDA(cudaMemsetAsync(out, 0, sizeof(double), st));
+  const int64_t want = (n + 1023) / 1024;
+  const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, 4 * 152));
+  k_max_abs<<<blocks, 1024, 0, st>>>(v, n, (unsigned long long*)out);
   AZ_LAUNCH_CHECK();
   return AZ_OK;
 }

@@ -181,18 +181,29 @@ __global__ void __launch_bounds__(512) k_gram_partial(const TA* __restrict__ A, 
     partial[(int64_t)blockIdx.x * npair + a + (int64_t)c * ka] = sacc2;
   }
 }
+// One warp per output entry: lanes stride over the per-block partial sums,
+// then a shuffle tree (fixed order, so the result is deterministic).
 __global__ void k_gram_reduce(const double* __restrict__ partial, int nblk, int npair, int ka, int sym, int RA,
                               double* __restrict__ G) {
-  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
   if (p >= npair) return;
-  int a = p % ka, c = p / ka;
+  const int a = p % ka, c = p / ka;
   // symmetric case: entries in blocks below the block diagonal were not
   // computed; read the mirrored entry
   int src = p;
   if (sym && (a / RA) > (c / RA)) src = c + a * ka;
   double s = 0.0;
-  for (int b = 0; b < nblk; ++b) s += partial[(int64_t)b * npair + src];
-  G[p] = s;  // column-major ka x kb: p = a + c*ka
+  for (int b = lane; b < nblk; b += 32) s += partial[(int64_t)b * npair + src];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) G[p] = s;  // column-major ka x kb: p = a + c*ka
+}
+az_status launch_gram_reduce(const double* partial, int nblk, int ka, int kb, double* G, cudaStream_t st) {
+  const int npair = ka * kb;
+  k_gram_reduce<<<(unsigned)(((int64_t)npair * 32 + 255) / 256), 256, 0, st>>>(partial, nblk, npair, ka, 0, 1, G);
+  AZ_LCHECK();
+  return AZ_OK;
 }
 // mode: products summed in FP32 within a tile ("fast", FP32 inputs only),
 // else double-float for FP32 inputs, else FP64.
@@ -225,7 +236,7 @@ az_status launch_gram(const TA* A, int64_t lda, int ka, const TB* B, int64_t ldb
     smem_once(k, sm);
     k<<<nblk, threads, sm, st>>>(A, lda, ka, B, ldb, kb, M, partial, sym);
   }
-  k_gram_reduce<<<(npair + 255) / 256, 256, 0, st>>>(partial, nblk, npair, ka, sym, RA, G);
+  k_gram_reduce<<<(unsigned)(((int64_t)npair * 32 + 255) / 256), 256, 0, st>>>(partial, nblk, npair, ka, sym, RA, G);
   AZ_LCHECK();
   return AZ_OK;
 }

@@ -23,6 +23,8 @@ int gram_blocks(int64_t M);
 template <typename TA, typename TB>
 az_status launch_gram(const TA* A, int64_t lda, int ka, const TB* B, int64_t ldb, int kb, int64_t M,
                       double* partial, double* G, cudaStream_t st, bool fast = false);
+// G (ka x kb) = sum over nblk per-block partials (partial[b * ka * kb + a + c * ka]).
+az_status launch_gram_reduce(const double* partial, int nblk, int ka, int kb, double* G, cudaStream_t st);
 // out[M x r] = A[M x k] * S[k x r] (S FP64, column-major ld k), FP64 accumulation.
 template <typename TA, typename TO>
 az_status launch_tsprod(const TA* A, int64_t lda, int k, const double* S, int r, int64_t M, TO* out, int64_t ldo,

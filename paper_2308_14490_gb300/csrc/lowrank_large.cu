@@ -148,7 +148,7 @@ __global__ void k_svd_outputs(const double* __restrict__ S, const double* __rest
 }
 
 template <typename T>
-az_status large_factor_t(LargeK* L, const T* Y, int64_t ldy, T* A, T* Ut, double tau, double floor, double* VS,
+az_status large_factor_t(LargeK* L, const T* Y, int64_t ldy, T* A, T* Ut, int64_t ldu, double tau, double floor, double* VS,
                          double* sig, FactorInfo* info, cudaStream_t st) {
   const int64_t M = L->M;
   const int k = L->k;
@@ -181,18 +181,18 @@ az_status large_factor_t(LargeK* L, const T* Y, int64_t ldy, T* A, T* Ut, double
   const T one = 1, zero = 0;
   if (sizeof(T) == 8) {
     AZ_BLAS(cublasDgemm(L->blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)M, k, k, (const double*)&one, (const double*)A, (int)M,
-                        (const double*)L->UR, k, (const double*)&zero, (double*)Ut, (int)M));
+                        (const double*)L->UR, k, (const double*)&zero, (double*)Ut, (int)ldu));
   } else {
     AZ_BLAS(cublasSgemm(L->blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)M, k, k, (const float*)&one, (const float*)A, (int)M,
-                        (const float*)L->UR, k, (const float*)&zero, (float*)Ut, (int)M));
+                        (const float*)L->UR, k, (const float*)&zero, (float*)Ut, (int)ldu));
   }
   return AZ_OK;
 }
 
-az_status large_factor(LargeK* L, const void* Y, int64_t ldy, void* A, void* Ut, double tau, double floor, double* VS,
+az_status large_factor(LargeK* L, const void* Y, int64_t ldy, void* A, void* Ut, int64_t ldu, double tau, double floor, double* VS,
                        double* sig, FactorInfo* info, cudaStream_t st) {
-  return L->fp64 ? large_factor_t<double>(L, (const double*)Y, ldy, (double*)A, (double*)Ut, tau, floor, VS, sig, info, st)
-                 : large_factor_t<float>(L, (const float*)Y, ldy, (float*)A, (float*)Ut, tau, floor, VS, sig, info, st);
+  return L->fp64 ? large_factor_t<double>(L, (const double*)Y, ldy, (double*)A, (double*)Ut, ldu, tau, floor, VS, sig, info, st)
+                 : large_factor_t<float>(L, (const float*)Y, ldy, (float*)A, (float*)Ut, ldu, tau, floor, VS, sig, info, st);
 }
 
 __global__ void k_f2d_cols(const float* __restrict__ a, int n, double* __restrict__ b) {

@@ -9,7 +9,7 @@ struct LargeK;
 az_status large_create(LargeK** out, int64_t M, int k, bool fp64, void* A_probe, size_t* bytes);
 void large_destroy(LargeK* L);
 // From the sketch Y (M x k): U_tau (M x k, zero beyond rank), VS (k x k), sigma, info.  A: M x k scratch.
-az_status large_factor(LargeK* L, const void* Y, int64_t ldy, void* A, void* Ut, double tau, double floor, double* VS,
+az_status large_factor(LargeK* L, const void* Y, int64_t ldy, void* A, void* Ut, int64_t ldu, double tau, double floor, double* VS,
                        double* sig, FactorInfo* info, cudaStream_t st);
 az_status large_project(LargeK* L, const void* Ut, int64_t ldu, const void* g, int64_t ldg, int n, double* c,
                         cudaStream_t st);

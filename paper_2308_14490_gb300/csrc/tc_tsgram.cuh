@@ -1,0 +1,24 @@
+// Tall-skinny product G = A^T B (A: M x ka, B: M x kb, FP32, column-major,
+// M long) on the 5th-generation tensor cores: TMA tiles, tcgen05.mma
+// (kind::tf32) with split operands for FP32-level accuracy, accumulators in
+// tensor memory.  Used in the mixed path for the projection c = U_tau^T g of
+// the truncated low-rank solve in step 1 of Algorithm 1 (Sec. 3.2.3).
+#pragma once
+#include <cstdint>
+
+#include "az_internal.cuh"
+
+namespace az {
+
+// Limits of the tensor-core path: ka, kb <= 64; lda, ldb multiples of 4
+// (16-byte row strides for TMA); A, B 16-byte aligned.
+bool tc_tsgram_ok(const void* A, int64_t lda, int ka, const void* B, int64_t ldb, int kb);
+
+// G (ka x kb, column-major, FP64) = A^T B.  partial: >= tc_tsgram_blocks() *
+// ka * kb doubles of scratch.  err: device int, set to a nonzero code if a
+// pipeline wait timed out (the result is then invalid).
+az_status launch_tc_tsgram(const float* A, int64_t lda, int ka, const float* B, int64_t ldb, int kb, int64_t M,
+                           double* partial, double* G, int* err, cudaStream_t st);
+int tc_tsgram_blocks();
+
+}  // namespace az
