@@ -13,9 +13,22 @@
 // in registers.  Every thread of the block must call this (it contains
 // __syncthreads()); threads with active == false only take part in barriers.
 #pragma once
+#include <type_traits>
+
 #include "fft.cuh"
 
 namespace az {
+
+// The last stage hands each output to the epilogue as epi(o, v), or, when the
+// epilogue accepts them, as epi(o, v, u, o0, Ns) with o = o0 + u * Ns and u
+// the (compile-time, after unrolling) output slot of the butterfly: an
+// epilogue that multiplies by w^(c * o) can then form it from w^(c * o0) and
+// the powers w^(c * Ns * 2^b) instead of one table gather per output.
+template <typename Epi, typename V>
+__device__ __forceinline__ void epi_call(Epi& epi, int o, const V& v, int u, int o0, int Ns) {
+  if constexpr (std::is_invocable_v<Epi&, int, V, int, int, int>) epi(o, v, u, o0, Ns);
+  else epi(o, v);
+}
 
 template <int PADSH> __device__ __forceinline__ int padix(int e) { return e + (e >> PADSH); }
 
@@ -77,7 +90,7 @@ __device__ __forceinline__ void fft_stage(V (&v)[E], V* __restrict__ sm, int log
 #pragma unroll
       for (int u = 0; u < R; ++u) {
         const int o = (j - k) * R + k + u * Ns;
-        if (last) epi(o, v[g * R + u]);
+        if (last) epi_call(epi, o, v[g * R + u], u, (j - k) * R + k, Ns);
         else sm[padix<PADSH>(line * cs + o * is)] = v[g * R + u];
       }
     }

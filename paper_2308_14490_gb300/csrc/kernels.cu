@@ -215,6 +215,34 @@ __device__ __forceinline__ V big_tw(const V* __restrict__ A, const V* __restrict
   if (inv) w.y = -w.y;
   return w;
 }
+// w^(c * o) for the outputs o = o0 + u * Ns of one butterfly of a last FFT
+// stage: w^(c * o0) is gathered once per butterfly and w^(c * Ns * 2^b) once per
+// thread, so an output costs at most four complex products (u < 16) instead of
+// two table gathers; the result is within a few rounding units of the table.
+template <typename V>
+struct BigTwPow {
+  V p[4];
+  V base;
+  __device__ __forceinline__ void init(const V* A, const V* B, int c, int Ns, int R, bool inv) {
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+      if ((1 << b) < R) p[b] = big_tw<V>(A, B, c * (Ns << b), inv);
+  }
+  __device__ __forceinline__ V at(const V* A, const V* B, int c, int u, int o0, bool inv) {
+    if (u == 0) base = big_tw<V>(A, B, c * o0, inv);
+    V w = base;
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+      if (u & (1 << b)) w = cmul(w, p[b]);
+    return w;
+  }
+};
+// stride Ns and radix R of the last stage of fft_reg for a line of 2^logn with E per thread
+__device__ __forceinline__ void last_stage_shape(int logn, int logE, int& Ns, int& R) {
+  if (logn >= logE) { Ns = 1 << (logn - logE); R = 1 << logE; }
+  else { Ns = 1; R = 1 << logn; }
+}
+
 // ceil(a / 2^l) and floor(a / 2^l) for signed a (arithmetic shift floors)
 __device__ __forceinline__ int cdiv_p2(int a, int l) { return -((-a) >> l); }
 __device__ __forceinline__ int fdiv_p2(int a, int l) { return a >> l; }
@@ -1047,7 +1075,10 @@ az_status launch_sumsq_cols(const double* v, int64_t ld, int64_t rows, int ncols
 #define REG_MINB 3
 #endif
 #define PADC 4   // shared-memory padding: one element every 16 (column and row layouts)
-template <typename T> struct EPT { static constexpr int E = sizeof(T) == 4 ? AZ_REG_E32 : 8; };
+template <typename T> struct EPT {
+  static constexpr int E = sizeof(T) == 4 ? AZ_REG_E32 : 8;
+  static constexpr int LOGE = E == 16 ? 4 : (E == 8 ? 3 : 2);
+};
 
 template <typename T, int MODE, typename TB>
 __global__ void __launch_bounds__(REG_THREADS, REG_MINB) k_colfwd_r(Geom g, const int32_t* __restrict__ pos2m, const TB* __restrict__ b,
@@ -1134,8 +1165,17 @@ __global__ void __launch_bounds__(REG_THREADS, REG_MINB) k_colfwd_r(Geom g, cons
     if (colB < ncols) v.y = cvt<T>(bB[m]);
     return v;
   };
-  auto epi = [&](int k0, V v) {
-    if (g.dim == 1 && k0 != 0 && n1 != 0) v = cmul(v, big_tw<V>((const V*)tb.bigA, (const V*)tb.bigB, n1 * k0, false));
+  // four-step twiddle w_L^(n1 k0) (1D), formed from per-butterfly powers
+  BigTwPow<V> tw;
+  const V* twA = (const V*)tb.bigA;
+  const V* twB = (const V*)tb.bigB;
+  if (g.dim == 1) {
+    int NsL, RL;
+    last_stage_shape(g.logD0, EPT<T>::LOGE, NsL, RL);
+    tw.init(twA, twB, n1, NsL, RL, false);
+  }
+  auto epi = [&](int k0, V v, int u, int o0, int Ns) {
+    if (g.dim == 1) v = cmul(v, tw.at(twA, twB, n1, u, o0, false));
     X1[(k0 << g.logD1) + n1] = v;
   };
   fft_reg<V, E, false, PADC>(sm, g.logD0, true, line, tl, 1, C, twp, TW_N >> g.logD0, pro, epi, MODE == 1);
@@ -1190,8 +1230,17 @@ __global__ void __launch_bounds__(REG_THREADS, REG_MINB) k_rowfold_r(Geom g, con
       V o; o.x = ar; o.y = ai;
       return o;
     };
-    auto epi = [&](int n1, V v) {
-      if (g.dim == 1 && k0 != 0 && n1 != 0) v = cmul(v, big_tw<V>((const V*)tb.bigNA, (const V*)tb.bigNB, n1 * k0, true));
+    // four-step twiddle conj(w_N^(n1 k0)) (1D), formed from per-butterfly powers
+    BigTwPow<V> tw;
+    const V* nA = (const V*)tb.bigNA;
+    const V* nB = (const V*)tb.bigNB;
+    if (g.dim == 1) {
+      int NsL, RL;
+      last_stage_shape(g.logN1, LOGE2, NsL, RL);
+      tw.init(nA, nB, k0, NsL, RL, true);
+    }
+    auto epi = [&](int n1, V v, int u, int o0, int Ns) {
+      if (g.dim == 1) v = cmul(v, tw.at(nA, nB, k0, u, o0, true));
       X3[(k0 << g.logN1) + n1] = v;
     };
     fft_reg<V, E2, true, PADC>(smF, g.logN1, true, gg, tl, g.N1, 1, twp, TW_N >> g.logN1, pro, epi);
