@@ -621,6 +621,7 @@ az_status launch_colinv_v1(const Geom& g, const typename C2<T>::t* X3, int pair0
 // Rows of A at the kept grid points: out[m, c] = alpha*b[m, c] + beta*(A z)[m, c].
 // One thread per kept point m and a group of CPT columns (index arithmetic and
 // taps shared across the group).
+constexpr int STENCIL_WIN = 512;   // coefficients staged per block and column (1D)
 template <typename T, typename TZ, typename TB, typename TO, int CPT>
 __global__ void __launch_bounds__(256) k_stencil_rows(Geom g, int kind, T inv2e2, const int32_t* __restrict__ idx, int M,
                                                       const T* __restrict__ x0, const T* __restrict__ x2,
@@ -629,24 +630,47 @@ __global__ void __launch_bounds__(256) k_stencil_rows(Geom g, int kind, T inv2e2
                                                       int64_t ldb, T alpha, T beta, TO* __restrict__ outb, int64_t ldo,
                                                       int ncols) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= M) return;
+  const bool act = m < M;
   const int cbase = blockIdx.y * CPT;
   const int nc = min(CPT, ncols - cbase);
-  const int i = __ldg(idx + m);
+  const int i = act ? __ldg(idx + m) : 0;
   T acc[CPT];
 #pragma unroll
   for (int c = 0; c < CPT; ++c) acc[c] = 0;
   if (g.dim == 1) {
     const int ls = g.logs[0], s = g.s[0], Nm = (int)g.N - 1;
     const int jlo = cdiv_p2(i - Wx, ls), jhi = fdiv_p2(i + Wx, ls);
-    for (int j = jlo; j <= jhi; ++j) {
-      const T tap = __ldg(x0 + (i - s * j + Wx));
-      const int jj = j & Nm;
+    // coefficients the block needs: one window when its rows are (nearly)
+    // contiguous, staged once in shared memory with coalesced loads
+    const int m0 = blockIdx.x * blockDim.x;
+    const int m1 = min(M, m0 + (int)blockDim.x) - 1;
+    const int wlo = cdiv_p2(__ldg(idx + m0) - Wx, ls), whi = fdiv_p2(__ldg(idx + m1) + Wx, ls);
+    const int nwin = whi - wlo + 1;
+    __shared__ TZ swin[CPT * STENCIL_WIN];
+    if (nwin <= STENCIL_WIN) {
+      for (int t = threadIdx.x; t < nc * nwin; t += blockDim.x) {
+        const int c = t / nwin, o = t - c * nwin;
+        swin[c * STENCIL_WIN + o] = zb[(int64_t)(cbase + c) * ldz + ((wlo + o) & Nm)];
+      }
+      __syncthreads();
+      if (act) {
+        for (int j = jlo; j <= jhi; ++j) {
+          const T tap = __ldg(x0 + (i - s * j + Wx));
 #pragma unroll
-      for (int c = 0; c < CPT; ++c)
-        if (c < nc) acc[c] += tap * (T)__ldg(zb + (int64_t)(cbase + c) * ldz + jj);
+          for (int c = 0; c < CPT; ++c)
+            if (c < nc) acc[c] += tap * (T)swin[c * STENCIL_WIN + (j - wlo)];
+        }
+      }
+    } else if (act) {
+      for (int j = jlo; j <= jhi; ++j) {
+        const T tap = __ldg(x0 + (i - s * j + Wx));
+        const int jj = j & Nm;
+#pragma unroll
+        for (int c = 0; c < CPT; ++c)
+          if (c < nc) acc[c] += tap * (T)__ldg(zb + (int64_t)(cbase + c) * ldz + jj);
+      }
     }
-  } else {
+  } else if (act) {
     const int sx = g.s[0], sy = g.s[1];
     const int Nxm = (int)g.n[0] - 1, Nym = (int)g.n[1] - 1, lNy = g.logn[1];
     const int ix = i >> g.logD1, iy = i & (g.D1 - 1);
@@ -667,6 +691,7 @@ __global__ void __launch_bounds__(256) k_stencil_rows(Geom g, int kind, T inv2e2
       }
     }
   }
+  if (!act) return;
 #pragma unroll
   for (int c = 0; c < CPT; ++c) {
     if (c < nc) {

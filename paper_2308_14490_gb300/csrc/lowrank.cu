@@ -676,10 +676,92 @@ __global__ void __launch_bounds__(256) k_update_x(const TW* __restrict__ W, int6
     if (xf) xf[(int64_t)c * ldz + j] = (float)s;   // exact FP32 copy (may alias z)
   }
 }
+// FP32 variant for aligned shapes: a CTA stages its 512-row tile of W and all
+// of u in shared memory; each warp then streams whole columns of z and x with
+// 16-byte accesses (4 rows per lane), so every global access is a full,
+// contiguous 512-byte warp transaction.
+constexpr int UPX_ROWS = 512;
+__global__ void __launch_bounds__(256) k_update_x_v4(const float* __restrict__ W, int64_t ldw, int k,
+                                                     const double* __restrict__ u, const float* z, int64_t ldz,
+                                                     int64_t N, int nrhs, double* x, int64_t ldx, int accumulate,
+                                                     float* xf) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* sW = (float*)smem_raw;                 // [a][UPX_ROWS]
+  float* su = sW + (size_t)k * UPX_ROWS;         // [c][k]
+  const int64_t r0 = (int64_t)blockIdx.x * UPX_ROWS;
+  const int rows = (int)(N - r0 < UPX_ROWS ? N - r0 : UPX_ROWS);   // multiple of 4
+  for (int t = threadIdx.x; t < k * (UPX_ROWS / 4); t += blockDim.x) {
+    const int a = t / (UPX_ROWS / 4), q = (t % (UPX_ROWS / 4)) * 4;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (q < rows) v = *(const float4*)(W + (int64_t)a * ldw + r0 + q);
+    *(float4*)(sW + a * UPX_ROWS + q) = v;
+  }
+  for (int t = threadIdx.x; t < k * nrhs; t += blockDim.x) su[t] = (float)u[t];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int NQ = UPX_ROWS / 128;   // 16-byte chunks per lane and column, loaded together
+  for (int c = warp; c < nrhs; c += 8) {
+    const float* uc = su + c * k;
+    const float* zc = z + (int64_t)c * ldz + r0;
+    double* xc = x + (int64_t)c * ldx + r0;
+    float4 s[NQ];
+    double2 xa[NQ], xb[NQ];
+#pragma unroll
+    for (int t = 0; t < NQ; ++t) {
+      const int q = lane * 4 + t * 128;
+      s[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+      xa[t] = make_double2(0.0, 0.0);
+      xb[t] = make_double2(0.0, 0.0);
+      if (q < rows) {
+        s[t] = *(const float4*)(zc + q);
+        if (accumulate) {
+          xa[t] = *(const double2*)(xc + q);
+          xb[t] = *(const double2*)(xc + q + 2);
+        }
+      }
+    }
+    for (int a = 0; a < k; ++a) {
+      const float ua = uc[a];
+#pragma unroll
+      for (int t = 0; t < NQ; ++t) {
+        const float4 w = *(const float4*)(sW + a * UPX_ROWS + lane * 4 + t * 128);
+        s[t].x = fmaf(w.x, ua, s[t].x);
+        s[t].y = fmaf(w.y, ua, s[t].y);
+        s[t].z = fmaf(w.z, ua, s[t].z);
+        s[t].w = fmaf(w.w, ua, s[t].w);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < NQ; ++t) {
+      const int q = lane * 4 + t * 128;
+      if (q >= rows) continue;
+      xa[t].x += cvt<double>(s[t].x);
+      xa[t].y += cvt<double>(s[t].y);
+      xb[t].x += cvt<double>(s[t].z);
+      xb[t].y += cvt<double>(s[t].w);
+      *(double2*)(xc + q) = xa[t];
+      *(double2*)(xc + q + 2) = xb[t];
+      if (xf) *(float4*)(xf + (int64_t)c * ldz + r0 + q) = s[t];   // exact FP32 copy (may alias z)
+    }
+  }
+}
+
 template <typename TW, typename TZ>
 az_status launch_update_x(const TW* W, int64_t ldw, int k, const double* u, const TZ* z, int64_t ldz, int64_t N,
                           int nrhs, double* x, int64_t ldx, bool accumulate, cudaStream_t st, float* xf) {
   ProfScope ps("update_x", (double)N * (k * sizeof(TW) + nrhs * (sizeof(TZ) + 8.0 * (accumulate ? 2 : 1))), st);
+  if constexpr (sizeof(TW) == 4 && sizeof(TZ) == 4) {
+    const size_t sm4 = ((size_t)k * UPX_ROWS + (size_t)k * nrhs) * sizeof(float);
+    const bool aligned = N % 4 == 0 && ldw % 4 == 0 && ldz % 4 == 0 && ldx % 2 == 0 && ((uintptr_t)W & 15) == 0 &&
+                         ((uintptr_t)z & 15) == 0 && ((uintptr_t)x & 15) == 0 && ((uintptr_t)xf & 15) == 0;
+    if (aligned && sm4 <= 160 * 1024) {
+      smem_once(k_update_x_v4, sm4);
+      k_update_x_v4<<<(unsigned)((N + UPX_ROWS - 1) / UPX_ROWS), 256, sm4, st>>>(W, ldw, k, u, z, ldz, N, nrhs, x, ldx,
+                                                                               accumulate ? 1 : 0, xf);
+      AZ_LCHECK();
+      return AZ_OK;
+    }
+  }
   size_t sm = (size_t)k * nrhs * sizeof(TW);
   unsigned grid = (unsigned)((N + 255) / 256);
   if (k <= 8) k_update_x<TW, TZ, 8><<<grid, 256, sm, st>>>(W, ldw, k, u, z, ldz, N, nrhs, x, ldx, accumulate ? 1 : 0, xf);
