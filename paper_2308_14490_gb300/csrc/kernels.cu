@@ -1105,10 +1105,43 @@ template <typename T> struct EPT {
   static constexpr int LOGE = E == 16 ? 4 : (E == 8 ? 3 : 2);
 };
 
-template <typename T, int MODE, typename TB>
-__global__ void __launch_bounds__(REG_THREADS, REG_MINB) k_colfwd_r(Geom g, const int32_t* __restrict__ pos2m, const TB* __restrict__ b,
-                                                  int64_t ldb, int ncols, SketchIn<T> in, int pair0, int logC,
+// Compile-time shapes for the register passes.  ShapeRT leaves every size to
+// the Geom at run time; Shape1D<LL, LS, LC> fixes a 1D grid with L = 2^LL,
+// s = 2^LS and 2^LC lines per CTA, so that all FFT index arithmetic folds to
+// constants (the passes are issue-bound, about half of it integer work).
+struct ShapeRT {
+  static constexpr bool fixed = false;
+  static constexpr int logC = 0;
+};
+template <int LL, int LS, int LC>
+struct Shape1D {
+  static constexpr bool fixed = true;
+  static constexpr int logD1 = (LL + 1) / 2, logD0 = LL - logD1, logN1 = logD1 - LS, logC = LC;
+};
+template <class S>
+__device__ __forceinline__ Geom fix_geom(const Geom& g) {
+  Geom r = g;
+  if constexpr (S::fixed) {
+    r.dim = 1;
+    r.logD0 = S::logD0; r.D0 = 1 << S::logD0;
+    r.logD1 = S::logD1; r.D1 = 1 << S::logD1;
+    r.logN1 = S::logN1; r.N1 = 1 << S::logN1;
+    r.logG0 = S::logD0; r.G0 = 1 << S::logD0;
+    r.Rg = 1; r.logRg = 0; r.Rstride = 0; r.Fq = 1 << (S::logD1 - S::logN1);
+    r.logs[0] = S::logD1 - S::logN1; r.s[0] = 1 << r.logs[0];
+    r.L = (int64_t)1 << (S::logD0 + S::logD1); r.N = r.L >> r.logs[0]; r.logN = S::logD0 + S::logN1;
+  }
+  return r;
+}
+// Host side: the fixed shape a launch may use (config-2 scale: L = 2^21, s = 2)
+static bool is_shape_21_1(const Geom& g) { return g.dim == 1 && g.L == ((int64_t)1 << 21) && g.s[0] == 2; }
+
+template <typename T, int MODE, typename TB, class S>
+__global__ void __launch_bounds__(REG_THREADS, REG_MINB) k_colfwd_r(Geom g_in, const int32_t* __restrict__ pos2m, const TB* __restrict__ b,
+                                                  int64_t ldb, int ncols, SketchIn<T> in, int pair0, int logC_in,
                                                   typename C2<T>::t* X1base, PassTabs tb) {
+  const Geom g = fix_geom<S>(g_in);
+  const int logC = S::fixed ? S::logC : logC_in;
   // MODE 0: gather b (E b on the grid); MODE 1: sketch stencil A^c R with the mask
   using V = typename C2<T>::t;
   constexpr int E = EPT<T>::E;
@@ -1206,10 +1239,12 @@ __global__ void __launch_bounds__(REG_THREADS, REG_MINB) k_colfwd_r(Geom g, cons
   fft_reg<V, E, false, PADC>(sm, g.logD0, true, line, tl, 1, C, twp, TW_N >> g.logD0, pro, epi, MODE == 1);
 }
 
-template <typename T, int E2>
-__global__ void __launch_bounds__(REG_THREADS, REG_MINB) k_rowfold_r(Geom g, const typename C2<T>::t* __restrict__ X1base,
-                                                   const T* __restrict__ H, int logGPB, typename C2<T>::t* X3base,
+template <typename T, int E2, class S>
+__global__ void __launch_bounds__(REG_THREADS, REG_MINB) k_rowfold_r(Geom g_in, const typename C2<T>::t* __restrict__ X1base,
+                                                   const T* __restrict__ H, int logGPB_in, typename C2<T>::t* X3base,
                                                    PassTabs tb) {
+  const Geom g = fix_geom<S>(g_in);
+  const int logGPB = S::fixed ? S::logC : logGPB_in;
   using V = typename C2<T>::t;
   constexpr int E = EPT<T>::E;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1272,10 +1307,12 @@ __global__ void __launch_bounds__(REG_THREADS, REG_MINB) k_rowfold_r(Geom g, con
   }
 }
 
-template <typename T, typename TO, bool WMODE>
-__global__ void __launch_bounds__(REG_THREADS, REG_MINB) k_colinv_r(Geom g, const typename C2<T>::t* __restrict__ X3base, int pair0,
-                                                  int ncols, int logC, TO* __restrict__ out, int64_t ldo,
+template <typename T, typename TO, bool WMODE, class S>
+__global__ void __launch_bounds__(REG_THREADS, REG_MINB) k_colinv_r(Geom g_in, const typename C2<T>::t* __restrict__ X3base, int pair0,
+                                                  int ncols, int logC_in, TO* __restrict__ out, int64_t ldo,
                                                   const uint32_t* __restrict__ bits, int64_t nw, PassTabs tb) {
+  const Geom g = fix_geom<S>(g_in);
+  const int logC = S::fixed ? S::logC : logC_in;
   using V = typename C2<T>::t;
   constexpr int E = EPT<T>::E;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1329,7 +1366,8 @@ az_status launch_colfwd_stencil(const Geom& g, const SketchIn<T>& in, int pair0,
   const int C = reg_cols<T>(g.D0, g.D1);
   const int threads = C * (g.D0 / EPT<T>::E);
   size_t sm = ((size_t)padix_host(g.D0 * C, PADC) + 32 + (g.dim == 2 ? (size_t)g.n[0] * C : 0)) * sizeof(V);
-  auto kern = k_colfwd_r<T, 1, double>;
+  auto kern = k_colfwd_r<T, 1, double, ShapeRT>;
+  if (sizeof(T) == 4 && is_shape_21_1(g) && C == 4) kern = k_colfwd_r<T, 1, double, Shape1D<21, 1, 2>>;
   if (set_smem(kern, sm) != cudaSuccess) { set_error("smem attribute"); return AZ_ERR_CUDA; }
   dim3 grid(g.D1 / C, npairs);
   ProfScope ps(sizeof(T) == 4 ? "colfwd_sketch_f32" : "colfwd_sketch_f64", (double)npairs * g.L * sizeof(V) + npairs * 2.0 * g.N / 8 + 4.0 * g.L, st);
@@ -1346,7 +1384,8 @@ az_status launch_colfwd_gather(const Geom& g, const int32_t* pos2m, const TB* b,
   const int C = reg_cols<T>(g.D0, g.D1);
   const int threads = C * (g.D0 / EPT<T>::E);
   size_t sm = ((size_t)padix_host(g.D0 * C, PADC) + 32) * sizeof(V);
-  auto kern = k_colfwd_r<T, 0, TB>;
+  auto kern = k_colfwd_r<T, 0, TB, ShapeRT>;
+  if (sizeof(T) == 4 && is_shape_21_1(g) && C == 4) kern = k_colfwd_r<T, 0, TB, Shape1D<21, 1, 2>>;
   if (set_smem(kern, sm) != cudaSuccess) { set_error("smem attribute"); return AZ_ERR_CUDA; }
   dim3 grid(g.D1 / C, npairs);
   SketchIn<T> none{};
@@ -1371,17 +1410,25 @@ az_status launch_rowfold(const Geom& g, const typename C2<T>::t* X1, const T* H,
   dim3 grid(g.G0 / GPB, npairs);
   ProfScope ps(sizeof(T) == 4 ? "rowfold_f32" : "rowfold_f64", (double)npairs * (g.L + g.N) * sizeof(V) + (double)g.L * sizeof(T), st);
   if (E2 == 8) {
-    if (set_smem(k_rowfold_r<T, 8>, sm) != cudaSuccess) { set_error("smem attribute"); return AZ_ERR_CUDA; }
-    k_rowfold_r<T, 8><<<grid, threads, sm, st>>>(g, X1, H, ilog2i(GPB), X3, tb);
+    auto kern = k_rowfold_r<T, 8, ShapeRT>;
+    if (sizeof(T) == 4 && is_shape_21_1(g) && GPB == 2) kern = k_rowfold_r<T, 8, Shape1D<21, 1, 1>>;
+    if (set_smem(kern, sm) != cudaSuccess) { set_error("smem attribute"); return AZ_ERR_CUDA; }
+    kern<<<grid, threads, sm, st>>>(g, X1, H, ilog2i(GPB), X3, tb);
   } else if (E2 == 4) {
-    if (set_smem(k_rowfold_r<T, 4>, sm) != cudaSuccess) { set_error("smem attribute"); return AZ_ERR_CUDA; }
-    k_rowfold_r<T, 4><<<grid, threads, sm, st>>>(g, X1, H, ilog2i(GPB), X3, tb);
+    auto kern = k_rowfold_r<T, 4, ShapeRT>;
+    if (sizeof(T) == 4 && is_shape_21_1(g) && GPB == 2) kern = k_rowfold_r<T, 4, Shape1D<21, 1, 1>>;
+    if (set_smem(kern, sm) != cudaSuccess) { set_error("smem attribute"); return AZ_ERR_CUDA; }
+    kern<<<grid, threads, sm, st>>>(g, X1, H, ilog2i(GPB), X3, tb);
   } else if (E2 == 2) {
-    if (set_smem(k_rowfold_r<T, 2>, sm) != cudaSuccess) { set_error("smem attribute"); return AZ_ERR_CUDA; }
-    k_rowfold_r<T, 2><<<grid, threads, sm, st>>>(g, X1, H, ilog2i(GPB), X3, tb);
+    auto kern = k_rowfold_r<T, 2, ShapeRT>;
+    if (sizeof(T) == 4 && is_shape_21_1(g) && GPB == 2) kern = k_rowfold_r<T, 2, Shape1D<21, 1, 1>>;
+    if (set_smem(kern, sm) != cudaSuccess) { set_error("smem attribute"); return AZ_ERR_CUDA; }
+    kern<<<grid, threads, sm, st>>>(g, X1, H, ilog2i(GPB), X3, tb);
   } else {
-    if (set_smem(k_rowfold_r<T, 16>, sm) != cudaSuccess) { set_error("smem attribute"); return AZ_ERR_CUDA; }
-    k_rowfold_r<T, 16><<<grid, threads, sm, st>>>(g, X1, H, ilog2i(GPB), X3, tb);
+    auto kern = k_rowfold_r<T, 16, ShapeRT>;
+    if (sizeof(T) == 4 && is_shape_21_1(g) && GPB == 2) kern = k_rowfold_r<T, 16, Shape1D<21, 1, 1>>;
+    if (set_smem(kern, sm) != cudaSuccess) { set_error("smem attribute"); return AZ_ERR_CUDA; }
+    kern<<<grid, threads, sm, st>>>(g, X1, H, ilog2i(GPB), X3, tb);
   }
   AZ_LAUNCH_CHECK();
   return AZ_OK;
@@ -1398,11 +1445,15 @@ az_status launch_colinv(const Geom& g, const typename C2<T>::t* X3, int pair0, i
   dim3 grid(g.N1 / C, npairs);
   ProfScope ps(sizeof(T) == 4 ? "colinv_f32" : "colinv_f64", (double)npairs * g.N * sizeof(V) + (double)std::min(ncols - 2 * pair0, 2 * npairs) * g.N * sizeof(TO), st);
   if (bits) {
-    if (set_smem(k_colinv_r<T, TO, true>, sm) != cudaSuccess) { set_error("smem attribute"); return AZ_ERR_CUDA; }
-    k_colinv_r<T, TO, true><<<grid, threads, sm, st>>>(g, X3, pair0, ncols, ilog2i(C), out, ldo, bits, nw, tb);
+    auto kern = k_colinv_r<T, TO, true, ShapeRT>;
+    if (sizeof(T) == 4 && is_shape_21_1(g) && C == 4) kern = k_colinv_r<T, TO, true, Shape1D<21, 1, 2>>;
+    if (set_smem(kern, sm) != cudaSuccess) { set_error("smem attribute"); return AZ_ERR_CUDA; }
+    kern<<<grid, threads, sm, st>>>(g, X3, pair0, ncols, ilog2i(C), out, ldo, bits, nw, tb);
   } else {
-    if (set_smem(k_colinv_r<T, TO, false>, sm) != cudaSuccess) { set_error("smem attribute"); return AZ_ERR_CUDA; }
-    k_colinv_r<T, TO, false><<<grid, threads, sm, st>>>(g, X3, pair0, ncols, ilog2i(C), out, ldo, bits, nw, tb);
+    auto kern = k_colinv_r<T, TO, false, ShapeRT>;
+    if (sizeof(T) == 4 && is_shape_21_1(g) && C == 4) kern = k_colinv_r<T, TO, false, Shape1D<21, 1, 2>>;
+    if (set_smem(kern, sm) != cudaSuccess) { set_error("smem attribute"); return AZ_ERR_CUDA; }
+    kern<<<grid, threads, sm, st>>>(g, X3, pair0, ncols, ilog2i(C), out, ldo, bits, nw, tb);
   }
   AZ_LAUNCH_CHECK();
   return AZ_OK;

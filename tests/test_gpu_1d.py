@@ -185,3 +185,30 @@ def test_fine_grid_error(az):
     err_g = np.abs(vals - f)[mf].max()
     err_o = np.abs(opf.Ac(AZ(op, p.k, 7, 1e-8).solve(b))[:, 0] - f)[mf].max()
     assert err_g <= max(1.01 * err_o, err_o + 1e-9 * np.abs(f).max())
+
+
+def test_config2_scale_zstar_and_solve(az):
+    """Config-2 geometry (N = 2^20, L = 2^21, s = 2, Omega = [-0.7, 0.3], k = 24,
+    mixed): the same FFT-pass kernels and launch shapes the benchmark step times.
+    Z* in FP32 against the oracle's FP64 FFT form, and the refined solve's relres
+    against the oracle AZ with the same R, k and tau."""
+    gu = _gu()
+    p = W.config2(1 << 20, 4)
+    op = Operator(p.grid, p.mask)
+    b = p.rhs()
+    h = gu.setup(p, az.AZ_MIXED, seed=1)
+    try:
+        ys = np.random.default_rng(11).standard_normal((op.M, 3))
+        z = torch.zeros((3, op.N), dtype=torch.float64, device=gu.dev())
+        az.az_apply_Zstar(h, gu.to_dev_cols(ys), z)
+        ref = op.Zstar(ys)
+        # FP32 transforms of length 2^21: a few hundred units of FP32 rounding
+        assert np.abs(gu.from_dev_cols(z) - ref).max() <= 2e-5 * np.abs(ref).max()
+        x = torch.zeros((b.shape[1], op.N), dtype=torch.float64, device=gu.dev())
+        az.az_solve(h, gu.to_dev_cols(b), x)
+        xg = gu.from_dev_cols(x)
+    finally:
+        az.az_destroy(h)
+    r_o = relres(op, AZ(op, 24, 1, 1e-8).solve(b), b)
+    r_g = relres(op, xg, b)
+    assert np.all(np.abs(r_g - r_o) <= 1e-8), (r_g - r_o)
