@@ -75,8 +75,6 @@ struct az_setup_t {
   int32_t* scan = nullptr;
   double* samp[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [dim][phi, phi'']
   double* Gd[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
-  double2* c1 = nullptr;
-  double2* c2 = nullptr;
   double* Q1 = nullptr;     // Mtot x k
   double* Rd = nullptr;     // N x k (collocation sketch)
   double* r64 = nullptr;    // Mtot x cols (relres residual), lazily
@@ -254,10 +252,6 @@ az_status big_tables(az_setup_t* h, int64_t n, double2** A64, double2** B64, flo
   return AZ_OK;
 }
 
-__global__ void k_real_to_complex(const double* in, int64_t n, double2* out) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = make_double2(in[i], 0.0);
-}
 template <typename TI>
 __global__ void k_to_double(const TI* in, int64_t ldi, int64_t rows, int ncols, double* out, int64_t ldo) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -290,17 +284,13 @@ az_status alloc_symbol(az_setup_t* h) {
   const int nder = h->kind == 1 ? 2 : 1;
   for (int d = 0; d < g.dim; ++d)
     for (int q = 0; q < nder; ++q) {
-      AZ_TRY(dalloc_t(h, &h->samp[d][q], g.Ld[d]));
+      if (g.dim == 2) AZ_TRY(dalloc_t(h, &h->samp[d][q], g.Ld[d]));
       if (g.dim == 2) AZ_TRY(dalloc_t(h, &h->Gd[d][q], g.Ld[d]));
       AZ_TRY(dalloc_t(h, &h->taps64[d + 2 * q], 2 * h->W64[d] + 1));
       AZ_TRY(dalloc_t(h, &h->taps32[d + 2 * q], 2 * h->W32[d] + 1));
       AZ_TRY(dalloc_t(h, &h->tapsH[d + 2 * q], 2 * h->W64[d] + 1));
       AZ_TRY(dalloc_t(h, &h->tapsL[d + 2 * q], 2 * h->W64[d] + 1));
     }
-  if (g.dim == 1) {
-    AZ_TRY(dalloc_t(h, &h->c1, g.L));
-    AZ_TRY(dalloc_t(h, &h->c2, g.L));
-  }
   AZ_TRY(dalloc_t(h, &h->Ghat, g.L));
   AZ_TRY(dalloc_t(h, &h->S, g.N + 1));
   AZ_TRY(dalloc_t(h, &h->H64, g.L));
@@ -308,31 +298,28 @@ az_status alloc_symbol(az_setup_t* h) {
   return AZ_OK;
 }
 
-// S2: periodised samples (Eq. periodic_rbf), stencil taps, Ghat = DFT_L(g)
-// (Lemma 4.2), S_k = sum over the alias group of Ghat^2 and H = Ghat / S
+// S2: stencil taps of the periodised kernel (Eq. periodic_rbf), Ghat =
+// DFT_L(g) (Lemma 4.2; 1D in its Poisson-summation form, 2D as line DFTs of
+// the samples), S_k = sum over the alias group of Ghat^2 and H = Ghat / S
 // (Eq. B_pinv), stored in the row-pass layout.  Launches only.
 az_status build_symbol(az_setup_t* h, cudaStream_t st) {
   Geom& g = h->g;
   const double eps = h->eps;
   const int nder = h->kind == 1 ? 2 : 1;
-  for (int d = 0; d < g.dim; ++d)
-    for (int q = 0; q < nder; ++q) {
-      const double hL = 2.0 * g.T[d] / (double)g.Ld[d];
-      AZ_TRY(launch_samples(h->samp[d][q], g.Ld[d], hL, eps, q == 0 ? 0 : 2, image_count(eps, g.T[d]), st));
-      AZ_TRY(launch_taps(h->samp[d][q], g.Ld[d], h->W64[d], h->taps64[d + 2 * q], h->W32[d], h->taps32[d + 2 * q], st,
-                         h->tapsH[d + 2 * q], h->tapsL[d + 2 * q]));
-    }
   if (g.dim == 1) {
-    {
-      ProfScope ps("symbol", 24.0 * g.L, st);
-      k_real_to_complex<<<(unsigned)((g.L + 255) / 256), 256, 0, st>>>(h->samp[0][0], g.L, h->c1);
-      AZ_CUDA(cudaGetLastError());
-    }
-    PassTabs tb = tabs<double>(h);
-    AZ_TRY(launch_colfwd_load<double>(g, h->c1, 1, h->c2, tb, st));
-    AZ_TRY(launch_rowfft<double>(g, h->c2, 1, h->c1, tb, st));
-    AZ_TRY(launch_spec_to_natural(g, h->c1, h->Ghat, st));
+    // taps from the image sum; Ghat = DFT_L(g) in its Poisson-summation form
+    const double hL = 2.0 * g.T[0] / (double)g.Ld[0];
+    AZ_TRY(launch_taps_direct(g.Ld[0], hL, eps, image_count(eps, g.T[0]), h->W64[0], h->taps64[0], h->W32[0],
+                              h->taps32[0], st, h->tapsH[0], h->tapsL[0]));
+    AZ_TRY(launch_symbol_closed_1d(g.L, eps * hL, h->Ghat, st));
   } else {
+    for (int d = 0; d < g.dim; ++d)
+      for (int q = 0; q < nder; ++q) {
+        const double hL = 2.0 * g.T[d] / (double)g.Ld[d];
+        AZ_TRY(launch_samples(h->samp[d][q], g.Ld[d], hL, eps, q == 0 ? 0 : 2, image_count(eps, g.T[d]), st));
+        AZ_TRY(launch_taps(h->samp[d][q], g.Ld[d], h->W64[d], h->taps64[d + 2 * q], h->W32[d], h->taps32[d + 2 * q],
+                           st, h->tapsH[d + 2 * q], h->tapsL[d + 2 * q]));
+      }
     for (int d = 0; d < 2; ++d)
       for (int q = 0; q < nder; ++q) AZ_TRY(launch_line_dft_real(h->samp[d][q], (int)g.Ld[d], h->Gd[d][q], h->tw64, st));
     AZ_TRY(launch_symbol_full(g, h->kind, eps, h->Gd[0][0], h->Gd[1][0], h->Gd[0][1], h->Gd[1][1], h->Ghat, st));

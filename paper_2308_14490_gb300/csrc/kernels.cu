@@ -132,19 +132,25 @@ az_status launch_compact(const uint8_t* mask, int64_t L, int32_t* pos2m, int32_t
 }
 
 // ------------------------------------------------------------------ S2: samples, taps
+// g(m) = sum_p f((m + p L) h_L), f = phi or phi'' (Eq. periodic_rbf on the L-grid)
+__device__ double periodised_sample(int64_t m, int64_t L, double hL, double eps, int deriv, int pimg) {
+  m = ((m % L) + L) % L;
+  const double mm = (double)(m > L / 2 ? m - L : m);
+  const double e2 = eps * eps;
+  double acc = 0.0;
+  for (int p = -pimg; p <= pimg; ++p) {
+    const double r = (mm + (double)p * (double)L) * hL;
+    const double q = e2 * r * r;
+    if (q > 760.0) continue;   // exp(-q) underflows to zero in FP64
+    const double ex = exp(-q);
+    acc += deriv == 0 ? ex : -2.0 * e2 * ex * (1.0 - 2.0 * e2 * r * r);
+  }
+  return acc;
+}
 __global__ void k_samples(double* g, int64_t L, double hL, double eps, int deriv, int pimg) {
   int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= L) return;
-  double mm = (double)(m > L / 2 ? m - L : m);
-  double e2 = eps * eps, acc = 0.0;
-  for (int p = -pimg; p <= pimg; ++p) {
-    double r = (mm + (double)p * (double)L) * hL;
-    const double q = e2 * r * r;
-    if (q > 760.0) continue;   // exp(-q) underflows to zero in FP64
-    double ex = exp(-q);
-    acc += deriv == 0 ? ex : -2.0 * e2 * ex * (1.0 - 2.0 * e2 * r * r);
-  }
-  g[m] = acc;
+  g[m] = periodised_sample(m, L, hL, eps, deriv, pimg);
 }
 az_status launch_samples(double* g, int64_t L, double hL, double eps, int deriv, int pimg, cudaStream_t st) {
   ProfScope ps("samples", 8.0 * L, st);
@@ -161,6 +167,76 @@ __global__ void k_taps(const double* g, int64_t L, int W64, double* t64, int W32
   }
   if (i <= 2 * W32) t32[i] = (float)g[fmod_pos((int64_t)i - W32, L)];
 }
+// Taps straight from the image sum (1D: the L samples themselves are not needed)
+__global__ void k_taps_direct(int64_t L, double hL, double eps, int pimg, int W64, double* t64, int W32, float* t32,
+                              float* th, float* tl) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i <= 2 * W64) {
+    const double v = periodised_sample((int64_t)i - W64, L, hL, eps, 0, pimg);
+    t64[i] = v;
+    if (th) { const float h = (float)v; th[i] = h; tl[i] = (float)(v - (double)h); }
+  }
+  if (i <= 2 * W32) t32[i] = (float)periodised_sample((int64_t)i - W32, L, hL, eps, 0, pimg);
+}
+az_status launch_taps_direct(int64_t L, double hL, double eps, int pimg, int W64, double* t64, int W32, float* t32,
+                             cudaStream_t st, float* th, float* tl) {
+  const int W = W64 > W32 ? W64 : W32;
+  ProfScope ps("taps", 12.0 * (2 * W + 1), st);
+  k_taps_direct<<<(2 * W + 1 + 127) / 128, 128, 0, st>>>(L, hL, eps, pimg, W64, t64, W32, t32, th, tl);
+  AZ_LAUNCH_CHECK();
+  return AZ_OK;
+}
+
+// 1D symbol from the Poisson-summation form of DFT_L(g) (proof of Lemma 4.3):
+// with a = eps h_L and t = k/L taken in [-1/2, 1/2],
+//   Ghat_k = sqrt(pi)/a * sum_p exp(-(pi/a)^2 (t + p)^2),
+// which equals the DFT of the periodised samples to rounding (the oracle pins
+// both forms against each other).  A thread takes J consecutive k (never
+// across k = L/2, where t jumps) and, per image p, evaluates the Gaussian by
+// the exact recurrence E_{j+1} = E_j F_j, F_{j+1} = F_j Q (u_j = t_j + p,
+// F_j = exp(-c d (2 u_j + d)), Q = exp(-2 c d^2), d = 1/L): three FP64
+// exponentials per image and J outputs instead of one per output (FP64 exp is
+// slow on this part), at a cost of about 2J rounding units.
+constexpr int SYM_J = 16;
+__global__ void k_symbol_closed_1d(int64_t L, double a, int Q, int J, double* Ghat) {
+  const int64_t k0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * J;
+  if (k0 >= L) return;
+  const double c = (M_PI / a) * (M_PI / a);
+  const double d = 1.0 / (double)L;
+  const double t0 = (double)(k0 > L / 2 ? k0 - L : k0) * d;
+  double acc[SYM_J];
+#pragma unroll
+  for (int j = 0; j < SYM_J; ++j) acc[j] = 0.0;
+  const double q = exp(-2.0 * c * d * d);
+  for (int p = -Q; p <= Q; ++p) {
+    const double u0 = t0 + (double)p;
+    // the whole run lies where this image is below 2^-1074 of 1: skip it
+    const double umin = fmin(fabs(u0), fabs(u0 + (J - 1) * d));
+    if (u0 * (u0 + (J - 1) * d) > 0.0 && c * umin * umin > 745.0) continue;
+    double e = exp(-c * u0 * u0);
+    double f = exp(-c * d * (2.0 * u0 + d));
+#pragma unroll
+    for (int j = 0; j < SYM_J; ++j) {
+      if (j < J) acc[j] += e;
+      e *= f;
+      f *= q;
+    }
+  }
+  const double sc = sqrt(M_PI) / a;
+#pragma unroll
+  for (int j = 0; j < SYM_J; ++j)
+    if (j < J) Ghat[k0 + j] = sc * acc[j];
+}
+az_status launch_symbol_closed_1d(int64_t L, double a, double* Ghat, cudaStream_t st) {
+  const int Q = (int)std::ceil(0.5 + a * std::sqrt(745.0) / M_PI);
+  const int J = (L % (2 * SYM_J) == 0) ? SYM_J : 1;   // runs end at k = L/2
+  const int64_t nth = L / J;
+  ProfScope ps("symbol", 8.0 * L, st);
+  k_symbol_closed_1d<<<(unsigned)((nth + 255) / 256), 256, 0, st>>>(L, a, Q, J, Ghat);
+  AZ_LAUNCH_CHECK();
+  return AZ_OK;
+}
+
 az_status launch_taps(const double* g, int64_t L, int W64, double* t64, int W32, float* t32, cudaStream_t st,
                       float* th, float* tl) {
   const int W = W64 > W32 ? W64 : W32;
@@ -385,24 +461,6 @@ __global__ void __launch_bounds__(256) k_colfwd_gather(Geom g, const int32_t* __
   colfwd_finish<T>(g, s0, s1, logC, c0, X1, tb);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_colfwd_load(Geom g, const typename C2<T>::t* __restrict__ inbase, int logC,
-                                                     typename C2<T>::t* X1base, PassTabs tb) {
-  using V = typename C2<T>::t;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int C = 1 << logC, Cm = C - 1;
-  V* s0 = (V*)smem_raw;
-  V* s1 = s0 + (size_t)g.D0 * C;
-  const int c0 = blockIdx.x * C;
-  const V* in = inbase + (int64_t)blockIdx.y * g.L;
-  V* X1 = X1base + (int64_t)blockIdx.y * g.L;
-  const int total = g.D0 << logC;
-  for (int t = threadIdx.x; t < total; t += blockDim.x) {
-    const int c = t & Cm, n0 = t >> logC;
-    s0[t] = in[(n0 << g.logD1) + c0 + c];
-  }
-  colfwd_finish<T>(g, s0, s1, logC, c0, X1, tb);
-}
 
 template <typename T>
 az_status launch_colfwd_stencil_v1(const Geom& g, const SketchIn<T>& in, int pair0, int npairs,
@@ -431,19 +489,6 @@ az_status launch_colfwd_gather_v1(const Geom& g, const int32_t* pos2m, const TB*
   AZ_LAUNCH_CHECK();
   return AZ_OK;
 }
-template <typename T>
-az_status launch_colfwd_load(const Geom& g, const typename C2<T>::t* in, int npairs,
-                             typename C2<T>::t* X1, const PassTabs& tb, cudaStream_t st) {
-  using V = typename C2<T>::t;
-  int C = col_tile<V>(g.D0, g.D1);
-  size_t sm = 2 * (size_t)g.D0 * C * sizeof(V);
-  if (set_smem(k_colfwd_load<T>, sm) != cudaSuccess) { set_error("smem attribute"); return AZ_ERR_CUDA; }
-  dim3 grid(g.D1 / C, npairs);
-  ProfScope ps("colfwd_load", 2.0 * npairs * g.L * sizeof(V), st);
-  k_colfwd_load<T><<<grid, 256, sm, st>>>(g, in, ilog2i(C), X1, tb);
-  AZ_LAUNCH_CHECK();
-  return AZ_OK;
-}
 
 // ------------------------------------------------------------------ row passes
 template <typename V> static int row_groups_per_cta(const Geom& g) {
@@ -456,39 +501,6 @@ template <typename V> static int row_groups_per_cta(const Geom& g) {
   return p;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_rowfft(Geom g, const typename C2<T>::t* __restrict__ X1base, int logGPB,
-                                                typename C2<T>::t* X2base, PassTabs tb) {
-  using V = typename C2<T>::t;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int GPB = 1 << logGPB;
-  V* s0 = (V*)smem_raw;
-  V* s1 = s0 + (size_t)GPB * g.D1;
-  const V* X1 = X1base + (int64_t)blockIdx.y * g.L;
-  V* X2 = X2base + (int64_t)blockIdx.y * g.L;
-  const int r0 = blockIdx.x * GPB;
-  const int total = GPB << g.logD1;
-  for (int t = threadIdx.x; t < total; t += blockDim.x) s0[t] = X1[(r0 << g.logD1) + t];
-  __syncthreads();
-  int cur = fft_lines<V, false>(s0, s1, g.logD1, logGPB, g.D1, 1, (const V*)tb.tw, TW_N >> g.logD1);
-  V* res = cur ? s1 : s0;
-  for (int t = threadIdx.x; t < total; t += blockDim.x) X2[(r0 << g.logD1) + t] = res[t];
-}
-template <typename T>
-az_status launch_rowfft(const Geom& g, const typename C2<T>::t* X1, int npairs, typename C2<T>::t* X2,
-                        const PassTabs& tb, cudaStream_t st) {
-  using V = typename C2<T>::t;
-  if (g.dim != 1) return AZ_ERR_ARG;
-  int GPB = 1;
-  while (GPB * 2 * 2 * (size_t)g.D1 * sizeof(V) <= 65536 && GPB * 2 <= 8 && g.D0 % (GPB * 2) == 0) GPB *= 2;
-  size_t sm = 2 * (size_t)GPB * g.D1 * sizeof(V);
-  if (set_smem(k_rowfft<T>, sm) != cudaSuccess) { set_error("smem attribute"); return AZ_ERR_CUDA; }
-  dim3 grid(g.D0 / GPB, npairs);
-  ProfScope ps("rowfft", 2.0 * npairs * g.L * sizeof(V), st);
-  k_rowfft<T><<<grid, 256, sm, st>>>(g, X1, ilog2i(GPB), X2, tb);
-  AZ_LAUNCH_CHECK();
-  return AZ_OK;
-}
 
 // Row pass of the sketch / solve: forward FFT of each group's rows, fold of the
 // alias group with H = Ghat/S (Eq. B_pinv), inverse FFT of length N1, twiddle
@@ -1011,18 +1023,6 @@ az_status launch_max_abs(const double* v, int64_t n, double* out, cudaStream_t s
   AZ_LAUNCH_CHECK();
   return AZ_OK;
 }
-__global__ void k_spec_to_natural(Geom g, const double2* X, double* out) {
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= g.L) return;
-  int64_t k0 = t / g.D1, k1 = t % g.D1;
-  out[k0 + (int64_t)g.D0 * k1] = X[t].x;
-}
-az_status launch_spec_to_natural(const Geom& g, const double2* X, double* out, cudaStream_t st) {
-  ProfScope ps("symbol", 24.0 * g.L, st);
-  k_spec_to_natural<<<(unsigned)((g.L + 255) / 256), 256, 0, st>>>(g, X, out);
-  AZ_LAUNCH_CHECK();
-  return AZ_OK;
-}
 __global__ void k_line_dft_real(const double* in, int logn, double* out, const double2* tw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = 1 << logn;
@@ -1479,13 +1479,6 @@ INST_R(float)
 INST_R(double)
 
 // ------------------------------------------------------------------ explicit instantiations
-#define INST_T(T)                                                                                           \
-  template az_status launch_colfwd_load<T>(const Geom&, const C2<T>::t*, int, C2<T>::t*, const PassTabs&,    \
-                                           cudaStream_t);                                                   \
-  template az_status launch_rowfft<T>(const Geom&, const C2<T>::t*, int, C2<T>::t*, const PassTabs&,        \
-                                      cudaStream_t);
-INST_T(float)
-INST_T(double)
 
 #define INST_ST(T, TZ, TB, TO)                                                                              \
   template az_status launch_stencil_rows<T, TZ, TB, TO>(const Geom&, int, double, const int32_t*, int64_t,  \

@@ -12,6 +12,10 @@ az_status launch_compact(const uint8_t* mask, int64_t L, int32_t* pos2m, int32_t
 // S2: periodised samples g(m) = sum_p f((m + p L) h_L) on one dimension
 // (f = phi or phi''), FP64, m = 0..L-1.
 az_status launch_samples(double* g, int64_t L, double hL, double eps, int deriv, int pimg, cudaStream_t st);
+// 1D: stencil taps from the image sum, and Ghat from its Poisson-summation form
+az_status launch_taps_direct(int64_t L, double hL, double eps, int pimg, int W64, double* t64, int W32, float* t32,
+                             cudaStream_t st, float* th, float* tl);
+az_status launch_symbol_closed_1d(int64_t L, double a, double* Ghat, cudaStream_t st);
 // stencil taps t[m + W] = g(m mod L) for |m| <= W, FP64 and FP32 copies
 az_status launch_taps(const double* g, int64_t L, int W64, double* t64, int W32, float* t32, cudaStream_t st,
                       float* th = nullptr, float* tl = nullptr);
@@ -50,13 +54,6 @@ template <typename T, typename TB>
 az_status launch_colfwd_gather(const Geom& g, const int32_t* pos2m, const TB* b, int64_t ldb, int ncols,
                                int pair0, int npairs, typename C2<T>::t* X1, const PassTabs& tb,
                                cudaStream_t st, int64_t M_rows);
-template <typename T>
-az_status launch_colfwd_load(const Geom& g, const typename C2<T>::t* in, int npairs,
-                             typename C2<T>::t* X1, const PassTabs& tb, cudaStream_t st);
-// Row pass: plain forward FFT of the rows (spectrum layout out)
-template <typename T>
-az_status launch_rowfft(const Geom& g, const typename C2<T>::t* X1, int npairs, typename C2<T>::t* X2,
-                        const PassTabs& tb, cudaStream_t st);
 // Row pass with the alias-group fold by H = Ghat * S^{-1}: output on the N-grid (npairs x N complex)
 template <typename T>
 az_status launch_rowfold(const Geom& g, const typename C2<T>::t* X1, const T* H, int npairs,
@@ -95,7 +92,6 @@ az_status launch_H(const Geom& g, const double* Ghat, const double* S, double th
                    cudaStream_t st);
 az_status launch_max_abs(const double* v, int64_t n, double* out, cudaStream_t st);
 // Take the real part of a spectrum (1D four-step layout -> natural frequency order)
-az_status launch_spec_to_natural(const Geom& g, const double2* X, double* out, cudaStream_t st);
 // One-line FFT (length n <= 4096) of a real FP64 array: out = Re(DFT(in))
 az_status launch_line_dft_real(const double* in, int n, double* out, const double2* tw, cudaStream_t st);
 

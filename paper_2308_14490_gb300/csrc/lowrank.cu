@@ -579,18 +579,29 @@ __global__ void k_factor2(const double* __restrict__ G2, int k, const double* __
     sg[j] = sqrt(sacc);
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < r1; ++i) {
-      int best = i;
-      for (int j = i + 1; j < r1; ++j) if (sg[j] > sg[best]) best = j;
-      if (best != i) {
-        double u = sg[i]; sg[i] = sg[best]; sg[best] = u;
-        for (int rr = 0; rr < k; ++rr) { u = A[i * k + rr]; A[i * k + rr] = A[best * k + rr]; A[best * k + rr] = u; }
-        for (int rr = 0; rr < r1; ++rr) { u = VR[i * r1 + rr]; VR[i * r1 + rr] = VR[best * r1 + rr]; VR[best * r1 + rr] = u; }
-      }
+  // stable rank of each column (larger norm first, ties by index), then a
+  // parallel permutation through the scratch above sg
+  {
+    int* rank = (int*)(sg + k);
+    double* tmp = (double*)(rank + k + (k & 1));
+    for (int j = threadIdx.x; j < r1; j += blockDim.x) {
+      int rj = 0;
+      for (int i = 0; i < r1; ++i) rj += (sg[i] > sg[j]) || (sg[i] == sg[j] && i < j);
+      rank[j] = rj;
     }
+    __syncthreads();
+    for (int t = threadIdx.x; t < r1 * k; t += blockDim.x) tmp[rank[t / k] * k + t % k] = A[t];
+    __syncthreads();
+    for (int t = threadIdx.x; t < r1 * k; t += blockDim.x) A[t] = tmp[t];
+    __syncthreads();
+    for (int t = threadIdx.x; t < r1 * r1; t += blockDim.x) tmp[rank[t / r1] * r1 + t % r1] = VR[t];
+    double sgv = 0.0;
+    if (threadIdx.x < r1) sgv = sg[threadIdx.x];
+    __syncthreads();
+    for (int t = threadIdx.x; t < r1 * r1; t += blockDim.x) VR[t] = tmp[t];
+    if (threadIdx.x < r1) sg[rank[threadIdx.x]] = sgv;
+    __syncthreads();
   }
-  __syncthreads();
   __shared__ int rs;
   if (threadIdx.x == 0) {
     int r = 0;
@@ -625,7 +636,9 @@ __global__ void k_factor2(const double* __restrict__ G2, int k, const double* __
 az_status launch_factor2(const double* G2, int k, const double* V, const double* lam, double tau, double floor,
                          double* T, double* VS, double* sig, FactorInfo* info, cudaStream_t st, bool f32jac) {
   if (k > 64) { set_error("factor: k > 64 not supported by the one-CTA factorisation"); return AZ_ERR_ARG; }
-  size_t sm = (3 * (size_t)k * k + k) * sizeof(double) + 2 * (size_t)k * k * sizeof(float);
+  // R, A, VR, sg, then the FP32 Jacobi copies or the sort's rank + scratch
+  size_t sm = (3 * (size_t)k * k + k) * sizeof(double) +
+              std::max(2 * (size_t)k * k * sizeof(float), (size_t)(k + 1) * sizeof(int) + sizeof(int) + (size_t)k * k * sizeof(double));
   smem_once(k_factor2, sm);
   ProfScope ps("factor2", 0.0, st);
   (void)lam;
