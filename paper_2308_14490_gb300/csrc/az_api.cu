@@ -634,6 +634,16 @@ az_status az_setup(const az_grid* gr, const uint8_t* mask, const double* bpts, i
     h->Mtot = M + h->Mb;
     h->ldm = (h->Mtot + 31) / 32 * 32;
     if (h->Mtot < 1) { set_error("az_setup: Omega contains no grid point"); rc = AZ_ERR_ARG; break; }
+    if (M > 0) {
+      // kept points forming one run of consecutive grid indices (a 1D
+      // interval): the gather then needs no index-map lookups
+      int32_t ends[2] = {0, 0};
+      if (cudaMemcpy(&ends[0], h->idx, sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess ||
+          cudaMemcpy(&ends[1], h->idx + (M - 1), sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        set_error("az_setup: reading the index map failed"); rc = AZ_ERR_CUDA; break;
+      }
+      if ((int64_t)ends[1] - ends[0] + 1 == M) { h->g.run0 = ends[0]; h->g.runM = M; }
+    }
     if (h->Mb) {
       rc = dalloc_t(h, &h->bpts, 2 * h->Mb); if (rc) break;
       if (cudaMemcpyAsync(h->bpts, bpts, 2 * h->Mb * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess) { rc = AZ_ERR_CUDA; break; }

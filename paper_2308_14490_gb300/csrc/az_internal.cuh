@@ -120,6 +120,9 @@ struct Geom {
   int Rg, Rstride, Fq;        // fold: rows per group, row stride, within-row alias count
   int Wst32[2], Wst64[2];     // stencil half-widths (grid units of the L-grid)
   int logN, logs[2], logn[2], logLd[2], logRg;
+  // kept grid points: when they are the run [run0, run0 + runM) of grid
+  // indices (runM > 0), row m of b is grid point run0 + m
+  int64_t run0, runM;
 };
 
 // Device tables owned by a setup.

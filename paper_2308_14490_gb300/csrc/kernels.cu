@@ -758,25 +758,48 @@ __global__ void __launch_bounds__(256) k_resid_df(Geom g, int kind, double inv2e
                                                   const double* __restrict__ bb, int64_t ldb, float* __restrict__ out,
                                                   int64_t ldo, int ncols) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= M) return;
+  const bool act = m < M;
   const int cbase = blockIdx.y * CPT;
   const int nc = min(CPT, ncols - cbase);
-  const int i = __ldg(idx + m);
+  const int i = act ? __ldg(idx + m) : 0;
   DFa acc[CPT];
 #pragma unroll
   for (int c = 0; c < CPT; ++c) { acc[c].hi = 0.f; acc[c].lo = 0.f; }
   if (g.dim == 1) {
     const int ls = g.logs[0], s = g.s[0], Nm = (int)g.N - 1;
     const int jlo = cdiv_p2(i - Wx, ls), jhi = fdiv_p2(i + Wx, ls);
-    for (int j = jlo; j <= jhi; ++j) {
-      const int ti = i - s * j + Wx;
-      const float th = __ldg(x0h + ti), tl = __ldg(x0l + ti);
-      const int jj = j & Nm;
+    // the block's window of x staged in shared memory (as in k_stencil_rows)
+    const int m0 = blockIdx.x * blockDim.x;
+    const int m1 = min(M, m0 + (int)blockDim.x) - 1;
+    const int wlo = cdiv_p2(__ldg(idx + m0) - Wx, ls), whi = fdiv_p2(__ldg(idx + m1) + Wx, ls);
+    const int nwin = whi - wlo + 1;
+    __shared__ float swin[CPT * STENCIL_WIN];
+    if (nwin <= STENCIL_WIN) {
+      for (int t = threadIdx.x; t < nc * nwin; t += blockDim.x) {
+        const int c = t / nwin, o = t - c * nwin;
+        swin[c * STENCIL_WIN + o] = xf[(int64_t)(cbase + c) * ldx + ((wlo + o) & Nm)];
+      }
+      __syncthreads();
+      if (act) {
+        for (int j = jlo; j <= jhi; ++j) {
+          const int ti = i - s * j + Wx;
+          const float th = __ldg(x0h + ti), tl = __ldg(x0l + ti);
 #pragma unroll
-      for (int c = 0; c < CPT; ++c)
-        if (c < nc) dfa_add(acc[c], __ldg(xf + (int64_t)(cbase + c) * ldx + jj), th, tl);
+          for (int c = 0; c < CPT; ++c)
+            if (c < nc) dfa_add(acc[c], swin[c * STENCIL_WIN + (j - wlo)], th, tl);
+        }
+      }
+    } else if (act) {
+      for (int j = jlo; j <= jhi; ++j) {
+        const int ti = i - s * j + Wx;
+        const float th = __ldg(x0h + ti), tl = __ldg(x0l + ti);
+        const int jj = j & Nm;
+#pragma unroll
+        for (int c = 0; c < CPT; ++c)
+          if (c < nc) dfa_add(acc[c], __ldg(xf + (int64_t)(cbase + c) * ldx + jj), th, tl);
+      }
     }
-  } else {
+  } else if (act) {
     const int sx = g.s[0], sy = g.s[1];
     const int Nxm = (int)g.n[0] - 1, Nym = (int)g.n[1] - 1, lNy = g.logn[1];
     const int ix = i >> g.logD1, iy = i & (g.D1 - 1);
@@ -809,6 +832,7 @@ __global__ void __launch_bounds__(256) k_resid_df(Geom g, int kind, double inv2e
       }
     }
   }
+  if (!act) return;
 #pragma unroll
   for (int c = 0; c < CPT; ++c) {
     if (c < nc) {
@@ -1133,6 +1157,15 @@ __device__ __forceinline__ Geom fix_geom(const Geom& g) {
   }
   return r;
 }
+// Row of b for grid point pos, or -1 outside Omega: arithmetic when the kept
+// points are one run of grid indices, else the index map.
+__device__ __forceinline__ int kept_row(const Geom& g, const int32_t* __restrict__ pos2m, int pos) {
+  if (g.runM > 0) {
+    const int64_t m = (int64_t)pos - g.run0;
+    return (m >= 0 && m < g.runM) ? (int)m : -1;
+  }
+  return __ldg(pos2m + pos);
+}
 // Host side: the fixed shape a launch may use (config-2 scale: L = 2^21, s = 2)
 static bool is_shape_21_1(const Geom& g) { return g.dim == 1 && g.L == ((int64_t)1 << 21) && g.s[0] == 2; }
 
@@ -1187,7 +1220,7 @@ __global__ void __launch_bounds__(REG_THREADS, REG_MINB) k_colfwd_r(Geom g_in, c
       const int c = t & (C - 1), p = t >> logC;
       const int pos = (p << g.logD1) + c0 + c;
       V v; v.x = 0; v.y = 0;
-      if (__ldg(pos2m + pos) >= 0) {
+      if (kept_row(g, pos2m, pos) >= 0) {
         if (g.dim == 1) {
           const int ls = g.logs[0], s = g.s[0], Nm = (int)g.N - 1, W = in.Wx;
           const int jlo = cdiv_p2(pos - W, ls), jhi = fdiv_p2(pos + W, ls);
@@ -1217,7 +1250,7 @@ __global__ void __launch_bounds__(REG_THREADS, REG_MINB) k_colfwd_r(Geom g_in, c
     if (MODE == 1) return sm[padix<PADC>((p << logC) + line)];
     const int pos = (p << g.logD1) + n1;
     V v; v.x = 0; v.y = 0;
-    const int m = __ldg(pos2m + pos);
+    const int m = kept_row(g, pos2m, pos);
     if (m < 0) return v;
     v.x = cvt<T>(bA[m]);
     if (colB < ncols) v.y = cvt<T>(bB[m]);
