@@ -646,6 +646,10 @@ __global__ void __launch_bounds__(256) k_stencil_rows(Geom g, int kind, T inv2e2
   const int cbase = blockIdx.y * CPT;
   const int nc = min(CPT, ncols - cbase);
   const int i = act ? __ldg(idx + m) : 0;
+  // the b values are independent of the stencil: issue their loads first
+  TB bv[CPT];
+#pragma unroll
+  for (int c = 0; c < CPT; ++c) bv[c] = (bb && act && c < nc) ? bb[(int64_t)(cbase + c) * ldb + m] : (TB)0;
   T acc[CPT];
 #pragma unroll
   for (int c = 0; c < CPT; ++c) acc[c] = 0;
@@ -708,7 +712,7 @@ __global__ void __launch_bounds__(256) k_stencil_rows(Geom g, int kind, T inv2e2
   for (int c = 0; c < CPT; ++c) {
     if (c < nc) {
       T r = beta * acc[c];
-      if (bb) r += alpha * cvt<T>(bb[(int64_t)(cbase + c) * ldb + m]);
+      if (bb) r += alpha * cvt<T>(bv[c]);
       outb[(int64_t)(cbase + c) * ldo + m] = cvt<TO>(r);
     }
   }
