@@ -233,15 +233,31 @@ def fp64_torch_comparator(p, b_dev, steps=2, warmup=1):
 def serving_leg(seconds):
     """The mixed request stream: Poisson arrivals at 200/s of 1D / 2D approximations
     and 2D Poisson collocations drawn from a seeded pool of 32 setups, 1..32 RHS
-    each, continuous batching over 4 streams with CUDA-graph replay."""
+    each, continuous batching over 4 streams with CUDA-graph replay.  Three runs of
+    the same stream: mixed precision from a cold start (each setup built on its
+    first request), then mixed and all-FP64 with the pool built beforehand."""
+    import paper_2308_14490_gb300 as az
     import paper_2308_14490_gb300.serving as S
     pool = S.setup_pool(230814490, 32)
     reqs = S.poisson_stream(230814490, 200.0, seconds, pool)
-    srv = S.Server(64 << 30, nslots=4)
-    out = srv.run(reqs, realtime=True)
-    srv.close()
+    out = {}
+    for name, prec, warm in (("mixed_cold", az.AZ_MIXED, False), ("mixed_warm", az.AZ_MIXED, True),
+                             ("fp64_warm", az.AZ_FP64, True)):
+        srv = S.Server(64 << 30, nslots=4, precision=prec)
+        warm_ms = srv.warm(pool) if warm else 0.0
+        fresh = [S.Request(r.rid, r.arrival, r.spec, r.nrhs, r.seed) for r in reqs]
+        res = srv.run(fresh, realtime=True)
+        if warm:
+            res["warm_up_ms"] = warm_ms
+            # capacity: the same requests all queued at once (closed loop, no
+            # arrival gaps); only the throughput of this run is meaningful
+            again = [S.Request(r.rid, r.arrival, r.spec, r.nrhs, r.seed) for r in reqs]
+            cap = srv.run(again, realtime=False)
+            res["capacity_solves_per_s"] = cap["solves_per_s"]
+        srv.close()
+        out[name] = res
     out["stream"] = f"{len(reqs)} requests over {seconds:.0f} s (Poisson 200/s), pool of 32 setups; " \
-                    "2D setups use k <= 64 in this build"
+                    "2D setups use k = 64 (under-resolved, see the sketch-width reading)"
     return out
 
 

@@ -151,6 +151,10 @@ enum { AZ_ARRAY_SYMBOL = 0, AZ_ARRAY_SKETCH = 1, AZ_ARRAY_W = 2, AZ_ARRAY_R = 3,
        AZ_ARRAY_SIGMA = 5, AZ_ARRAY_KEPT = 6 };
 az_status az_get_array(az_handle h, int32_t which, double* dst_dev, void* stream);
 
+/* Sizes and factorisation results of a handle.  Waits (on the host) for the
+ * handle's latest factorisation (az_setup or az_refactor) only, not for solves
+ * in flight on other streams.  Returns AZ_ERR_CUDA if a solve that has
+ * completed raised the tensor-core pipeline's wait-timeout flag. */
 az_status az_get_info(az_handle h, az_info_t* info);
 
 /* Device bytes a setup of this size would hold (symbols, maps, sketch and

@@ -81,6 +81,7 @@ struct az_setup_t {
   double* bcoll = nullptr;  // Mtot x cols (scaled collocation data), lazily
   LargeK* wide = nullptr;   // k > 64: Householder QR + FP64 SVD + GEMM path
   int* tc_err = nullptr;    // set by a tensor-core pipeline wait that timed out
+  cudaEvent_t info_ev = nullptr;  // recorded after each factorisation (az_get_info waits on it)
 };
 
 namespace {
@@ -427,7 +428,9 @@ az_status sketch_and_factor(az_setup_t* h, cudaStream_t st) {
 az_status compute_setup(az_setup_t* h, cudaStream_t st, bool with_index_map) {
   if (with_index_map) AZ_TRY(launch_compact(h->mask, h->g.L, h->pos2m, h->idx, h->Md, h->scan, st));
   AZ_TRY(build_symbol(h, st));
-  return h->precision == AZ_FP64 ? sketch_and_factor<double>(h, st) : sketch_and_factor<float>(h, st);
+  AZ_TRY(h->precision == AZ_FP64 ? sketch_and_factor<double>(h, st) : sketch_and_factor<float>(h, st));
+  if (h->info_ev) AZ_CUDA(cudaEventRecord(h->info_ev, st));
+  return AZ_OK;
 }
 
 // One AZ solve of ncols columns (T precision): x (=|+=) Z* b + W VS U^T (b - A Z* b)
@@ -538,6 +541,7 @@ void destroy(az_setup_t* h) {
   if (h->r64) cudaFree(h->r64);
   if (h->bcoll) cudaFree(h->bcoll);
   if (h->wide) large_destroy(h->wide);
+  if (h->info_ev) cudaEventDestroy(h->info_ev);
   delete h;
 }
 
@@ -671,6 +675,7 @@ az_status az_setup(const az_grid* gr, const uint8_t* mask, const double* bpts, i
     rc = dalloc(h, &h->Y, (size_t)h->Mtot * h->k * tsz); if (rc) break;
     rc = dalloc(h, &h->Ut, (size_t)h->ldm * h->k * tsz); if (rc) break;
     rc = dalloc_t(h, &h->tc_err, 1); if (rc) break;
+    if (cudaEventCreateWithFlags(&h->info_ev, cudaEventDisableTiming) != cudaSuccess) { cudaGetLastError(); set_error("event"); rc = AZ_ERR_CUDA; break; }
     if (cudaMemsetAsync(h->tc_err, 0, sizeof(int), st) != cudaSuccess) { cudaGetLastError(); set_error("memset"); rc = AZ_ERR_CUDA; break; }
     rc = dalloc_t(h, &h->Q1, (size_t)h->Mtot * h->k); if (rc) break;
     if (h->kind == 1) { rc = dalloc_t(h, &h->Rd, (size_t)g.N * h->k); if (rc) break; }
@@ -785,7 +790,8 @@ az_status az_get_info(az_handle h, az_info_t* info) {
   if (!h || !info) { set_error("az_get_info: bad arguments"); return AZ_ERR_ARG; }
   FactorInfo fi;
   int tcerr = 0;
-  AZ_CUDA(cudaDeviceSynchronize());
+  // waits for the latest factorisation only, not for other streams' work
+  AZ_CUDA(cudaEventSynchronize(h->info_ev));
   AZ_CUDA(cudaMemcpy(&fi, h->info, sizeof(fi), cudaMemcpyDeviceToHost));
   AZ_CUDA(cudaMemcpy(&tcerr, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
   if (tcerr) { set_error(tc_wait_message(tcerr)); return AZ_ERR_CUDA; }

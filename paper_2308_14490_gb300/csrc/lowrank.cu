@@ -286,6 +286,8 @@ az_status launch_tsprod_df(const float* A, int64_t lda, int k, const double* S, 
     TO* oc = out + (int64_t)c0 * ldo;
     if (rc <= 16) {
       k_tsprod_df<TO, 16><<<grid, 128, 2 * (size_t)k * 16 * sizeof(float), st>>>(A, lda, k, Sc, rc, M, oc, ldo);
+    } else if (rc <= 24) {
+      k_tsprod_df<TO, 24><<<grid, 128, 2 * (size_t)k * 24 * sizeof(float), st>>>(A, lda, k, Sc, rc, M, oc, ldo);
     } else {
       k_tsprod_df<TO, 32><<<grid, 128, 2 * (size_t)k * 32 * sizeof(float), st>>>(A, lda, k, Sc, rc, M, oc, ldo);
     }

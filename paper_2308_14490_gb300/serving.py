@@ -13,6 +13,11 @@
   up; each slot is its own CUDA stream, so batches of different setups overlap
   on the device while new requests keep arriving.
 * Each (setup, bucket) solve is captured once into a CUDA graph and replayed.
+* Optional warm start: ``Server.warm`` builds a known pool of setups (and
+  captures their graphs) before requests arrive, so that the stream measures
+  steady-state serving; a cold run builds each setup on its first request.
+* ``precision`` selects the mixed (FP32 sketch and transforms, FP64 factor and
+  residual) or the all-FP64 path for every setup of the server.
 
 Right-hand sides are generated on the device from each request's seeded
 parameters (workload inputs, not solver arithmetic).
@@ -27,7 +32,7 @@ from dataclasses import dataclass, field
 import numpy as np
 import torch
 
-from . import (AZ_ERR_ADMISSION, AZ_GAUSS, AZ_MIXED, AZ_NEG_LAPLACE_GAUSS, AZError, az_destroy, az_get_info,
+from . import (AZ_ERR_ADMISSION, AZ_FP64, AZ_GAUSS, AZ_MIXED, AZ_NEG_LAPLACE_GAUSS, AZError, az_destroy, az_get_info,
                az_query_footprint, az_setup, az_solve, make_grid, make_options)
 
 BUCKETS = (2, 4, 8, 16, 32, 64)
@@ -75,7 +80,7 @@ class _Setup:
 
 class Server:
     def __init__(self, budget_bytes: int, nslots: int = 4, use_graphs: bool = True, device=None,
-                 keep_results: bool = False):
+                 keep_results: bool = False, precision: int = AZ_MIXED):
         self.dev = device or torch.device("cuda", torch.cuda.current_device())
         self.setup_stream = torch.cuda.Stream(device=self.dev)
         self.keep_results = keep_results
@@ -91,6 +96,8 @@ class Server:
         self.setup_builds = 0
         self.evictions = 0
         self.high_water = 0
+        self.precision = precision
+        self.build_ms = []                 # wall time of each setup build (host view)
 
     # ------------------------------------------------------------------ setups
     def _grid_coords(self, spec):
@@ -101,7 +108,8 @@ class Server:
         return cs
 
     def _build(self, spec: SetupSpec):
-        opts = make_options(AZ_MIXED, spec.k, 1e-8, 0.0, 1, 1)
+        t_build = time.perf_counter()
+        opts = make_options(self.precision, spec.k, 1e-8, 0.0, 1, 1 if self.precision == AZ_MIXED else 0)
         grid = make_grid(spec.dim, spec.n, spec.s, spec.T)
         cs = self._grid_coords(spec)
         if spec.dim == 1:
@@ -139,7 +147,20 @@ class Server:
         self.used += st.bytes
         self.setup_builds += 1
         self.high_water = max(self.high_water, self.used)
+        self.build_ms.append(1000.0 * (time.perf_counter() - t_build))
         return st
+
+    def warm(self, specs, buckets=BUCKETS):
+        """Build the given setups and capture their solve graphs before serving."""
+        t0 = time.perf_counter()
+        for spec in specs:
+            st = self.setups.get(spec.key) or self._build(spec)
+            if st is None:
+                continue
+            for b in buckets:
+                self._graph(st, b, self.slots[0])
+        torch.cuda.synchronize(self.dev)
+        return 1000.0 * (time.perf_counter() - t0)
 
     def _evict(self, st: _Setup):
         st.graphs.clear()
@@ -282,6 +303,9 @@ class Server:
                 "elapsed_s": elapsed, "solves_per_s": solves / elapsed if elapsed > 0 else None,
                 "latency_ms": {"p50": pct(0.50), "p99": pct(0.99), "max": lat[-1] if lat else None},
                 "setup_builds": self.setup_builds, "evictions": self.evictions,
+                "build_ms": {"p50": float(np.median(self.build_ms)) if self.build_ms else None,
+                             "max": max(self.build_ms) if self.build_ms else None},
+                "precision": "mixed" if self.precision == AZ_MIXED else "fp64",
                 "device_bytes_high_water": self.high_water}
 
 
