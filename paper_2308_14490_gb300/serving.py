@@ -13,6 +13,8 @@
   up; each slot is its own CUDA stream, so batches of different setups overlap
   on the device while new requests keep arriving.
 * Each (setup, bucket) solve is captured once into a CUDA graph and replayed.
+  A bucket's first solve runs eagerly; its capture (which waits for the whole
+  device) is deferred to a moment when no request is queued or running.
 * Optional warm start: ``Server.warm`` builds a known pool of setups (and
   captures their graphs) before requests arrive, so that the stream measures
   steady-state serving; a cold run builds each setup on its first request.
@@ -98,6 +100,11 @@ class Server:
         self.high_water = 0
         self.precision = precision
         self.build_ms = []                 # wall time of each setup build (host view)
+        self.pending_capture = collections.deque()   # (setup key, bucket) solved eagerly, not yet captured
+        # process warm-up (library handles and kernels of the right-hand-side
+        # generator), so that the first request does not pay for it
+        a = torch.ones((8, 2), dtype=torch.float64, device=self.dev)
+        torch.cos(a @ a.T).sum().item()
 
     # ------------------------------------------------------------------ setups
     def _grid_coords(self, spec):
@@ -196,22 +203,37 @@ class Server:
     def _solve_fn(self, st, b_buf, x_buf, stream):
         az_solve(st.h, b_buf, x_buf, stream)
 
-    def _graph(self, st: _Setup, bucket: int, stream):
-        if bucket in st.graphs:
-            return st.graphs[bucket]
-        rows = st.info["M"] + st.info["Mb"]
-        b_buf = torch.zeros((bucket, rows), dtype=torch.float64, device=self.dev)
-        x_buf = torch.zeros((bucket, st.info["N"]), dtype=torch.float64, device=self.dev)
-        graph = None
-        if self.use_graphs:
+    def _graph(self, st: _Setup, bucket: int, stream, capture: bool = True):
+        """(graph or None, b_buf, x_buf) of a bucket; captures only when asked."""
+        ent = st.graphs.get(bucket)
+        if ent is None:
+            rows = st.info["M"] + st.info["Mb"]
+            b_buf = torch.zeros((bucket, rows), dtype=torch.float64, device=self.dev)
+            x_buf = torch.zeros((bucket, st.info["N"]), dtype=torch.float64, device=self.dev)
+            ent = (None, b_buf, x_buf)
+            st.graphs[bucket] = ent
+            if self.use_graphs and not capture:
+                self.pending_capture.append((st.spec.key, bucket))
+        if ent[0] is None and self.use_graphs and capture:
+            _, b_buf, x_buf = ent
             with torch.cuda.stream(stream):
                 self._solve_fn(st, b_buf, x_buf, stream)           # warm up (attribute set-up)
             stream.synchronize()
             graph = torch.cuda.CUDAGraph()
             with torch.cuda.graph(graph, stream=stream):
                 self._solve_fn(st, b_buf, x_buf, torch.cuda.current_stream())
-        st.graphs[bucket] = (graph, b_buf, x_buf)
-        return st.graphs[bucket]
+            ent = (graph, b_buf, x_buf)
+            st.graphs[bucket] = ent
+        return ent
+
+    def _capture_one(self):
+        """Capture one deferred graph (called only while the server is idle)."""
+        while self.pending_capture:
+            key, bucket = self.pending_capture.popleft()
+            st = self.setups.get(key)
+            if st is not None and bucket in st.graphs and st.graphs[bucket][0] is None:
+                self._graph(st, bucket, self.slots[0], capture=True)
+                return
 
     def _dispatch(self, slot: int, key, now_fn):
         q = self.queue[key]
@@ -235,7 +257,7 @@ class Server:
             del self.queue[key]
         bucket = next(b for b in BUCKETS if b >= ncols)
         stream = self.slots[slot]
-        graph, b_buf, x_buf = self._graph(st, bucket, stream)
+        graph, b_buf, x_buf = self._graph(st, bucket, stream, capture=False)
         with torch.cuda.stream(stream):
             b_buf.zero_()
             self._rhs(st, reqs, b_buf)
@@ -290,6 +312,9 @@ class Server:
             idle = all(b is None for b in self.slot_busy)
             if i >= n and not self.queue and idle:
                 break
+            if idle and not self.queue and self.pending_capture:
+                self._capture_one()
+                continue
             if realtime and i < n and not self.queue and idle:
                 time.sleep(max(0.0, min(0.001, reqs[i].arrival - now())))
         elapsed = now()
