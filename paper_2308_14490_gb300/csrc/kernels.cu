@@ -1174,7 +1174,7 @@ __device__ __forceinline__ int kept_row(const Geom& g, const int32_t* __restrict
 static bool is_shape_21_1(const Geom& g) { return g.dim == 1 && g.L == ((int64_t)1 << 21) && g.s[0] == 2; }
 
 template <typename T, int MODE, typename TB, class S>
-__global__ void __launch_bounds__(REG_THREADS, REG_MINB) k_colfwd_r(Geom g_in, const int32_t* __restrict__ pos2m, const TB* __restrict__ b,
+__global__ void __launch_bounds__(REG_THREADS, S::fixed ? 4 : REG_MINB) k_colfwd_r(Geom g_in, const int32_t* __restrict__ pos2m, const TB* __restrict__ b,
                                                   int64_t ldb, int ncols, SketchIn<T> in, int pair0, int logC_in,
                                                   typename C2<T>::t* X1base, PassTabs tb) {
   const Geom g = fix_geom<S>(g_in);
@@ -1345,7 +1345,7 @@ __global__ void __launch_bounds__(REG_THREADS, REG_MINB) k_rowfold_r(Geom g_in, 
 }
 
 template <typename T, typename TO, bool WMODE, class S>
-__global__ void __launch_bounds__(REG_THREADS, REG_MINB) k_colinv_r(Geom g_in, const typename C2<T>::t* __restrict__ X3base, int pair0,
+__global__ void __launch_bounds__(REG_THREADS, S::fixed ? 4 : REG_MINB) k_colinv_r(Geom g_in, const typename C2<T>::t* __restrict__ X3base, int pair0,
                                                   int ncols, int logC_in, TO* __restrict__ out, int64_t ldo,
                                                   const uint32_t* __restrict__ bits, int64_t nw, PassTabs tb) {
   const Geom g = fix_geom<S>(g_in);
