@@ -1228,11 +1228,32 @@ __global__ void __launch_bounds__(REG_THREADS, S::fixed ? 4 : REG_MINB) k_colfwd
         if (g.dim == 1) {
           const int ls = g.logs[0], s = g.s[0], Nm = (int)g.N - 1, W = in.Wx;
           const int jlo = cdiv_p2(pos - W, ls), jhi = fdiv_p2(pos + W, ls);
-          for (int j = jlo; j <= jhi; ++j) {
-            const T tap = __ldg(in.tapx + (pos - s * j + W));
-            const int jj = j & Nm;
-            v.x += tap * (T)rad_bit(in.bits, in.nw, jj, colA);
-            if (hasB) v.y += tap * (T)rad_bit(in.bits, in.nw, jj, colB);
+          if (jlo >= 0 && jhi < (int)g.N && jhi - jlo < 32) {
+            // no wrap-around and at most 33 bits: two words per column hold
+            // every R entry of the window
+            const int w0 = jlo >> 5;
+            const int64_t nw = in.nw;
+            const uint32_t* ba = in.bits + (int64_t)colA * nw + w0;
+            const uint64_t bitsA = (uint64_t)__ldg(ba) | ((int64_t)(w0 + 1) < nw ? (uint64_t)__ldg(ba + 1) << 32 : 0ull);
+            uint64_t bitsB = 0;
+            if (hasB) {
+              const uint32_t* bbp = in.bits + (int64_t)colB * nw + w0;
+              bitsB = (uint64_t)__ldg(bbp) | ((int64_t)(w0 + 1) < nw ? (uint64_t)__ldg(bbp + 1) << 32 : 0ull);
+            }
+            for (int j = jlo; j <= jhi; ++j) {
+              const T tap = __ldg(in.tapx + (pos - s * j + W));
+              const int sh = j - (w0 << 5);
+              v.x += ((bitsA >> sh) & 1ull) ? tap : -tap;
+              v.y += ((bitsB >> sh) & 1ull) ? tap : -tap;
+            }
+            if (!hasB) v.y = 0;
+          } else {
+            for (int j = jlo; j <= jhi; ++j) {
+              const T tap = __ldg(in.tapx + (pos - s * j + W));
+              const int jj = j & Nm;
+              v.x += tap * (T)rad_bit(in.bits, in.nw, jj, colA);
+              if (hasB) v.y += tap * (T)rad_bit(in.bits, in.nw, jj, colB);
+            }
           }
         } else {
           const int sx = g.s[0], Nxm = (int)g.n[0] - 1;
