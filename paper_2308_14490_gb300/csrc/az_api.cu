@@ -416,11 +416,16 @@ az_status sketch_and_factor(az_setup_t* h, cudaStream_t st) {
     // mixed: Q1 = Y B1 needs extended precision (its small directions cancel
     // by up to sigma_1 / sigma_r1), computed in double-float and rounded to
     // FP32; Q1 is then well conditioned, so G2 and Ut = Q1 T run in FP32.
+    // (FP32 Q1 in the FP64 Q1 buffer, leading dimension ldm: 16-byte rows for TMA)
     float* Q1f = (float*)h->Q1;
-    AZ_TRY(launch_tsprod_df<float>((const float*)Y, h->Mtot, k, h->B1, k, h->Mtot, Q1f, h->Mtot, st));
-    AZ_TRY((launch_gram<float, float>(Q1f, h->Mtot, k, Q1f, h->Mtot, k, h->Mtot, h->partial, h->G, st, true)));
+    AZ_TRY(launch_tsprod_df<float>((const float*)Y, h->Mtot, k, h->B1, k, h->Mtot, Q1f, h->ldm, st));
+    if (tc_tsgram_ok(Q1f, h->ldm, k, Q1f, h->ldm, k)) {
+      AZ_TRY(launch_tc_tsgram(Q1f, h->ldm, k, Q1f, h->ldm, k, h->Mtot, h->partial, h->G, h->tc_err, st));
+    } else {
+      AZ_TRY((launch_gram<float, float>(Q1f, h->ldm, k, Q1f, h->ldm, k, h->Mtot, h->partial, h->G, st, true)));
+    }
     AZ_TRY(launch_factor2(h->G, k, h->V, h->lam, h->tau_svd, h->floor, h->Tm, h->VS, h->sig, h->info, st, true));
-    AZ_TRY((launch_tsprod<float, float>(Q1f, h->Mtot, k, h->Tm, k, h->Mtot, (float*)h->Ut, h->ldm, st)));
+    AZ_TRY((launch_tsprod<float, float>(Q1f, h->ldm, k, h->Tm, k, h->Mtot, (float*)h->Ut, h->ldm, st)));
   }
   return AZ_OK;
 }
@@ -677,7 +682,7 @@ az_status az_setup(const az_grid* gr, const uint8_t* mask, const double* bpts, i
     rc = dalloc_t(h, &h->tc_err, 1); if (rc) break;
     if (cudaEventCreateWithFlags(&h->info_ev, cudaEventDisableTiming) != cudaSuccess) { cudaGetLastError(); set_error("event"); rc = AZ_ERR_CUDA; break; }
     if (cudaMemsetAsync(h->tc_err, 0, sizeof(int), st) != cudaSuccess) { cudaGetLastError(); set_error("memset"); rc = AZ_ERR_CUDA; break; }
-    rc = dalloc_t(h, &h->Q1, (size_t)h->Mtot * h->k); if (rc) break;
+    rc = dalloc_t(h, &h->Q1, (size_t)std::max<int64_t>(h->Mtot, (h->ldm + 1) / 2) * h->k); if (rc) break;   // also holds FP32 Q1 with ld ldm
     if (h->kind == 1) { rc = dalloc_t(h, &h->Rd, (size_t)g.N * h->k); if (rc) break; }
     for (double** p : {&h->G, &h->V, &h->B1, &h->Tm, &h->VS}) { rc = dalloc_t(h, p, (size_t)h->k * h->k); if (rc) break; }
     if (rc) break;

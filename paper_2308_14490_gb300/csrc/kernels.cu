@@ -208,11 +208,16 @@ __global__ void k_symbol_closed_1d(int64_t L, double a, int Q, int J, double* Gh
 #pragma unroll
   for (int j = 0; j < SYM_J; ++j) acc[j] = 0.0;
   const double q = exp(-2.0 * c * d * d);
+  // the largest image over the run has exponent at most c * emax^2, with
+  // emax the largest |t| of the run reduced to [-1/2, 1/2]; images whose
+  // exponent exceeds that by 40 everywhere on the run add below 2^-57 of
+  // the sum and are skipped
+  const double te = fmin(fmax(fabs(t0), fabs(t0 + (J - 1) * d)), 0.5);
+  const double ecut = c * te * te + 40.0;
   for (int p = -Q; p <= Q; ++p) {
     const double u0 = t0 + (double)p;
-    // the whole run lies where this image is below 2^-1074 of 1: skip it
     const double umin = fmin(fabs(u0), fabs(u0 + (J - 1) * d));
-    if (u0 * (u0 + (J - 1) * d) > 0.0 && c * umin * umin > 745.0) continue;
+    if (u0 * (u0 + (J - 1) * d) > 0.0 && c * umin * umin > fmin(ecut, 745.0)) continue;
     double e = exp(-c * u0 * u0);
     double f = exp(-c * d * (2.0 * u0 + d));
 #pragma unroll
