@@ -761,11 +761,83 @@ __global__ void __launch_bounds__(256) k_update_x_v4(const float* __restrict__ W
   }
 }
 
+// FP32 variant with W in registers: a thread owns two consecutive rows (all
+// k <= KB values of W for them in registers) and walks the right-hand sides
+// in groups of 8, reading u for a group as two 16-byte shared loads per a.
+// Every global access is a contiguous warp transaction (8 bytes of z, 16 of x
+// per lane).
+template <int KB>
+__global__ void __launch_bounds__(256) k_update_x_r2(const float* __restrict__ W, int64_t ldw, int k,
+                                                     const double* __restrict__ u, const float* z, int64_t ldz,
+                                                     int64_t N, int nrhs, double* x, int64_t ldx, int accumulate,
+                                                     float* xf) {
+  constexpr int CG = 8;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* su = (float*)smem_raw;   // [a][c], c padded to a multiple of CG
+  const int nc8 = (nrhs + CG - 1) / CG * CG;
+  for (int t = threadIdx.x; t < KB * nc8; t += blockDim.x) {
+    const int a = t / nc8, c = t % nc8;
+    su[t] = (a < k && c < nrhs) ? (float)u[c * k + a] : 0.f;
+  }
+  __syncthreads();
+  const int64_t j = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+  if (j >= N) return;
+  float2 w[KB];
+#pragma unroll
+  for (int a = 0; a < KB; ++a) w[a] = a < k ? *(const float2*)(W + (int64_t)a * ldw + j) : make_float2(0.f, 0.f);
+  for (int c0 = 0; c0 < nrhs; c0 += CG) {
+    float2 s[CG];
+    double2 xo[CG];
+#pragma unroll
+    for (int q = 0; q < CG; ++q) {
+      const int c = c0 + q;
+      s[q] = c < nrhs ? *(const float2*)(z + (int64_t)c * ldz + j) : make_float2(0.f, 0.f);
+      xo[q] = (accumulate && c < nrhs) ? *(const double2*)(x + (int64_t)c * ldx + j) : make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int a = 0; a < KB; ++a) {
+      const float4 u0 = *(const float4*)(su + a * nc8 + c0);
+      const float4 u1 = *(const float4*)(su + a * nc8 + c0 + 4);
+      const float uu[CG] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+#pragma unroll
+      for (int q = 0; q < CG; ++q) {
+        s[q].x = fmaf(w[a].x, uu[q], s[q].x);
+        s[q].y = fmaf(w[a].y, uu[q], s[q].y);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < CG; ++q) {
+      const int c = c0 + q;
+      if (c >= nrhs) break;
+      xo[q].x += cvt<double>(s[q].x);
+      xo[q].y += cvt<double>(s[q].y);
+      *(double2*)(x + (int64_t)c * ldx + j) = xo[q];
+      if (xf) *(float2*)(xf + (int64_t)c * ldz + j) = s[q];   // exact FP32 copy (may alias z)
+    }
+  }
+}
+
 template <typename TW, typename TZ>
 az_status launch_update_x(const TW* W, int64_t ldw, int k, const double* u, const TZ* z, int64_t ldz, int64_t N,
                           int nrhs, double* x, int64_t ldx, bool accumulate, cudaStream_t st, float* xf) {
   ProfScope ps("update_x", (double)N * (k * sizeof(TW) + nrhs * (sizeof(TZ) + 8.0 * (accumulate ? 2 : 1))), st);
   if constexpr (sizeof(TW) == 4 && sizeof(TZ) == 4) {
+    const bool al2 = N % 2 == 0 && ldw % 2 == 0 && ldz % 2 == 0 && ldx % 2 == 0 && ((uintptr_t)W & 7) == 0 &&
+                     ((uintptr_t)z & 7) == 0 && ((uintptr_t)x & 15) == 0 && ((uintptr_t)xf & 7) == 0;
+    if (al2 && k <= 24) {
+      const int nc8 = (nrhs + 7) / 8 * 8;
+      const unsigned grid2 = (unsigned)((N / 2 + 255) / 256);
+      const int acc = accumulate ? 1 : 0;
+      if (k <= 8) {
+        k_update_x_r2<8><<<grid2, 256, 8 * nc8 * sizeof(float), st>>>(W, ldw, k, u, z, ldz, N, nrhs, x, ldx, acc, xf);
+      } else if (k <= 16) {
+        k_update_x_r2<16><<<grid2, 256, 16 * nc8 * sizeof(float), st>>>(W, ldw, k, u, z, ldz, N, nrhs, x, ldx, acc, xf);
+      } else {
+        k_update_x_r2<24><<<grid2, 256, 24 * nc8 * sizeof(float), st>>>(W, ldw, k, u, z, ldz, N, nrhs, x, ldx, acc, xf);
+      }
+      AZ_LCHECK();
+      return AZ_OK;
+    }
     const size_t sm4 = ((size_t)k * UPX_ROWS + (size_t)k * nrhs) * sizeof(float);
     const bool aligned = N % 4 == 0 && ldw % 4 == 0 && ldz % 4 == 0 && ldx % 2 == 0 && ((uintptr_t)W & 15) == 0 &&
                          ((uintptr_t)z & 15) == 0 && ((uintptr_t)x & 15) == 0 && ((uintptr_t)xf & 15) == 0;
