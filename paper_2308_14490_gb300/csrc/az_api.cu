@@ -63,6 +63,7 @@ struct az_setup_t {
   void* zb = nullptr;   // N x 2 pairs_max (T)
   void* gb = nullptr;   // Mtot x 2 pairs_max (T, ld ldm)
   void* rb = nullptr;   // Mtot x 2 pairs_max (T) residual
+  float* xfb = nullptr; // N x 2 pairs_max: the mixed path's first-pass solution (exactly FP32)
   double* cb = nullptr; // k x 2 pairs_max
   double* ub = nullptr;
   double* normb = nullptr;  // 2 x 2 pairs_max
@@ -438,10 +439,12 @@ az_status compute_setup(az_setup_t* h, cudaStream_t st, bool with_index_map) {
   return AZ_OK;
 }
 
-// One AZ solve of ncols columns (T precision): x (=|+=) Z* b + W VS U^T (b - A Z* b)
+// One AZ solve of ncols columns (T precision): x (=|+=) Z* b + W VS U^T (b - A Z* b).
+// Mixed path: xf_out receives the (exactly FP32) result, x may then be null;
+// xbase (FP32, ld N) makes the update x = xbase + (...).
 template <typename T, typename TB>
 az_status az_once(az_setup_t* h, const TB* b, int64_t ldb, int ncols, double* x, int64_t ldx, bool accumulate,
-                  cudaStream_t st, bool want_xf = false) {
+                  cudaStream_t st, float* xf_out = nullptr, const float* xbase = nullptr) {
   const Geom& g = h->g;
   T* z = (T*)h->zb;
   T* gg = (T*)h->gb;
@@ -461,9 +464,8 @@ az_status az_once(az_setup_t* h, const TB* b, int64_t ldb, int ncols, double* x,
     AZ_TRY((launch_gram<T, T>((const T*)h->Ut, h->ldm, h->k, gg, h->ldm, ncols, h->Mtot, h->partial, h->cb, st, true)));
   }
   AZ_TRY(launch_small_mm(h->VS, h->k, h->cb, ncols, h->ub, st));
-  // the mixed path also leaves the (exactly FP32) first-pass solution in the z buffer
-  float* xf = (want_xf && !Prec<T>::fp64) ? (float*)z : nullptr;
-  AZ_TRY((launch_update_x<T, T>((const T*)h->W, g.N, h->k, h->ub, z, g.N, g.N, ncols, x, ldx, accumulate, st, xf)));
+  AZ_TRY((launch_update_x<T, T>((const T*)h->W, g.N, h->k, h->ub, z, g.N, g.N, ncols, x, ldx, accumulate, st,
+                                Prec<T>::fp64 ? nullptr : xf_out, Prec<T>::fp64 ? nullptr : xbase)));
   return AZ_OK;
 }
 
@@ -475,7 +477,16 @@ az_status solve_impl(az_setup_t* h, const double* b, int64_t ldb, int64_t nrhs, 
     const int nc = (int)std::min<int64_t>(chunk, nrhs - c0);
     const double* bc = b + c0 * ldb;
     double* xc = x + c0 * ldx;
-    AZ_TRY((az_once<T, double>(h, bc, ldb, nc, xc, ldx, false, st, h->refine > 0)));
+    // mixed path with refinement and no boundary rows: the first pass keeps
+    // its result only as the exact FP32 copy, and the second forms
+    // x = x1 + dx directly (one FP64 write of x instead of a write, a read
+    // and a write)
+    const bool mixed = !Prec<T>::fp64;
+    // (the wide path leaves the FP32 first-pass result in the z buffer instead)
+    const bool defer = mixed && h->refine > 0 && h->Mb == 0 && !h->wide;
+    AZ_TRY((az_once<T, double>(h, bc, ldb, nc, defer ? nullptr : xc, ldx, false, st,
+                               mixed && h->refine > 0 && !h->wide ? h->xfb : nullptr)));
+    const float* x1f = h->wide ? (const float*)h->zb : h->xfb;
     for (int it = 0; it < h->refine; ++it) {
       T* res = (T*)h->rb;
       if (!Prec<T>::fp64 && it == 0) {
@@ -484,7 +495,7 @@ az_status solve_impl(az_setup_t* h, const double* b, int64_t ldb, int64_t nrhs, 
         // residual (about 48 significant bits) at FP32 throughput
         const float* th[4] = {h->tapsH[0], h->tapsH[1], h->tapsH[2], h->tapsH[3]};
         const float* tl[4] = {h->tapsL[0], h->tapsL[1], h->tapsL[2], h->tapsL[3]};
-        AZ_TRY(launch_resid_df(h->g, h->kind, h->eps, h->idx, h->M, th, tl, h->W64[0], h->W64[1], (const float*)h->zb,
+        AZ_TRY(launch_resid_df(h->g, h->kind, h->eps, h->idx, h->M, th, tl, h->W64[0], h->W64[1], x1f,
                                h->g.N, bc, ldb, (float*)res, h->Mtot, nc, st));
         if (h->Mb) {
           AZ_TRY((launch_boundary_rows<double, double, double, T>(h->g, h->eps, h->bweight, h->bpts, h->Mb, xc, ldx,
@@ -494,7 +505,8 @@ az_status solve_impl(az_setup_t* h, const double* b, int64_t ldb, int64_t nrhs, 
         // r = b - A x with the residual computed in FP64
         AZ_TRY((apply_rows<double, double, double, T>(h, xc, ldx, bc, ldb, 1.0, -1.0, res, h->Mtot, nc, st)));
       }
-      AZ_TRY((az_once<T, T>(h, res, h->Mtot, nc, xc, ldx, true, st)));
+      if (defer && it == 0) AZ_TRY((az_once<T, T>(h, res, h->Mtot, nc, xc, ldx, false, st, nullptr, h->xfb)));
+      else AZ_TRY((az_once<T, T>(h, res, h->Mtot, nc, xc, ldx, true, st)));
     }
     if (relres) {
       if (!h->r64) {
@@ -532,6 +544,7 @@ az_status alloc_workspace(az_setup_t* h) {
   AZ_TRY(dalloc(h, &h->zb, (size_t)g.N * cols * tsz));
   AZ_TRY(dalloc(h, &h->gb, (size_t)h->ldm * cols * tsz));
   AZ_TRY(dalloc(h, &h->rb, (size_t)h->Mtot * cols * tsz));
+  if (h->precision == AZ_MIXED) AZ_TRY(dalloc_t(h, &h->xfb, (size_t)g.N * cols));
   AZ_TRY(dalloc_t(h, &h->cb, (size_t)h->k * cols));
   AZ_TRY(dalloc_t(h, &h->ub, (size_t)h->k * cols));
   AZ_TRY(dalloc_t(h, &h->normb, (size_t)2 * cols));

@@ -670,7 +670,8 @@ az_status launch_small_mm(const double* VS, int k, const double* c, int n, doubl
 template <typename TW, typename TZ, int KB>
 __global__ void __launch_bounds__(256) k_update_x(const TW* __restrict__ W, int64_t ldw, int k, const double* __restrict__ u,
                                                   const TZ* z, int64_t ldz, int64_t N, int nrhs,
-                                                  double* __restrict__ x, int64_t ldx, int accumulate, float* xf) {
+                                                  double* __restrict__ x, int64_t ldx, int accumulate, float* xf,
+                                                  const float* __restrict__ xbase) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TW* su = (TW*)smem_raw;   // [c*k + a]
   for (int t = threadIdx.x; t < k * nrhs; t += blockDim.x) su[t] = (TW)u[t];
@@ -685,10 +686,12 @@ __global__ void __launch_bounds__(256) k_update_x(const TW* __restrict__ W, int6
     const TW* uc = su + c * k;
 #pragma unroll
     for (int a = 0; a < KB; ++a) if (a < k) s = fma(w[a], uc[a], s);
-    double* xp = x + (int64_t)c * ldx + j;
     const double sd = cvt<double>(s);
-    *xp = accumulate ? *xp + sd : sd;
-    if (xf) xf[(int64_t)c * ldz + j] = (float)s;   // exact FP32 copy (may alias z)
+    if (x) {
+      double* xp = x + (int64_t)c * ldx + j;
+      *xp = xbase ? (double)xbase[(int64_t)c * ldz + j] + sd : (accumulate ? *xp + sd : sd);
+    }
+    if (xf) xf[(int64_t)c * ldz + j] = (float)s;   // exact FP32 copy
   }
 }
 // FP32 variant for aligned shapes: a CTA stages its 512-row tile of W and all
@@ -699,7 +702,7 @@ constexpr int UPX_ROWS = 512;
 __global__ void __launch_bounds__(256) k_update_x_v4(const float* __restrict__ W, int64_t ldw, int k,
                                                      const double* __restrict__ u, const float* z, int64_t ldz,
                                                      int64_t N, int nrhs, double* x, int64_t ldx, int accumulate,
-                                                     float* xf) {
+                                                     float* xf, const float* __restrict__ xbase) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* sW = (float*)smem_raw;                 // [a][UPX_ROWS]
   float* su = sW + (size_t)k * UPX_ROWS;         // [c][k]
@@ -718,7 +721,7 @@ __global__ void __launch_bounds__(256) k_update_x_v4(const float* __restrict__ W
   for (int c = warp; c < nrhs; c += 8) {
     const float* uc = su + c * k;
     const float* zc = z + (int64_t)c * ldz + r0;
-    double* xc = x + (int64_t)c * ldx + r0;
+    double* xc = x ? x + (int64_t)c * ldx + r0 : nullptr;
     float4 s[NQ];
     double2 xa[NQ], xb[NQ];
 #pragma unroll
@@ -729,7 +732,11 @@ __global__ void __launch_bounds__(256) k_update_x_v4(const float* __restrict__ W
       xb[t] = make_double2(0.0, 0.0);
       if (q < rows) {
         s[t] = *(const float4*)(zc + q);
-        if (accumulate) {
+        if (xbase) {
+          const float4 v = *(const float4*)(xbase + (int64_t)c * ldz + r0 + q);
+          xa[t] = make_double2(v.x, v.y);
+          xb[t] = make_double2(v.z, v.w);
+        } else if (accumulate && xc) {
           xa[t] = *(const double2*)(xc + q);
           xb[t] = *(const double2*)(xc + q + 2);
         }
@@ -750,13 +757,15 @@ __global__ void __launch_bounds__(256) k_update_x_v4(const float* __restrict__ W
     for (int t = 0; t < NQ; ++t) {
       const int q = lane * 4 + t * 128;
       if (q >= rows) continue;
-      xa[t].x += cvt<double>(s[t].x);
-      xa[t].y += cvt<double>(s[t].y);
-      xb[t].x += cvt<double>(s[t].z);
-      xb[t].y += cvt<double>(s[t].w);
-      *(double2*)(xc + q) = xa[t];
-      *(double2*)(xc + q + 2) = xb[t];
-      if (xf) *(float4*)(xf + (int64_t)c * ldz + r0 + q) = s[t];   // exact FP32 copy (may alias z)
+      if (xc) {
+        xa[t].x += cvt<double>(s[t].x);
+        xa[t].y += cvt<double>(s[t].y);
+        xb[t].x += cvt<double>(s[t].z);
+        xb[t].y += cvt<double>(s[t].w);
+        *(double2*)(xc + q) = xa[t];
+        *(double2*)(xc + q + 2) = xb[t];
+      }
+      if (xf) *(float4*)(xf + (int64_t)c * ldz + r0 + q) = s[t];   // exact FP32 copy
     }
   }
 }
@@ -770,7 +779,7 @@ template <int KB>
 __global__ void __launch_bounds__(256) k_update_x_r2(const float* __restrict__ W, int64_t ldw, int k,
                                                      const double* __restrict__ u, const float* z, int64_t ldz,
                                                      int64_t N, int nrhs, double* x, int64_t ldx, int accumulate,
-                                                     float* xf) {
+                                                     float* xf, const float* __restrict__ xbase) {
   constexpr int CG = 8;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* su = (float*)smem_raw;   // [a][c], c padded to a multiple of CG
@@ -792,7 +801,13 @@ __global__ void __launch_bounds__(256) k_update_x_r2(const float* __restrict__ W
     for (int q = 0; q < CG; ++q) {
       const int c = c0 + q;
       s[q] = c < nrhs ? *(const float2*)(z + (int64_t)c * ldz + j) : make_float2(0.f, 0.f);
-      xo[q] = (accumulate && c < nrhs) ? *(const double2*)(x + (int64_t)c * ldx + j) : make_double2(0.0, 0.0);
+      xo[q] = make_double2(0.0, 0.0);
+      if (c < nrhs && xbase) {
+        const float2 v = *(const float2*)(xbase + (int64_t)c * ldz + j);
+        xo[q] = make_double2(v.x, v.y);
+      } else if (c < nrhs && accumulate && x) {
+        xo[q] = *(const double2*)(x + (int64_t)c * ldx + j);
+      }
     }
 #pragma unroll
     for (int a = 0; a < KB; ++a) {
@@ -809,52 +824,61 @@ __global__ void __launch_bounds__(256) k_update_x_r2(const float* __restrict__ W
     for (int q = 0; q < CG; ++q) {
       const int c = c0 + q;
       if (c >= nrhs) break;
-      xo[q].x += cvt<double>(s[q].x);
-      xo[q].y += cvt<double>(s[q].y);
-      *(double2*)(x + (int64_t)c * ldx + j) = xo[q];
-      if (xf) *(float2*)(xf + (int64_t)c * ldz + j) = s[q];   // exact FP32 copy (may alias z)
+      if (x) {
+        xo[q].x += cvt<double>(s[q].x);
+        xo[q].y += cvt<double>(s[q].y);
+        *(double2*)(x + (int64_t)c * ldx + j) = xo[q];
+      }
+      if (xf) *(float2*)(xf + (int64_t)c * ldz + j) = s[q];   // exact FP32 copy
     }
   }
 }
 
 template <typename TW, typename TZ>
 az_status launch_update_x(const TW* W, int64_t ldw, int k, const double* u, const TZ* z, int64_t ldz, int64_t N,
-                          int nrhs, double* x, int64_t ldx, bool accumulate, cudaStream_t st, float* xf) {
-  ProfScope ps("update_x", (double)N * (k * sizeof(TW) + nrhs * (sizeof(TZ) + 8.0 * (accumulate ? 2 : 1))), st);
+                          int nrhs, double* x, int64_t ldx, bool accumulate, cudaStream_t st, float* xf,
+                          const float* xbase) {
+  // algorithmic bytes: W, z, then per column x written (and read when
+  // accumulating), the FP32 base read, the FP32 copy written
+  const double per_col = sizeof(TZ) + (x ? 8.0 * ((accumulate && !xbase) ? 2 : 1) : 0.0) + (xbase ? 4.0 : 0.0) +
+                         (xf ? 4.0 : 0.0);
+  ProfScope ps("update_x", (double)N * (k * sizeof(TW) + nrhs * per_col), st);
   if constexpr (sizeof(TW) == 4 && sizeof(TZ) == 4) {
     const bool al2 = N % 2 == 0 && ldw % 2 == 0 && ldz % 2 == 0 && ldx % 2 == 0 && ((uintptr_t)W & 7) == 0 &&
-                     ((uintptr_t)z & 7) == 0 && ((uintptr_t)x & 15) == 0 && ((uintptr_t)xf & 7) == 0;
+                     ((uintptr_t)z & 7) == 0 && ((uintptr_t)x & 15) == 0 && ((uintptr_t)xf & 7) == 0 &&
+                     ((uintptr_t)xbase & 7) == 0;
     if (al2 && k <= 24) {
       const int nc8 = (nrhs + 7) / 8 * 8;
       const unsigned grid2 = (unsigned)((N / 2 + 255) / 256);
       const int acc = accumulate ? 1 : 0;
       if (k <= 8) {
-        k_update_x_r2<8><<<grid2, 256, 8 * nc8 * sizeof(float), st>>>(W, ldw, k, u, z, ldz, N, nrhs, x, ldx, acc, xf);
+        k_update_x_r2<8><<<grid2, 256, 8 * nc8 * sizeof(float), st>>>(W, ldw, k, u, z, ldz, N, nrhs, x, ldx, acc, xf, xbase);
       } else if (k <= 16) {
-        k_update_x_r2<16><<<grid2, 256, 16 * nc8 * sizeof(float), st>>>(W, ldw, k, u, z, ldz, N, nrhs, x, ldx, acc, xf);
+        k_update_x_r2<16><<<grid2, 256, 16 * nc8 * sizeof(float), st>>>(W, ldw, k, u, z, ldz, N, nrhs, x, ldx, acc, xf, xbase);
       } else {
-        k_update_x_r2<24><<<grid2, 256, 24 * nc8 * sizeof(float), st>>>(W, ldw, k, u, z, ldz, N, nrhs, x, ldx, acc, xf);
+        k_update_x_r2<24><<<grid2, 256, 24 * nc8 * sizeof(float), st>>>(W, ldw, k, u, z, ldz, N, nrhs, x, ldx, acc, xf, xbase);
       }
       AZ_LCHECK();
       return AZ_OK;
     }
     const size_t sm4 = ((size_t)k * UPX_ROWS + (size_t)k * nrhs) * sizeof(float);
     const bool aligned = N % 4 == 0 && ldw % 4 == 0 && ldz % 4 == 0 && ldx % 2 == 0 && ((uintptr_t)W & 15) == 0 &&
-                         ((uintptr_t)z & 15) == 0 && ((uintptr_t)x & 15) == 0 && ((uintptr_t)xf & 15) == 0;
+                         ((uintptr_t)z & 15) == 0 && ((uintptr_t)x & 15) == 0 && ((uintptr_t)xf & 15) == 0 &&
+                         ((uintptr_t)xbase & 15) == 0;
     if (aligned && sm4 <= 160 * 1024) {
       smem_once(k_update_x_v4, sm4);
       k_update_x_v4<<<(unsigned)((N + UPX_ROWS - 1) / UPX_ROWS), 256, sm4, st>>>(W, ldw, k, u, z, ldz, N, nrhs, x, ldx,
-                                                                               accumulate ? 1 : 0, xf);
+                                                                               accumulate ? 1 : 0, xf, xbase);
       AZ_LCHECK();
       return AZ_OK;
     }
   }
   size_t sm = (size_t)k * nrhs * sizeof(TW);
   unsigned grid = (unsigned)((N + 255) / 256);
-  if (k <= 8) k_update_x<TW, TZ, 8><<<grid, 256, sm, st>>>(W, ldw, k, u, z, ldz, N, nrhs, x, ldx, accumulate ? 1 : 0, xf);
-  else if (k <= 16) k_update_x<TW, TZ, 16><<<grid, 256, sm, st>>>(W, ldw, k, u, z, ldz, N, nrhs, x, ldx, accumulate ? 1 : 0, xf);
-  else if (k <= 32) k_update_x<TW, TZ, 32><<<grid, 256, sm, st>>>(W, ldw, k, u, z, ldz, N, nrhs, x, ldx, accumulate ? 1 : 0, xf);
-  else k_update_x<TW, TZ, 64><<<grid, 256, sm, st>>>(W, ldw, k, u, z, ldz, N, nrhs, x, ldx, accumulate ? 1 : 0, xf);
+  if (k <= 8) k_update_x<TW, TZ, 8><<<grid, 256, sm, st>>>(W, ldw, k, u, z, ldz, N, nrhs, x, ldx, accumulate ? 1 : 0, xf, xbase);
+  else if (k <= 16) k_update_x<TW, TZ, 16><<<grid, 256, sm, st>>>(W, ldw, k, u, z, ldz, N, nrhs, x, ldx, accumulate ? 1 : 0, xf, xbase);
+  else if (k <= 32) k_update_x<TW, TZ, 32><<<grid, 256, sm, st>>>(W, ldw, k, u, z, ldz, N, nrhs, x, ldx, accumulate ? 1 : 0, xf, xbase);
+  else k_update_x<TW, TZ, 64><<<grid, 256, sm, st>>>(W, ldw, k, u, z, ldz, N, nrhs, x, ldx, accumulate ? 1 : 0, xf, xbase);
   AZ_LCHECK();
   return AZ_OK;
 }
@@ -866,7 +890,7 @@ template az_status launch_tsprod<float, double>(const float*, int64_t, int, cons
 template az_status launch_tsprod<double, double>(const double*, int64_t, int, const double*, int, int64_t, double*, int64_t, cudaStream_t);
 template az_status launch_tsprod<double, float>(const double*, int64_t, int, const double*, int, int64_t, float*, int64_t, cudaStream_t);
 template az_status launch_tsprod<float, float>(const float*, int64_t, int, const double*, int, int64_t, float*, int64_t, cudaStream_t);
-template az_status launch_update_x<float, float>(const float*, int64_t, int, const double*, const float*, int64_t, int64_t, int, double*, int64_t, bool, cudaStream_t, float*);
-template az_status launch_update_x<double, double>(const double*, int64_t, int, const double*, const double*, int64_t, int64_t, int, double*, int64_t, bool, cudaStream_t, float*);
+template az_status launch_update_x<float, float>(const float*, int64_t, int, const double*, const float*, int64_t, int64_t, int, double*, int64_t, bool, cudaStream_t, float*, const float*);
+template az_status launch_update_x<double, double>(const double*, int64_t, int, const double*, const double*, int64_t, int64_t, int, double*, int64_t, bool, cudaStream_t, float*, const float*);
 
 }  // namespace az

@@ -47,7 +47,10 @@ az_status launch_factor2(const double* G2, int k, const double* V, const double*
 az_status launch_small_mm(const double* VS, int k, const double* c, int n, double* u, cudaStream_t st);
 // x[:, c] = (accumulate ? x : 0) + z[:, c] + W u[:, c]  (N rows)
 template <typename TW, typename TZ>
+// x = z + W u (accumulate: x += z + W u; xbase: x = xbase + z + W u with xbase
+// FP32, ld ldz; x may be null when only the exact FP32 copy xf is wanted)
 az_status launch_update_x(const TW* W, int64_t ldw, int k, const double* u, const TZ* z, int64_t ldz, int64_t N,
-                          int nrhs, double* x, int64_t ldx, bool accumulate, cudaStream_t st, float* xf = nullptr);
+                          int nrhs, double* x, int64_t ldx, bool accumulate, cudaStream_t st, float* xf = nullptr,
+                          const float* xbase = nullptr);
 
 }  // namespace az
