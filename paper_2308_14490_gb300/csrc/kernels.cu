@@ -727,7 +727,7 @@ az_status launch_stencil_rows(const Geom& g, int kind, double eps, const int32_t
                               const StencilTaps& tp, const TZ* z, int64_t ldz, const TB* b, int64_t ldb,
                               T alpha, T beta, TO* out, int64_t ldo, int ncols, cudaStream_t st) {
   if (M == 0 || ncols == 0) return AZ_OK;
-  constexpr int CPT = 4;
+  constexpr int CPT = sizeof(T) == 4 ? 8 : 4;
   dim3 grid((unsigned)((M + 255) / 256), (ncols + CPT - 1) / CPT);
   ProfScope ps(sizeof(T) == 4 ? "stencil_rows_f32" : "stencil_rows_f64", (double)g.N * ncols * sizeof(TZ) + (double)M * ncols * ((b ? sizeof(TB) : 0) + sizeof(TO)) + 4.0 * M, st);
   k_stencil_rows<T, TZ, TB, TO, CPT><<<grid, 256, 0, st>>>(g, kind, (T)(1.0 / (2.0 * eps * eps)), idx, (int)M, (const T*)tp.x0,
