@@ -88,12 +88,18 @@ __global__ void __launch_bounds__(512) k_gram_partial(const TA* __restrict__ A, 
   const int tile_elems = GRAM_TILE * (ka + kb);
   double* red = (double*)smem_raw;                 // nsplit x nblk x RA*RB (reduction; aliases the tiles)
   const int nta = (ka + RA - 1) / RA, ntb = (kb + RB - 1) / RB;
-  const int nblkt = nta * ntb;
+  // symmetric product (B == A): threads only for the blocks on or above the
+  // block diagonal, enumerated column by column (bt = tb (tb + 1) / 2 + ta)
+  const int nblkt = sym ? nta * (nta + 1) / 2 : nta * ntb;
   const int nsplit = blockDim.x / nblkt;        // thread groups splitting each tile's rows
   const int bt = threadIdx.x % nblkt, sp = threadIdx.x / nblkt;
-  const int ta = bt % nta, tb = bt / nta;
-  // symmetric product (B == A): only blocks on or above the block diagonal
-  const bool active = sp < nsplit && (!sym || ta <= tb);
+  int ta = bt % nta, tb = bt / nta;
+  if (sym) {
+    tb = 0;
+    while ((tb + 1) * (tb + 2) / 2 <= bt) ++tb;
+    ta = bt - tb * (tb + 1) / 2;
+  }
+  const bool active = sp < nsplit;
   const int64_t r0 = (int64_t)blockIdx.x * GRAM_ROWS;
   const int64_t r1 = (M < r0 + GRAM_ROWS) ? M : r0 + GRAM_ROWS;
   const int ntiles = (int)((r1 - r0 + GRAM_TILE - 1) / GRAM_TILE);
@@ -172,8 +178,12 @@ __global__ void __launch_bounds__(512) k_gram_partial(const TA* __restrict__ A, 
   for (int t = threadIdx.x; t < nblkt * RA * RB; t += blockDim.x) {
     const int b2 = t / (RA * RB), e = t % (RA * RB);
     const int i = e / RB, j = e % RB;
-    const int ta2 = b2 % nta, tb2 = b2 / nta;
-    if (sym && ta2 > tb2) continue;
+    int ta2 = b2 % nta, tb2 = b2 / nta;
+    if (sym) {
+      tb2 = 0;
+      while ((tb2 + 1) * (tb2 + 2) / 2 <= b2) ++tb2;
+      ta2 = b2 - tb2 * (tb2 + 1) / 2;
+    }
     const int a = ta2 * RA + i, c = tb2 * RB + j;
     if (a >= ka || c >= kb) continue;
     double sacc2 = 0.0;
@@ -212,13 +222,14 @@ az_status launch_gram(const TA* A, int64_t lda, int ka, const TB* B, int64_t ldb
                       double* partial, double* G, cudaStream_t st, bool fast) {
   constexpr int RA = 4, RB = 4;
   const int npair = ka * kb;
-  const int nthr = ((ka + RA - 1) / RA) * ((kb + RB - 1) / RB);
+  const int sym = ((const void*)A == (const void*)B && ka == kb && lda == ldb) ? 1 : 0;
+  const int nta = (ka + RA - 1) / RA, ntb = (kb + RB - 1) / RB;
+  const int nthr = sym ? nta * (nta + 1) / 2 : nta * ntb;   // one thread per (upper) 4 x 4 block
   if (nthr > 1024) { set_error("gram: too many columns for this kernel"); return AZ_ERR_ARG; }
   const int nsplit = std::max(1, 512 / nthr);
   const int threads = nsplit * nthr;
   const int nblk = gram_blocks(M);
   const bool in32 = sizeof(TA) == 4 && sizeof(TB) == 4;
-  const int sym = ((const void*)A == (const void*)B && ka == kb && lda == ldb) ? 1 : 0;
   const size_t ts = in32 ? sizeof(float) : sizeof(double);
   size_t sm = 2 * (size_t)GRAM_TILE * (ka + kb) * ts;
   sm = std::max(sm, (size_t)nsplit * nthr * RA * RB * sizeof(double));
