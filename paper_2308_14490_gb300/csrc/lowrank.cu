@@ -628,16 +628,23 @@ __global__ void k_factor2(const double* __restrict__ G2, int k, const double* __
   }
   __syncthreads();
   const int r = rs;
-  // U_R = VR (r1 x r1, column c); T = R2^{-1} U_R[:, :r] by back substitution
-  for (int c = threadIdx.x; c < k; c += blockDim.x) {
-    for (int i = 0; i < k; ++i) T[(int64_t)c * k + i] = 0.0;
-    if (c < r) {
-      for (int i = r1 - 1; i >= 0; --i) {
-        double sacc = VR[c * r1 + i];
-        for (int l = i + 1; l < r1; ++l) sacc -= R[l * k + i] * T[(int64_t)c * k + l];
-        T[(int64_t)c * k + i] = sacc / R[i * k + i];
+  // U_R = VR (r1 x r1, column c); T = R2^{-1} U_R[:, :r] by back substitution,
+  // solved in a shared-memory scratch (after the sort buffers) and written out once
+  {
+    double* Ts = (double*)((int*)(sg + k) + k + (k & 1)) + (size_t)k * k;   // after rank + sort scratch
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+      double* tc = Ts + (size_t)c * k;
+      for (int i = 0; i < k; ++i) tc[i] = 0.0;
+      if (c < r) {
+        for (int i = r1 - 1; i >= 0; --i) {
+          double sacc = VR[c * r1 + i];
+          for (int l = i + 1; l < r1; ++l) sacc -= R[l * k + i] * tc[l];
+          tc[i] = sacc / R[i * k + i];
+        }
       }
     }
+    __syncthreads();
+    for (int t = threadIdx.x; t < k * k; t += blockDim.x) T[t] = Ts[t];
   }
   // VS = V_R[:, :r] Sigma^{-1} = A[:, c] / sigma_c^2
   for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
@@ -650,8 +657,11 @@ az_status launch_factor2(const double* G2, int k, const double* V, const double*
                          double* T, double* VS, double* sig, FactorInfo* info, cudaStream_t st, bool f32jac) {
   if (k > 64) { set_error("factor: k > 64 not supported by the one-CTA factorisation"); return AZ_ERR_ARG; }
   // R, A, VR, sg, then the FP32 Jacobi copies or the sort's rank + scratch
+  // R, A, VR, sg, then the FP32 Jacobi copies or the sort's rank + scratch,
+  // then the back-substitution scratch
   size_t sm = (3 * (size_t)k * k + k) * sizeof(double) +
-              std::max(2 * (size_t)k * k * sizeof(float), (size_t)(k + 1) * sizeof(int) + sizeof(int) + (size_t)k * k * sizeof(double));
+              std::max(2 * (size_t)k * k * sizeof(float), (size_t)(k + 1) * sizeof(int) + sizeof(int) + (size_t)k * k * sizeof(double)) +
+              (size_t)k * k * sizeof(double);
   smem_once(k_factor2, sm);
   ProfScope ps("factor2", 0.0, st);
   (void)lam;
