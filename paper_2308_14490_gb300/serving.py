@@ -82,7 +82,7 @@ class _Setup:
 
 class Server:
     def __init__(self, budget_bytes: int, nslots: int = 4, use_graphs: bool = True, device=None,
-                 keep_results: bool = False, precision: int = AZ_MIXED):
+                 keep_results: bool = False, precision: int = AZ_MIXED, warm_process: bool = True):
         self.dev = device or torch.device("cuda", torch.cuda.current_device())
         self.setup_stream = torch.cuda.Stream(device=self.dev)
         self.keep_results = keep_results
@@ -101,33 +101,61 @@ class Server:
         self.precision = precision
         self.build_ms = []                 # wall time of each setup build (host view)
         self.pending_capture = collections.deque()   # (setup key, bucket) solved eagerly, not yet captured
-        # process warm-up (library handles and kernels of the right-hand-side
-        # generator), so that the first request does not pay for it
+        # process warm-up: library handles and kernels of the right-hand-side
+        # generator, and one tiny setup and solve of each kind (first launches
+        # load kernels), so that the first request does not pay for them
         a = torch.ones((8, 2), dtype=torch.float64, device=self.dev)
         torch.cos(a @ a.T).sum().item()
+        if warm_process:
+            self._warm_process()
 
     # ------------------------------------------------------------------ setups
+    def _warm_process(self):
+        th = 2 * np.pi * np.arange(16) / 16
+        tiny = [SetupSpec(("warm1d",), 1, (64,), (2,), (1.0,), "approx", lambda x: (x >= -0.5) & (x <= 0.5), k=4),
+                SetupSpec(("warm2d",), 2, (16, 16), (2, 2), (1.0, 1.0), "approx", star_fn(0.5, 0.1, 5), k=4),
+                SetupSpec(("warmp",), 2, (16, 16), (2, 2), (1.0, 1.0), "poisson", star_fn(0.5, 0.1, 5),
+                          np.stack([0.5 * np.cos(th), 0.5 * np.sin(th)], 1), 10.0, k=4)]
+        builds = len(self.build_ms)
+        for spec in tiny:
+            st = self._build(spec)
+            if st is None:
+                continue
+            _, b_buf, x_buf = self._graph(st, BUCKETS[0], self.slots[0], capture=False)
+            self._rhs(st, [Request(-1, 0.0, spec, 1, 0)], b_buf)
+            self._solve_fn(st, b_buf, x_buf, self.slots[0])
+            torch.cuda.synchronize(self.dev)
+            self._evict(st)
+        # the warm-up is not part of the served workload's statistics
+        del self.build_ms[builds:]
+        self.setup_builds = 0
+        self.evictions = 0
+        self.high_water = 0
+        self.pending_capture.clear()
+
     def _grid_coords(self, spec):
+        """Oversampled grid coordinates per dimension, on the device (FP64)."""
         cs = []
         for d in range(spec.dim):
             L = spec.n[d] * spec.s[d]
-            cs.append(-spec.T[d] + np.arange(L) * (2 * spec.T[d] / L))
+            cs.append(-spec.T[d] + torch.arange(L, dtype=torch.float64, device=self.dev) * (2 * spec.T[d] / L))
         return cs
 
     def _build(self, spec: SetupSpec):
         t_build = time.perf_counter()
         opts = make_options(self.precision, spec.k, 1e-8, 0.0, 1, 1 if self.precision == AZ_MIXED else 0)
         grid = make_grid(spec.dim, spec.n, spec.s, spec.T)
+        # domain mask and kept points evaluated on the device
         cs = self._grid_coords(spec)
         if spec.dim == 1:
-            mask = spec.mask_fn(cs[0]).astype(np.uint8)
-            pts = cs[0][mask.astype(bool)][:, None]
+            sel = spec.mask_fn(cs[0])
+            pts = cs[0][sel][:, None]
         else:
-            X, Y = np.meshgrid(cs[0], cs[1], indexing="ij")
-            mask = spec.mask_fn(X, Y).astype(np.uint8).reshape(-1)
-            sel = mask.astype(bool)
-            pts = np.stack([X.reshape(-1)[sel], Y.reshape(-1)[sel]], 1)
-        M = int(mask.sum())
+            X, Y = torch.meshgrid(cs[0], cs[1], indexing="ij")
+            sel = spec.mask_fn(X, Y).reshape(-1)
+            pts = torch.stack([X.reshape(-1)[sel], Y.reshape(-1)[sel]], 1)
+        mt = sel.to(torch.uint8)
+        M = int(pts.shape[0])
         nb = 0 if spec.boundary is None else len(spec.boundary)
         need = az_query_footprint(grid, M, nb, opts, 64)
         if need > self.budget:
@@ -139,7 +167,6 @@ class Server:
                 return None
             victim = min(idle, key=lambda s: s.last_use)
             self._evict(victim)
-        mt = torch.from_numpy(mask).to(self.dev)
         bnd = None
         kernel = AZ_GAUSS
         if spec.kind == "poisson":
@@ -149,7 +176,7 @@ class Server:
         h = az_setup(grid, mt, spec.epsh / (2 * spec.T[0] / spec.n[0]), kernel, bnd, spec.weight, opts,
                      self.setup_stream)
         info = az_get_info(h)
-        st = _Setup(spec, h, info, self.dev, torch.from_numpy(pts).to(self.dev), bnd)
+        st = _Setup(spec, h, info, self.dev, pts.contiguous(), bnd)
         self.setups[spec.key] = st
         self.used += st.bytes
         self.setup_builds += 1
@@ -336,7 +363,12 @@ class Server:
 
 # --------------------------------------------------------------------------- the mixed workload
 def star_fn(r0, a, k):
-    return lambda X, Y: np.sqrt(X * X + Y * Y) <= r0 + a * np.cos(k * np.arctan2(Y, X))
+    """Star domain r(theta) = r0 + a cos(k theta) (numpy or torch coordinates)."""
+    def f(X, Y):
+        if isinstance(X, torch.Tensor):
+            return torch.sqrt(X * X + Y * Y) <= r0 + a * torch.cos(k * torch.atan2(Y, X))
+        return np.sqrt(X * X + Y * Y) <= r0 + a * np.cos(k * np.arctan2(Y, X))
+    return f
 
 
 def setup_pool(seed: int, count: int = 32, max2d: int = 512):

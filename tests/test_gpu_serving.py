@@ -52,7 +52,7 @@ def test_each_result_is_the_same_alone_and_in_the_mix(S):
         x_mix, x_one = mix.results[r.rid], alone.results[r.rid]
         rm, ro = _relres(az, st, x_mix, b), _relres(az, st, x_one, b)
         # mixed-precision bar 1e-8; the 2D setups here run with k far below
-        # their rank (k <= 64 in this build), so their residual is large and the
+        # their rank (the serving pool keeps k <= 64), so their residual is large and the
         # FP32 rounding enters it at first order: allow 1e-6 of the residual
         tol = np.maximum(1e-8, 1e-6 * ro)
         assert np.all(np.abs(rm - ro) <= tol), (r.spec.key, rm, ro)
