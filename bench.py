@@ -436,6 +436,19 @@ def run_ours(args):
                 "algorithmic_bytes_per_launch": ent["bytes"] / max(1, ent["launches"]),
                 "avg_launch_ms": ent["ms"] / max(1, ent["launches"]), "time_share": share}
 
+    # whole step against the pass-plan byte model fixed in advance for this
+    # workload: sketch k (24 L + 4 M) plus, per right-hand side of the mixed
+    # refined solve, (24 M + 32 L + 48 N) twice and the FP64 residual
+    # (24 N + 16 L + 16 M); and against the DRAM bytes ncu measured per step
+    Lg, Ng = g.L, g.N
+    plan = K_SKETCH * (24 * Lg + 4 * M) + NRHS * (2 * (24 * M + 32 * Lg + 48 * Ng) + (24 * Ng + 16 * Lg + 16 * M))
+    step_s = total_ms / args.steps / 1000.0
+    measured = sum(v["dram_bytes_per_step"] for v in load_traffic().values()) or None
+    step_roofline = {"bound": "hbm", "plan_bytes_per_step": int(plan), "achieved": round(plan / step_s / 1e9, 1),
+                     "peak": hbm, "unit": "GB/s", "frac": round(plan / step_s / 1e9 / hbm, 4),
+                     "dram_bytes_per_step": measured,
+                     "dram_frac": round(measured / step_s / 1e9 / hbm, 4) if measured else None}
+
     line = {"metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
@@ -446,7 +459,8 @@ def run_ours(args):
                            "max": max(per)},
             "parity": {"relres_max_mixed": max(rr_mixed), "relres_max_fp64": max(rr64),
                        "max_gap_mixed_vs_fp64": max(abs(a - c) for a, c in zip(rr_mixed, rr64)), "tol": 1e-8},
-            "roofline": roofline, "gpu_launches": int(launches), "clocks": clk, "e2e": e2e}
+            "roofline": roofline, "step_roofline": step_roofline, "gpu_launches": int(launches), "clocks": clk,
+            "e2e": e2e}
     if rank == 0 and world == 1 and not args.no_comparator:
         try:
             comp, rel = fp64_torch_comparator(p, b_dev)
