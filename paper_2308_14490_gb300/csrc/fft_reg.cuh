@@ -24,6 +24,15 @@ namespace az {
 // the (compile-time, after unrolling) output slot of the butterfly: an
 // epilogue that multiplies by w^(c * o) can then form it from w^(c * o0) and
 // the powers w^(c * Ns * 2^b) instead of one table gather per output.
+// The first stage reads input p through pro(p), or, when the prologue accepts
+// them, pro(p, g, u) with the butterfly group g and slot u of this thread
+// (compile-time after unrolling; p = tl + g P + u n/R).
+template <typename V, typename Pro>
+__device__ __forceinline__ V pro_call(Pro& pro, int p, int g, int u) {
+  if constexpr (std::is_invocable_v<Pro&, int, int, int>) return pro(p, g, u);
+  else return pro(p);
+}
+
 template <typename Epi, typename V>
 __device__ __forceinline__ void epi_call(Epi& epi, int o, const V& v, int u, int o0, int Ns) {
   if constexpr (std::is_invocable_v<Epi&, int, V, int, int, int>) epi(o, v, u, o0, Ns);
@@ -49,7 +58,7 @@ __device__ __forceinline__ void fft_stage(V (&v)[E], V* __restrict__ sm, int log
 #pragma unroll
       for (int u = 0; u < R; ++u) {
         const int p = j + u * nbf;
-        if (first) v[g * R + u] = pro(p);
+        if (first) v[g * R + u] = pro_call<V>(pro, p, g, u);
         else v[g * R + u] = sm[padix<PADSH>(line * cs + p * is)];
       }
     }

@@ -1144,7 +1144,7 @@ template <typename T> struct EPT {
 // constants (the passes are issue-bound, about half of it integer work).
 struct ShapeRT {
   static constexpr bool fixed = false;
-  static constexpr int logC = 0;
+  static constexpr int logD1 = 0, logD0 = 0, logN1 = 0, logC = 0;
 };
 template <int LL, int LS, int LC>
 struct Shape1D {
@@ -1319,6 +1319,48 @@ __global__ void __launch_bounds__(REG_THREADS, REG_MINB) k_rowfold_r(Geom g_in, 
   V* X3 = X3base + (int64_t)blockIdx.y * g.N;
   const int G0 = blockIdx.x * GPB;
   const V* twp = (const V*)tb.tw;
+  if constexpr (S::fixed && E == 16 && E2 == 8 && S::logD1 - S::logN1 == 1 && S::logN1 == 10) {
+    // 1D, s = 2, N1 = 1024: the last radix-16 stage of the forward row FFT
+    // leaves thread tl with the outputs tl + 128 u (u < 16), which hold both
+    // members k1 and k1 + N1 of every alias pair this thread folds, and the
+    // first (radix-2) stage of the inverse N1 FFT reads exactly the folded
+    // values tl + 128 q (q < 8) of the same thread: the fold runs in
+    // registers, without the shared-memory round trip of the row
+    constexpr int P = 128;
+    const int lr = threadIdx.x >> 7, tl = threadIdx.x & (P - 1);
+    const int row = G0 + lr;
+    const V* xr = X1 + ((int64_t)row << g.logD1);
+    V fwd[16];
+    {
+      auto pro = [&](int p) -> V { return xr[p]; };
+      auto epi = [&](int o, V v, int u, int o0, int Ns) { fwd[u] = v; };
+      fft_reg<V, E, false, PADC>(smX, g.logD1, true, lr, tl, g.D1, 1, twp, TW_N >> g.logD1, pro, epi);
+    }
+    const T* hr = H + ((int64_t)row << g.logD1);
+    BigTwPow<V> tw;
+    const V* nA = (const V*)tb.bigNA;
+    const V* nB = (const V*)tb.bigNB;
+    {
+      int NsL, RL;
+      last_stage_shape(g.logN1, 3, NsL, RL);
+      tw.init(nA, nB, row, NsL, RL, true);
+    }
+    // inverse first stage: radix 2, 4 groups, p = tl + 128 (g + 4 u)
+    auto pro = [&](int p, int gq, int u) -> V {
+      const int q = gq + 4 * u;
+      const T h0 = __ldg(hr + tl + P * q), h1 = __ldg(hr + tl + P * (q + 8));
+      V o;
+      o.x = h0 * fwd[q].x + h1 * fwd[q + 8].x;
+      o.y = h0 * fwd[q].y + h1 * fwd[q + 8].y;
+      return o;
+    };
+    auto epi = [&](int n1, V v, int u, int o0, int Ns) {
+      v = cmul(v, tw.at(nA, nB, row, u, o0, true));
+      X3[(row << g.logN1) + n1] = v;
+    };
+    fft_reg<V, E2, true, PADC>(smF, g.logN1, true, lr, tl, g.N1, 1, twp, TW_N >> g.logN1, pro, epi);
+    return;
+  }
   // forward FFT of the rows: P1 = D1/E threads per row
   {
     const int logP1 = g.logD1 - (E == 16 ? 4 : (E == 8 ? 3 : 2));
