@@ -67,7 +67,9 @@ typedef struct {
 
 typedef struct {
   int32_t precision;    /* AZ_FP64, or AZ_MIXED: FP32 transforms/sketch, FP64 factor work and residual */
-  int32_t k;            /* sketch width r + p (number of random columns, Sec. 3.2.3) */
+  int32_t k;            /* sketch width r + p (number of random columns, Sec. 3.2.3), 1..4096; 0 = adaptive:
+                           widths 64, 128, ... until the k-th singular value of the sketch is below
+                           1e-7 (FP64) or 1e-4 (mixed) of the largest (az_get_info reports the k used) */
   double tau_svd;       /* relative truncation of the low-rank solve (0 = default: 1e-8) */
   double tau_sym;       /* symbol truncation: S_k^{-1} := 0 if S_k <= tau_sym^2 max S (0 = exact) */
   uint64_t seed;        /* Philox key of the random test matrix */

@@ -611,8 +611,40 @@ az_status az_query_footprint(const az_grid* gr, int64_t M, int64_t n_boundary, c
   return AZ_OK;
 }
 
+static az_status setup_fixed(const az_grid* gr, const uint8_t* mask, const double* bpts, int64_t n_boundary,
+                             double eps, int32_t kernel, double boundary_weight, const az_options* opt, void* stream,
+                             az_handle* out);
+
+// k = 0: the sketch width grows (64, 128, ... up to 4096 and N) until the
+// k-th singular value of the sketch falls below tau_sat sigma_1, i.e. the
+// sketch holds every direction of the perturbation above the level that
+// precision resolves (FP64: 1e-7; mixed: 1e-4, the FP32 sketch's noise
+// floor).  Each attempt is a complete setup; a saturated one is discarded.
 az_status az_setup(const az_grid* gr, const uint8_t* mask, const double* bpts, int64_t n_boundary, double eps,
                    int32_t kernel, double boundary_weight, const az_options* opt, void* stream, az_handle* out) {
+  if (!opt || opt->k != 0) return setup_fixed(gr, mask, bpts, n_boundary, eps, kernel, boundary_weight, opt, stream, out);
+  if (!out || !gr) { set_error("az_setup: null argument"); return AZ_ERR_ARG; }
+  *out = nullptr;
+  int64_t N = 1;
+  for (int d = 0; d < gr->dim && d < 2; ++d) N *= gr->n[d];
+  const double tsat = opt->precision == AZ_FP64 ? 1e-7 : 1e-4;
+  az_options o = *opt;
+  for (int k = 64;; k *= 2) {
+    o.k = (int)std::min<int64_t>(std::min<int64_t>(k, 4096), std::max<int64_t>(1, N));
+    az_handle h = nullptr;
+    AZ_TRY(setup_fixed(gr, mask, bpts, n_boundary, eps, kernel, boundary_weight, &o, stream, &h));
+    az_info_t info;
+    const az_status rc = az_get_info(h, &info);
+    if (rc) { az_destroy(h); return rc; }
+    const bool saturated = info.rank >= o.k && info.sigma_max > 0 && info.sigma_min_kept > tsat * info.sigma_max;
+    if (!saturated || o.k >= 4096 || o.k >= N) { *out = h; return AZ_OK; }
+    az_destroy(h);
+  }
+}
+
+static az_status setup_fixed(const az_grid* gr, const uint8_t* mask, const double* bpts, int64_t n_boundary,
+                             double eps, int32_t kernel, double boundary_weight, const az_options* opt, void* stream,
+                             az_handle* out) {
   if (!out) { set_error("az_setup: null output handle"); return AZ_ERR_ARG; }
   *out = nullptr;
   if (!mask) { set_error("az_setup: Omega mask is required"); return AZ_ERR_ARG; }
