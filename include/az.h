@@ -74,6 +74,9 @@ typedef struct {
   double tau_sym;       /* symbol truncation: S_k^{-1} := 0 if S_k <= tau_sym^2 max S (0 = exact) */
   uint64_t seed;        /* Philox key of the random test matrix */
   int32_t refine_steps; /* FP64-residual refinement steps per solve (default 1 in MIXED, 0 in FP64) ; -1 = default */
+  double k0;            /* collocation (AZ_NEG_LAPLACE_GAUSS) only: wavenumber of the Helmholtz operator
+                           -(Laplacian + k0^2) of Sec. 6.2 (0 = Poisson); the interior rows are
+                           -(Laplacian + k0^2) phi_j / (2 eps^2) */
 } az_options;
 
 typedef struct {

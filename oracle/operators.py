@@ -15,10 +15,11 @@ Paper passages followed:
 * Sec. 5.1 Eqs. (circulant_system_2d), (B_pinv_2d): 2D is the tensor product;
   the coefficient index is j = jx*Ny + jy and the grid index i = ix*Ly + iy
   (x-major), as in the paper's j = (m-1) N^y + n.
-* Sec. 6.2 (Ai_2d_bvp and the three-term splitting of A^ic): the Poisson rows
-  are -(phi''_x phi_y + phi_x phi''_y) divided by 2 eps^2 (the normalisation of
-  Example 6.1 read as a division, so the rows have O(1) entries; k0 = 0), and
-  Z* = [F B^dagger P E, 0] has zero columns for the boundary rows.
+* Sec. 6.2 (Ai_2d_bvp and the three-term splitting of A^ic): the Helmholtz
+  rows are -(phi''_x phi_y + phi_x phi''_y + k0^2 phi_x phi_y) divided by
+  2 eps^2 (the normalisation of Example 6.1 read as a division, so the rows
+  have O(1) entries; k0 = 0 is the Poisson operator), and Z* = [F B^dagger P E, 0]
+  has zero columns for the boundary rows.
 
 Reading of the symbol truncation: S_k^{-1} is replaced by 0 when
 S_k <= tau_sym^2 * max S (tau_sym = 0 gives the exact pseudo-inverse).
@@ -31,7 +32,7 @@ from . import rbf
 class Operator:
     """A^c, A and Z* for one problem (approximation or Poisson collocation)."""
 
-    def __init__(self, grid, mask, kind="approx", boundary=None, weight=1.0, tau_sym=0.0):
+    def __init__(self, grid, mask, kind="approx", boundary=None, weight=1.0, tau_sym=0.0, k0=0.0):
         self.grid = grid
         self.dim = grid.dim
         self.n = tuple(int(v) for v in grid.n)
@@ -41,6 +42,7 @@ class Operator:
         self.Ltot = grid.Ltot
         self.eps = grid.eps
         self.kind = kind
+        self.k0 = float(k0)
         self.mask = np.asarray(mask).reshape(-1).astype(np.uint8)
         assert self.mask.size == self.Ltot
         self.idx = np.flatnonzero(self.mask)          # compact index map (S1)
@@ -67,7 +69,7 @@ class Operator:
         if self.kind == "approx":
             return np.outer(gx, gy)
         hx, hy = self.G2
-        return -(np.outer(hx, gy) + np.outer(gx, hy)) / (2.0 * self.eps ** 2)
+        return -(np.outer(hx, gy) + np.outer(gx, hy) + self.k0 ** 2 * np.outer(gx, gy)) / (2.0 * self.eps ** 2)
 
     def _fold(self, F):
         """Sum an L-grid array over each alias group {k + qN}: result on the N-grid."""
@@ -163,7 +165,7 @@ class Operator:
         (ax0, ax2), (ay0, ay2) = mats
         if self.kind == "approx":
             return np.kron(ax0, ay0)
-        return -(np.kron(ax2, ay0) + np.kron(ax0, ay2)) / (2.0 * self.eps ** 2)
+        return -(np.kron(ax2, ay0) + np.kron(ax0, ay2) + self.k0 ** 2 * np.kron(ax0, ay0)) / (2.0 * self.eps ** 2)
 
     def A_dense(self):
         A = self.Ac_dense()[self.idx]

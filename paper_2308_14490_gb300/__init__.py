@@ -30,7 +30,8 @@ class az_grid(ctypes.Structure):
 
 class az_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("k", ctypes.c_int32), ("tau_svd", ctypes.c_double),
-                ("tau_sym", ctypes.c_double), ("seed", ctypes.c_uint64), ("refine_steps", ctypes.c_int32)]
+                ("tau_sym", ctypes.c_double), ("seed", ctypes.c_uint64), ("refine_steps", ctypes.c_int32),
+                ("k0", ctypes.c_double)]
 
 
 class az_info_t(ctypes.Structure):
@@ -107,9 +108,10 @@ def make_grid(dim, n, s, T):
     return g
 
 
-def make_options(precision=AZ_MIXED, k=24, tau_svd=0.0, tau_sym=0.0, seed=1, refine_steps=-1):
+def make_options(precision=AZ_MIXED, k=24, tau_svd=0.0, tau_sym=0.0, seed=1, refine_steps=-1, k0=0.0):
     o = az_options()
     o.precision, o.k, o.tau_svd, o.tau_sym, o.seed, o.refine_steps = precision, k, tau_svd, tau_sym, seed, refine_steps
+    o.k0 = k0
     return o
 
 

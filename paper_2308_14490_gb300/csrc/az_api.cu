@@ -27,6 +27,7 @@ struct az_setup_t {
   Geom g{};
   int kind = 0, precision = AZ_MIXED, k = 0, refine = 1;
   double eps = 0, tau_svd = 1e-8, tau_sym = 0, bweight = 1.0, floor = 0;
+  double k0 = 0;            // Helmholtz wavenumber of the collocation operator (0 = Poisson)
   uint64_t seed = 0;
   int64_t M = 0, Mb = 0, Mtot = 0;
   int64_t ldm = 0;        // leading dimension of Ut and gb: Mtot rounded up to 32 (16-byte TMA strides)
@@ -319,6 +320,11 @@ az_status build_symbol(az_setup_t* h, cudaStream_t st) {
       for (int q = 0; q < nder; ++q) {
         const double hL = 2.0 * g.T[d] / (double)g.Ld[d];
         AZ_TRY(launch_samples(h->samp[d][q], g.Ld[d], hL, eps, q == 0 ? 0 : 2, image_count(eps, g.T[d]), st));
+        // Helmholtz (Sec. 6.2): -(phi''_x phi_y + phi_x phi''_y + k0^2 phi_x phi_y) =
+        // -(phi''_x phi_y + phi_x (phi''_y + k0^2 phi_y)): the k0 term joins the y
+        // second-derivative samples, and taps, symbol, stencils and residual follow
+        if (d == 1 && q == 1 && h->k0 != 0.0)
+          AZ_TRY(launch_axpy(g.Ld[1], h->k0 * h->k0, h->samp[1][0], h->samp[1][1], st));
         AZ_TRY(launch_taps(h->samp[d][q], g.Ld[d], h->W64[d], h->taps64[d + 2 * q], h->W32[d], h->taps32[d + 2 * q],
                            st, h->tapsH[d + 2 * q], h->tapsL[d + 2 * q]));
       }
@@ -653,7 +659,8 @@ static az_status setup_fixed(const az_grid* gr, const uint8_t* mask, const doubl
   if (n_boundary < 0 || (n_boundary > 0 && !bpts)) { set_error("az_setup: boundary points"); return AZ_ERR_ARG; }
   az_options o;
   if (opt) o = *opt;
-  else { o.precision = AZ_MIXED; o.k = 24; o.tau_svd = 0; o.tau_sym = 0; o.seed = 1; o.refine_steps = -1; }
+  else { o.precision = AZ_MIXED; o.k = 24; o.tau_svd = 0; o.tau_sym = 0; o.seed = 1; o.refine_steps = -1; o.k0 = 0; }
+  if (!std::isfinite(o.k0)) { set_error("az_setup: k0 must be finite"); return AZ_ERR_ARG; }
   if (o.precision != AZ_FP64 && o.precision != AZ_MIXED) { set_error("az_setup: precision"); return AZ_ERR_ARG; }
   if (o.k < 1 || o.k > 4096) { set_error("az_setup: k must be in [1, 4096]"); return AZ_ERR_ARG; }
   if (kernel == AZ_NEG_LAPLACE_GAUSS && (!gr || gr->dim != 2)) { set_error("az_setup: collocation needs dim = 2"); return AZ_ERR_ARG; }
@@ -667,6 +674,7 @@ static az_status setup_fixed(const az_grid* gr, const uint8_t* mask, const doubl
   h->eps = eps;
   h->tau_svd = o.tau_svd > 0 ? o.tau_svd : 1e-8;
   h->tau_sym = o.tau_sym > 0 ? o.tau_sym : 0.0;
+  h->k0 = h->kind == 1 ? o.k0 : 0.0;
   h->seed = o.seed;
   h->refine = o.refine_steps >= 0 ? o.refine_steps : (o.precision == AZ_MIXED ? 1 : 0);
   h->bweight = boundary_weight;

@@ -147,6 +147,16 @@ __device__ double periodised_sample(int64_t m, int64_t L, double hL, double eps,
   }
   return acc;
 }
+__global__ void k_axpy(int64_t n, double a, const double* __restrict__ x, double* __restrict__ y) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] += a * x[i];
+}
+az_status launch_axpy(int64_t n, double a, const double* x, double* y, cudaStream_t st) {
+  ProfScope ps("samples", 24.0 * n, st);
+  k_axpy<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, a, x, y);
+  AZ_LAUNCH_CHECK();
+  return AZ_OK;
+}
 __global__ void k_samples(double* g, int64_t L, double hL, double eps, int deriv, int pimg) {
   int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= L) return;

@@ -12,6 +12,7 @@ az_status launch_compact(const uint8_t* mask, int64_t L, int32_t* pos2m, int32_t
 // S2: periodised samples g(m) = sum_p f((m + p L) h_L) on one dimension
 // (f = phi or phi''), FP64, m = 0..L-1.
 az_status launch_samples(double* g, int64_t L, double hL, double eps, int deriv, int pimg, cudaStream_t st);
+az_status launch_axpy(int64_t n, double a, const double* x, double* y, cudaStream_t st);   // y += a x
 // 1D: stencil taps from the image sum, and Ghat from its Poisson-summation form
 az_status launch_taps_direct(int64_t L, double hL, double eps, int pimg, int W64, double* t64, int W32, float* t32,
                              cudaStream_t st, float* th, float* tl);

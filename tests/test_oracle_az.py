@@ -138,6 +138,16 @@ def test_poisson_az_matches_direct():
         assert abs(r2 - r1) <= 0.05 * r1 and r1 < 2e-3
 
 
+def test_helmholtz_az_matches_direct():
+    p = W.helmholtz(n=16, nb=64, k=300, k0=6.0)
+    op = Operator(p.grid, p.mask, "poisson", p.boundary, p.weight, k0=p.k0)
+    b = np.concatenate([p.rhs() / (2 * op.eps ** 2), p.weight * p.boundary_rhs()])
+    x = AZ(op, p.k, 11, 1e-8).solve(b)
+    xd, _ = direct_tsvd(op.A_dense(), b, 1e-8)
+    r2, r1 = relres(op, x, b)[0], relres(op, xd, b)[0]
+    assert abs(r2 - r1) <= 0.05 * r1 and r1 < 2e-3
+
+
 def test_refinement_keeps_relres():
     p = W.config1()
     op = Operator(p.grid, p.mask)

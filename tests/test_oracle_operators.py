@@ -60,6 +60,35 @@ def test_dense_poisson_rows_from_definition():
         assert abs(A[ix * 12 + iy, jx * 6 + jy] - ref) < 1e-13
 
 
+def test_dense_helmholtz_rows_from_definition():
+    # Sec. 6.2 with k0 != 0: -(phi''(x)phi(y) + phi(x)phi''(y) + k0^2 phi(x)phi(y)) / (2 eps^2).
+    g = W.Grid(2, (6, 6), (2, 2), (1.0, 1.0), 1.0)
+    k0 = 7.3
+    op = Operator(g, np.ones(g.Ltot, np.uint8), kind="poisson", k0=k0)
+    A = op.Ac_dense()
+    e = g.eps
+    for (ix, iy, jx, jy) in [(0, 0, 0, 0), (3, 5, 1, 2), (11, 2, 5, 5), (7, 7, 3, 4)]:
+        x = -1 + ix * 2 / 12
+        y = -1 + iy * 2 / 12
+        cx = -1 + jx * 2 / 6
+        cy = -1 + jy * 2 / 6
+        px, py = _phi_per(x - cx, e, 1.0), _phi_per(y - cy, e, 1.0)
+        ref = -(_phi_per(x - cx, e, 1.0, 2) * py + px * _phi_per(y - cy, e, 1.0, 2) + k0 ** 2 * px * py) / (2 * e * e)
+        assert abs(A[ix * 12 + iy, jx * 6 + jy] - ref) < 1e-13
+
+
+def test_helmholtz_fft_forms_equal_dense():
+    g = W.Grid(2, (8, 8), (2, 2), (1.0, 1.0), 1.0)
+    op = Operator(g, np.ones(g.Ltot, np.uint8), kind="poisson", k0=5.0)
+    a = np.random.default_rng(6).standard_normal((g.N, 3))
+    d = op.Ac_dense() @ a
+    assert np.abs(op.Ac(a) - d).max() <= 1e-13 * np.abs(d).max()
+    opm = Operator(g, W.disc_mask(g, 0.75), kind="poisson", boundary=W.star_boundary(10), weight=3.0, k0=5.0)
+    y = np.random.default_rng(7).standard_normal((opm.M + opm.Mb, 2))
+    ref = opm.Zstar_dense() @ y
+    assert np.abs(opm.Zstar(y) - ref).max() <= 1e-11 * np.abs(ref).max()
+
+
 def test_boundary_rows_from_definition():
     g = W.Grid(2, (8, 8), (2, 2), (1.0, 1.0), 1.0)
     pts = W.star_boundary(16)

@@ -132,6 +132,7 @@ class Problem:
     weight: float = 1.0
     kind: str = "approx"                            # "approx" | "poisson"
     exact: list = field(default_factory=list)      # exact solutions (poisson)
+    k0: float = 0.0                                 # Helmholtz wavenumber of the collocation operator
 
     def rhs(self) -> np.ndarray:
         pts = kept_points(self.grid, self.mask)
@@ -149,6 +150,15 @@ def config1() -> Problem:
     m = interval_mask(g, -0.5, 0.5)
     f = lambda p: np.exp(p[:, 0]) * np.cos(8 * p[:, 0])
     return Problem("1d-n256", g, m, 20, [f])
+
+
+def helmholtz(n: int = 16, nb: int = 64, k: int = 64, k0: float = 6.0, weight: float = 10.0) -> Problem:
+    """2D Helmholtz -(Lap + k0^2) u = f on the config-4 star, u = sin(pi x)cos(pi y)."""
+    g = Grid(2, (n, n), (2, 2), (1.0, 1.0), 1.0)
+    m = star_mask(g)
+    u = lambda p: np.sin(np.pi * p[:, 0]) * np.cos(np.pi * p[:, 1])
+    f = lambda p: (2 * np.pi ** 2 - k0 ** 2) * np.sin(np.pi * p[:, 0]) * np.cos(np.pi * p[:, 1])
+    return Problem(f"2d-star-helmholtz-n{n}", g, m, k, [f], star_boundary(nb), [u], weight, "poisson", [u], k0)
 
 
 def cos_family(nrhs: int, seed: int = SEED):
