@@ -70,7 +70,10 @@ typedef struct {
   int32_t k;            /* sketch width r + p (number of random columns, Sec. 3.2.3), 1..4096; 0 = adaptive:
                            widths 64, 128, ... until the k-th singular value of the sketch is below
                            1e-7 (FP64) or 1e-4 (mixed) of the largest (az_get_info reports the k used) */
-  double tau_svd;       /* relative truncation of the low-rank solve (0 = default: 1e-8) */
+  double tau_svd;       /* relative truncation of the low-rank solve (0 = default: 1e-8).  The narrow
+                           (k <= 64) factorisation works on the Gram matrix and resolves singular values
+                           down to about 1e-8 of the largest, so in AZ_FP64 a tau_svd below 1e-8 takes the
+                           Householder factorisation of the wide sketches at any width */
   double tau_sym;       /* symbol truncation: S_k^{-1} := 0 if S_k <= tau_sym^2 max S (0 = exact) */
   uint64_t seed;        /* Philox key of the random test matrix */
   int32_t refine_steps; /* FP64-residual refinement steps per solve (default 1 in MIXED, 0 in FP64) ; -1 = default */

@@ -15,6 +15,9 @@ Paper passages followed:
 * Sec. 5.1 Eqs. (circulant_system_2d), (B_pinv_2d): 2D is the tensor product;
   the coefficient index is j = jx*Ny + jy and the grid index i = ix*Ly + iy
   (x-major), as in the paper's j = (m-1) N^y + n.
+* Sec. 6.1 Example 6.1 (the ODE u'' + k0^2 u = g on [-1, 1] with Dirichlet rows
+  at the end points): 1D interior rows -(phi'' + k0^2 phi) / (2 eps^2), boundary
+  rows phi_j(x_b) times the weight, Z* with zero columns for those rows.
 * Sec. 6.2 (Ai_2d_bvp and the three-term splitting of A^ic): the Helmholtz
   rows are -(phi''_x phi_y + phi_x phi''_y + k0^2 phi_x phi_y) divided by
   2 eps^2 (the normalisation of Example 6.1 read as a division, so the rows
@@ -62,9 +65,9 @@ class Operator:
     # ------------------------------------------------------------------ symbols
     def _full_symbol(self):
         if self.dim == 1:
-            if self.kind != "approx":
-                raise ValueError("1D collocation is not part of this oracle")
-            return self.G0[0].copy()
+            if self.kind == "approx":
+                return self.G0[0].copy()
+            return -(self.G2[0] + self.k0 ** 2 * self.G0[0]) / (2.0 * self.eps ** 2)
         gx, gy = self.G0
         if self.kind == "approx":
             return np.outer(gx, gy)
@@ -99,8 +102,10 @@ class Operator:
         return v.reshape(self.Ltot, -1)
 
     def boundary_rows(self, a):
-        """w * A^b a: Dirichlet rows phi_j(p_b) at the boundary points (Sec. 6.2)."""
+        """w * A^b a: Dirichlet rows phi_j(p_b) at the boundary points (Sec. 6.1, 6.2)."""
         a = np.asarray(a, dtype=np.float64)
+        if self.dim == 1:
+            return self.weight * (self._boundary_factors()[0] @ a)
         Bx, By = self._boundary_factors()
         a2 = a.reshape(self.n[0], self.n[1], -1)
         t = np.einsum("bi,ijc->bjc", Bx, a2)
@@ -108,7 +113,7 @@ class Operator:
 
     def _boundary_factors(self):
         out = []
-        for d in range(2):
+        for d in range(self.dim):
             T = self.grid.T[d]
             c = -T + np.arange(self.n[d]) * (2.0 * T / self.n[d])
             P = rbf.image_count(self.eps, T)
@@ -161,7 +166,9 @@ class Operator:
             else:
                 mats.append((m0, None))
         if self.dim == 1:
-            return mats[0][0]
+            if self.kind == "approx":
+                return mats[0][0]
+            return -(mats[0][1] + self.k0 ** 2 * mats[0][0]) / (2.0 * self.eps ** 2)
         (ax0, ax2), (ay0, ay2) = mats
         if self.kind == "approx":
             return np.kron(ax0, ay0)
@@ -169,7 +176,9 @@ class Operator:
 
     def A_dense(self):
         A = self.Ac_dense()[self.idx]
-        if self.Mb:
+        if self.Mb and self.dim == 1:
+            A = np.concatenate([A, self.weight * self._boundary_factors()[0]], axis=0)
+        elif self.Mb:
             Bx, By = self._boundary_factors()
             Ab = self.weight * (Bx[:, :, None] * By[:, None, :]).reshape(self.Mb, -1)
             A = np.concatenate([A, Ab], axis=0)

@@ -22,6 +22,7 @@ using namespace az;
 // Sketch widths up to this use the one-CTA factorisation and register-blocked
 // tall products; wider sketches use the Householder QR + GEMM path.
 static constexpr int kNarrowK = 64;
+static constexpr double kGramTau = 1e-8;   // smallest sigma / sigma_1 the FP64 Gram route resolves
 
 struct az_setup_t {
   Geom g{};
@@ -312,9 +313,11 @@ az_status build_symbol(az_setup_t* h, cudaStream_t st) {
   if (g.dim == 1) {
     // taps from the image sum; Ghat = DFT_L(g) in its Poisson-summation form
     const double hL = 2.0 * g.T[0] / (double)g.Ld[0];
+    // (collocation, Example 6.1: the interior kernel -(phi'' + k0^2 phi) / (2 eps^2)
+    // takes the place of phi in the taps and the symbol; boundary rows use phi)
     AZ_TRY(launch_taps_direct(g.Ld[0], hL, eps, image_count(eps, g.T[0]), h->W64[0], h->taps64[0], h->W32[0],
-                              h->taps32[0], st, h->tapsH[0], h->tapsL[0]));
-    AZ_TRY(launch_symbol_closed_1d(g.L, eps * hL, h->Ghat, st));
+                              h->taps32[0], st, h->tapsH[0], h->tapsL[0], h->kind, h->k0));
+    AZ_TRY(launch_symbol_closed_1d(g.L, eps * hL, h->Ghat, st, h->kind, hL, h->k0, eps));
   } else {
     for (int d = 0; d < g.dim; ++d)
       for (int q = 0; q < nder; ++q) {
@@ -411,7 +414,7 @@ az_status sketch_and_factor(az_setup_t* h, cudaStream_t st) {
   }
   // pass 1: G1 = Y^T Y, SVQB
   AZ_TRY((launch_gram<T, T>(Y, h->Mtot, k, Y, h->Mtot, k, h->Mtot, h->partial, h->G, st)));
-  const double taug = Prec<T>::fp64 ? 1e-8 : 1e-7;
+  const double taug = Prec<T>::fp64 ? kGramTau : 1e-7;
   AZ_TRY(launch_factor1(h->G, k, taug, h->floor * h->floor, h->V, h->lam, h->B1, h->info, st));
   // pass 2: Q1 = Y B1, G2 = Q1^T Q1, Cholesky, SVD of the small factor, Ut = Q1 T
   if (Prec<T>::fp64) {
@@ -621,6 +624,21 @@ static az_status setup_fixed(const az_grid* gr, const uint8_t* mask, const doubl
                              double eps, int32_t kernel, double boundary_weight, const az_options* opt, void* stream,
                              az_handle* out);
 
+// The mixed path inverts the symbol in FP32.  Within one alias group of the
+// Gaussian symbol (Eq. periodic_rbf, Poisson summation) the largest member
+// lies at most half a coarse period from the origin, where Ghat has fallen
+// by exp(-(pi / (2 eps h))^2) from its peak; Z* scales FP32 rounding by that
+// range.  The sketch stays usable while the amplified rounding,
+// 2^-24 exp((pi / (2 eps h))^2), is below 1e-3, i.e. eps h >= 0.504 (the
+// eps h = 1 regime of the large workloads passes; the tau0 = 1e-10 regime of
+// Eq. constant_shapeparam, eps h = 0.33, does not and needs AZ_FP64).
+static bool mixed_resolves(const Geom& g, double eps) {
+  double epsh = 1e300;
+  for (int d = 0; d < g.dim; ++d) epsh = std::min(epsh, eps * 2.0 * g.T[d] / (double)(g.Ld[d] / g.s[d]));
+  const double a = M_PI / (2.0 * epsh);
+  return a * a <= std::log(1e-3 * 16777216.0);
+}
+
 // k = 0: the sketch width grows (64, 128, ... up to 4096 and N) until the
 // k-th singular value of the sketch falls below tau_sat sigma_1, i.e. the
 // sketch holds every direction of the perturbation above the level that
@@ -663,10 +681,15 @@ static az_status setup_fixed(const az_grid* gr, const uint8_t* mask, const doubl
   if (!std::isfinite(o.k0)) { set_error("az_setup: k0 must be finite"); return AZ_ERR_ARG; }
   if (o.precision != AZ_FP64 && o.precision != AZ_MIXED) { set_error("az_setup: precision"); return AZ_ERR_ARG; }
   if (o.k < 1 || o.k > 4096) { set_error("az_setup: k must be in [1, 4096]"); return AZ_ERR_ARG; }
-  if (kernel == AZ_NEG_LAPLACE_GAUSS && (!gr || gr->dim != 2)) { set_error("az_setup: collocation needs dim = 2"); return AZ_ERR_ARG; }
+  if (!gr) { set_error("az_setup: grid"); return AZ_ERR_ARG; }
   az_setup_t* h = new az_setup_t();
   az_status rc = make_geom(gr, h->g);
   if (rc) { delete h; return rc; }
+  if (o.precision == AZ_MIXED && !mixed_resolves(h->g, eps)) {
+    delete h;
+    set_error("az_setup: eps h is too small for the FP32 sketch (mixed precision needs eps h >= 0.504); use AZ_FP64");
+    return AZ_ERR_ARG;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   h->kind = kernel == AZ_NEG_LAPLACE_GAUSS ? 1 : 0;
   h->precision = o.precision;
@@ -707,8 +730,8 @@ static az_status setup_fixed(const az_grid* gr, const uint8_t* mask, const doubl
       if ((int64_t)ends[1] - ends[0] + 1 == M) { h->g.run0 = ends[0]; h->g.runM = M; }
     }
     if (h->Mb) {
-      rc = dalloc_t(h, &h->bpts, 2 * h->Mb); if (rc) break;
-      if (cudaMemcpyAsync(h->bpts, bpts, 2 * h->Mb * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess) { rc = AZ_ERR_CUDA; break; }
+      rc = dalloc_t(h, &h->bpts, (size_t)g.dim * h->Mb); if (rc) break;   // Mb x dim
+      if (cudaMemcpyAsync(h->bpts, bpts, (size_t)g.dim * h->Mb * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess) { rc = AZ_ERR_CUDA; break; }
     }
     // twiddle tables (host-built constants)
     {
@@ -743,7 +766,10 @@ static az_status setup_fixed(const az_grid* gr, const uint8_t* mask, const doubl
     rc = dalloc_t(h, &h->sig, h->k); if (rc) break;
     rc = dalloc_t(h, &h->info, 1); if (rc) break;
     rc = alloc_workspace(h); if (rc) break;
-    if (h->k > kNarrowK) {
+    // The Gram route squares the sketch's condition number, so in FP64 it
+    // resolves singular values down to about 1e-8 sigma_1; a tighter tau
+    // takes the Householder route whatever the width.
+    if (h->k > kNarrowK || (h->precision == AZ_FP64 && h->tau_svd < kGramTau)) {
       size_t wb = 0;
       rc = large_create(&h->wide, h->Mtot, h->k, h->precision == AZ_FP64, h->Q1, &wb);
       h->bytes += wb;

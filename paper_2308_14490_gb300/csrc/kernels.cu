@@ -178,21 +178,28 @@ __global__ void k_taps(const double* g, int64_t L, int W64, double* t64, int W32
   if (i <= 2 * W32) t32[i] = (float)g[fmod_pos((int64_t)i - W32, L)];
 }
 // Taps straight from the image sum (1D: the L samples themselves are not needed)
+// (ode != 0: taps of the collocation kernel -(phi'' + k0^2 phi) / (2 eps^2), Example 6.1)
+__device__ __forceinline__ double tap_value(int64_t m, int64_t L, double hL, double eps, int pimg, int ode, double k0) {
+  const double g0 = periodised_sample(m, L, hL, eps, 0, pimg);
+  if (!ode) return g0;
+  const double g2 = periodised_sample(m, L, hL, eps, 2, pimg);
+  return -(g2 + k0 * k0 * g0) / (2.0 * eps * eps);
+}
 __global__ void k_taps_direct(int64_t L, double hL, double eps, int pimg, int W64, double* t64, int W32, float* t32,
-                              float* th, float* tl) {
+                              float* th, float* tl, int ode, double k0) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i <= 2 * W64) {
-    const double v = periodised_sample((int64_t)i - W64, L, hL, eps, 0, pimg);
+    const double v = tap_value((int64_t)i - W64, L, hL, eps, pimg, ode, k0);
     t64[i] = v;
     if (th) { const float h = (float)v; th[i] = h; tl[i] = (float)(v - (double)h); }
   }
-  if (i <= 2 * W32) t32[i] = (float)periodised_sample((int64_t)i - W32, L, hL, eps, 0, pimg);
+  if (i <= 2 * W32) t32[i] = (float)tap_value((int64_t)i - W32, L, hL, eps, pimg, ode, k0);
 }
 az_status launch_taps_direct(int64_t L, double hL, double eps, int pimg, int W64, double* t64, int W32, float* t32,
-                             cudaStream_t st, float* th, float* tl) {
+                             cudaStream_t st, float* th, float* tl, int ode, double k0) {
   const int W = W64 > W32 ? W64 : W32;
   ProfScope ps("taps", 12.0 * (2 * W + 1), st);
-  k_taps_direct<<<(2 * W + 1 + 127) / 128, 128, 0, st>>>(L, hL, eps, pimg, W64, t64, W32, t32, th, tl);
+  k_taps_direct<<<(2 * W + 1 + 127) / 128, 128, 0, st>>>(L, hL, eps, pimg, W64, t64, W32, t32, th, tl, ode, k0);
   AZ_LAUNCH_CHECK();
   return AZ_OK;
 }
@@ -208,15 +215,18 @@ az_status launch_taps_direct(int64_t L, double hL, double eps, int pimg, int W64
 // exponentials per image and J outputs instead of one per output (FP64 exp is
 // slow on this part), at a cost of about 2J rounding units.
 constexpr int SYM_J = 16;
-__global__ void k_symbol_closed_1d(int64_t L, double a, int Q, int J, double* Ghat) {
+// (ode != 0: the symbol of -(phi'' + k0^2 phi) / (2 eps^2); the Fourier
+// transform of phi'' is -(2 pi nu)^2 times that of phi, nu = (t + p) / h_L)
+__global__ void k_symbol_closed_1d(int64_t L, double a, int Q, int J, double* Ghat, int ode, double hL, double kw,
+                                   double eps) {
   const int64_t k0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * J;
   if (k0 >= L) return;
   const double c = (M_PI / a) * (M_PI / a);
   const double d = 1.0 / (double)L;
   const double t0 = (double)(k0 > L / 2 ? k0 - L : k0) * d;
-  double acc[SYM_J];
+  double acc[SYM_J], acc2[SYM_J];
 #pragma unroll
-  for (int j = 0; j < SYM_J; ++j) acc[j] = 0.0;
+  for (int j = 0; j < SYM_J; ++j) { acc[j] = 0.0; acc2[j] = 0.0; }
   const double q = exp(-2.0 * c * d * d);
   // the largest image over the run has exponent at most c * emax^2, with
   // emax the largest |t| of the run reduced to [-1/2, 1/2]; images whose
@@ -232,22 +242,30 @@ __global__ void k_symbol_closed_1d(int64_t L, double a, int Q, int J, double* Gh
     double f = exp(-c * d * (2.0 * u0 + d));
 #pragma unroll
     for (int j = 0; j < SYM_J; ++j) {
-      if (j < J) acc[j] += e;
+      if (j < J) {
+        acc[j] += e;
+        if (ode) {
+          const double u = u0 + j * d;
+          acc2[j] += e * u * u;
+        }
+      }
       e *= f;
       f *= q;
     }
   }
   const double sc = sqrt(M_PI) / a;
+  const double w2 = (2.0 * M_PI / hL) * (2.0 * M_PI / hL);
 #pragma unroll
   for (int j = 0; j < SYM_J; ++j)
-    if (j < J) Ghat[k0 + j] = sc * acc[j];
+    if (j < J) Ghat[k0 + j] = ode ? sc * (w2 * acc2[j] - kw * kw * acc[j]) / (2.0 * eps * eps) : sc * acc[j];
 }
-az_status launch_symbol_closed_1d(int64_t L, double a, double* Ghat, cudaStream_t st) {
+az_status launch_symbol_closed_1d(int64_t L, double a, double* Ghat, cudaStream_t st, int ode, double hL, double k0,
+                                  double eps) {
   const int Q = (int)std::ceil(0.5 + a * std::sqrt(745.0) / M_PI);
   const int J = (L % (2 * SYM_J) == 0) ? SYM_J : 1;   // runs end at k = L/2
   const int64_t nth = L / J;
   ProfScope ps("symbol", 8.0 * L, st);
-  k_symbol_closed_1d<<<(unsigned)((nth + 255) / 256), 256, 0, st>>>(L, a, Q, J, Ghat);
+  k_symbol_closed_1d<<<(unsigned)((nth + 255) / 256), 256, 0, st>>>(L, a, Q, J, Ghat, ode, hL, k0, eps);
   AZ_LAUNCH_CHECK();
   return AZ_OK;
 }
@@ -899,6 +917,18 @@ __global__ void k_boundary_rows(Geom g, T eps, T w, int Wc, const double* __rest
   if (m >= Mb) return;
   const int c = blockIdx.y;
   const TZ* z = zb + (int64_t)c * ldz;
+  if (g.dim == 1) {
+    // Dirichlet row of the ODE (Example 6.1): w sum_j phi_per(p - c_j) z_j
+    const double px = pts[m], hx = 2.0 * g.T[0] / g.n[0];
+    const int64_t cxi = (int64_t)floor((px + g.T[0]) / hx);
+    T acc = 0;
+    for (int64_t jx = cxi - Wc; jx <= cxi + Wc + 1; ++jx)
+      acc += gauss<T>((T)(px - (-g.T[0] + (double)jx * hx)), eps) * (T)z[fmod_pos(jx, g.n[0])];
+    T r = beta * w * acc;
+    if (bb) r += alpha * (T)bb[(int64_t)c * ldb + m];
+    outb[(int64_t)c * ldo + m] = (TO)r;
+    return;
+  }
   const double px = pts[2 * m], py = pts[2 * m + 1];
   const double hx = 2.0 * g.T[0] / g.n[0], hy = 2.0 * g.T[1] / g.n[1];
   const int64_t cxi = (int64_t)floor((px + g.T[0]) / hx), cyi = (int64_t)floor((py + g.T[1]) / hy);
@@ -920,7 +950,7 @@ __global__ void k_boundary_rows(Geom g, T eps, T w, int Wc, const double* __rest
 static int center_window(const Geom& g, double eps) {
   double h = 2.0 * g.T[0] / (double)g.n[0];
   int Wc = (int)std::ceil(std::sqrt(42.0) / (eps * h)) + 1;
-  int lim = (int)std::min<int64_t>(g.n[0], g.n[1]) / 2 - 1;
+  int lim = (int)(g.dim == 1 ? g.n[0] : std::min<int64_t>(g.n[0], g.n[1])) / 2 - 1;
   return std::max(0, std::min(Wc, lim));
 }
 template <typename T, typename TZ, typename TB, typename TO>

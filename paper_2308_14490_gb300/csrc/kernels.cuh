@@ -14,9 +14,11 @@ az_status launch_compact(const uint8_t* mask, int64_t L, int32_t* pos2m, int32_t
 az_status launch_samples(double* g, int64_t L, double hL, double eps, int deriv, int pimg, cudaStream_t st);
 az_status launch_axpy(int64_t n, double a, const double* x, double* y, cudaStream_t st);   // y += a x
 // 1D: stencil taps from the image sum, and Ghat from its Poisson-summation form
+// (ode != 0: of the collocation kernel -(phi'' + k0^2 phi) / (2 eps^2) instead of phi)
 az_status launch_taps_direct(int64_t L, double hL, double eps, int pimg, int W64, double* t64, int W32, float* t32,
-                             cudaStream_t st, float* th, float* tl);
-az_status launch_symbol_closed_1d(int64_t L, double a, double* Ghat, cudaStream_t st);
+                             cudaStream_t st, float* th, float* tl, int ode = 0, double k0 = 0.0);
+az_status launch_symbol_closed_1d(int64_t L, double a, double* Ghat, cudaStream_t st, int ode = 0, double hL = 0.0,
+                                  double k0 = 0.0, double eps = 1.0);
 // stencil taps t[m + W] = g(m mod L) for |m| <= W, FP64 and FP32 copies
 az_status launch_taps(const double* g, int64_t L, int W64, double* t64, int W32, float* t32, cudaStream_t st,
                       float* th = nullptr, float* tl = nullptr);

@@ -37,3 +37,23 @@ def test_host_side_errors_without_gpu():
     g = az.make_grid(1, (1 << 20,), (2,), (1.0,))
     st = az._lib.az_query_footprint(C.byref(g), 1 << 20, 0, C.byref(o), 64, C.byref(b))
     assert st == az.AZ_OK and b.value > (1 << 20) * 24 * 4
+
+
+def test_mixed_precision_refuses_small_eps_h():
+    # The mixed path's FP32 symbol inverse needs eps h >= 0.504; the tau0 =
+    # 1e-10 shape parameter of Eq. constant_shapeparam (eps h = 0.327) is
+    # refused before any device work (the mask pointer is never read).
+    import ctypes as C
+    import paper_2308_14490_gb300 as az
+    import workloads as W
+    n, T = 256, 1.5
+    epsh = W.epsh_from_tau0(1e-10)
+    g = az.make_grid(1, (n,), (2,), (T,))
+    o = az.make_options(az.AZ_MIXED, 64, 1e-8, 0.0, 1, 1)
+    h = C.c_void_p()
+    dummy = (C.c_uint8 * 4)()
+    eps = epsh / (2 * T / n)
+    st = az._lib.az_setup(C.byref(g), dummy, None, 0, C.c_double(eps), az.AZ_GAUSS, C.c_double(1.0),
+                          C.byref(o), None, C.byref(h))
+    assert st == az.AZ_ERR_ARG and not h.value
+    assert "AZ_FP64" in az.az_last_error()

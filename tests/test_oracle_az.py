@@ -21,10 +21,7 @@ def paper_value(key):
     raise KeyError(key)
 
 
-def epsh_from_tau0(tau0):
-    # Eq. constant_shapeparam: eps = c N, c = pi / (2 T sqrt(2 log(1 + tau0^-2)));
-    # with h = 2T/N this is eps*h = pi / sqrt(2 log(1 + tau0^-2)).
-    return math.pi / math.sqrt(2 * math.log(1 + tau0 ** -2))
+epsh_from_tau0 = W.epsh_from_tau0
 
 
 def test_config1_az_matches_direct_tsvd():
@@ -146,6 +143,25 @@ def test_helmholtz_az_matches_direct():
     xd, _ = direct_tsvd(op.A_dense(), b, 1e-8)
     r2, r1 = relres(op, x, b)[0], relres(op, xd, b)[0]
     assert abs(r2 - r1) <= 0.05 * r1 and r1 < 2e-3
+
+
+@pytest.mark.parametrize("n", [128, 512])
+def test_ode_az_error_and_direct(n):
+    # Example 6.1 with T = 1.5, s = 2, tau0 = 1e-10: the maximum error on
+    # [-1, 1] against the closed-form solution sin(n x / 5) is below 1e-8
+    # (Fig. d1_ode_nonper), and the AZ residual matches the direct TSVD's.
+    p = W.ode(n=n, k=64)
+    op = Operator(p.grid, p.mask, "poisson", p.boundary, p.weight, k0=p.k0)
+    b = np.concatenate([p.rhs() / (2 * op.eps ** 2), p.weight * p.boundary_rhs()])
+    x = AZ(op, p.k, 11, 1e-12).solve(b)
+    xd, _ = direct_tsvd(op.A_dense(), b, 1e-12)
+    assert relres(op, x, b)[0] < 1e-9 and relres(op, xd, b)[0] < 1e-9
+    gf = W.Grid(1, p.grid.n, (4,), p.grid.T, p.grid.epsh)
+    xf = W.grid_coords(gf, 0)
+    inside = (xf >= -1.0) & (xf <= 1.0)
+    opf = Operator(gf, np.ones(gf.Ltot, np.uint8))
+    for c in (x, xd):
+        assert np.abs(opf.Ac(c)[:, 0] - np.sin(p.k0 * xf))[inside].max() < 1e-8
 
 
 def test_refinement_keeps_relres():

@@ -89,6 +89,31 @@ def test_helmholtz_fft_forms_equal_dense():
     assert np.abs(opm.Zstar(y) - ref).max() <= 1e-11 * np.abs(ref).max()
 
 
+def test_dense_ode_rows_from_definition():
+    # Example 6.1: interior rows -(phi'' + k0^2 phi) / (2 eps^2); Dirichlet rows w phi at x = -1, 1.
+    g = W.Grid(1, (24,), (2,), (1.5,), 1.0)
+    k0 = 4.2
+    op = Operator(g, W.interval_mask(g, -1.0, 1.0), kind="poisson", boundary=np.array([[-1.0], [1.0]]),
+                  weight=10.0, k0=k0)
+    Ac = op.Ac_dense()
+    e = g.eps
+    for (i, j) in [(0, 0), (5, 3), (47, 23), (20, 11)]:
+        x = -1.5 + i * 3.0 / 48
+        c = -1.5 + j * 3.0 / 24
+        ref = -(_phi_per(x - c, e, 1.5, 2) + k0 ** 2 * _phi_per(x - c, e, 1.5)) / (2 * e * e)
+        assert abs(Ac[i, j] - ref) < 1e-13 * max(1.0, abs(ref))
+    A = op.A_dense()
+    for bi, xb in enumerate((-1.0, 1.0)):
+        for j in (0, 7, 23):
+            c = -1.5 + j * 3.0 / 24
+            assert abs(A[op.M + bi, j] - 10.0 * _phi_per(xb - c, e, 1.5)) < 1e-14
+    a = np.random.default_rng(8).standard_normal((g.N, 2))
+    assert np.abs(op.A(a) - A @ a).max() <= 1e-13 * np.abs(A @ a).max()
+    y = np.random.default_rng(9).standard_normal((op.M + op.Mb, 2))
+    ref = op.Zstar_dense() @ y
+    assert np.abs(op.Zstar(y) - ref).max() <= 1e-11 * np.abs(ref).max()
+
+
 def test_boundary_rows_from_definition():
     g = W.Grid(2, (8, 8), (2, 2), (1.0, 1.0), 1.0)
     pts = W.star_boundary(16)

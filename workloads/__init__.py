@@ -19,6 +19,8 @@ Readings of the paper that fix these inputs:
 from __future__ import annotations
 
 from dataclasses import dataclass, field
+import math
+
 import numpy as np
 
 SEED = 230814490
@@ -150,6 +152,26 @@ def config1() -> Problem:
     m = interval_mask(g, -0.5, 0.5)
     f = lambda p: np.exp(p[:, 0]) * np.cos(8 * p[:, 0])
     return Problem("1d-n256", g, m, 20, [f])
+
+
+def epsh_from_tau0(tau0: float) -> float:
+    """Shape parameter of Eq. constant_shapeparam: eps = c N with
+    c = pi / (2 T sqrt(2 log(1 + tau0^-2))); with h = 2T/N this is
+    eps h = pi / sqrt(2 log(1 + tau0^-2))."""
+    return math.pi / math.sqrt(2 * math.log(1 + tau0 ** -2))
+
+
+def ode(n: int = 256, T: float = 1.5, k: int = 64, k0: float | None = None, weight: float = 10.0,
+        tau0: float = 1e-10) -> Problem:
+    """1D ODE of Example 6.1: u'' + k0^2 u = 0 on [-1, 1], u(+-1) = sin(+-k0), solution
+    sin(k0 x) with k0 = n / 5 by default (the paper's choice), s = 2, T = 1.5 and the
+    shape parameter of Eq. constant_shapeparam at tau0 = 1e-10 (Fig. d1_ode_nonper)."""
+    k0 = n / 5.0 if k0 is None else float(k0)
+    g = Grid(1, (n,), (2,), (T,), epsh_from_tau0(tau0))
+    m = interval_mask(g, -1.0, 1.0)
+    u = lambda p: np.sin(k0 * p[:, 0])
+    f = lambda p: np.zeros(p.shape[0])
+    return Problem(f"1d-ode-n{n}", g, m, k, [f], np.array([[-1.0], [1.0]]), [u], weight, "poisson", [u], k0)
 
 
 def helmholtz(n: int = 16, nb: int = 64, k: int = 64, k0: float = 6.0, weight: float = 10.0) -> Problem:
