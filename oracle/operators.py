@@ -24,6 +24,16 @@ Paper passages followed:
   have O(1) entries; k0 = 0 is the Poisson operator), and Z* = [F B^dagger P E, 0]
   has zero columns for the boundary rows.
 
+* Sec. 6.3 (the flower-domain Helmholtz problem: du/dn = 0 on the outer
+  boundary, u = 0 on the inner one): a boundary point with a nonzero unit
+  normal n gives a Neumann row n . grad phi_j(p_b), the sum over dimensions
+  of n_d times the product of phi' in dimension d and phi in the others.
+
+Reading of the Neumann rows: the paper does not say how it scales them.  They
+are divided by eps (the derivative of phi is O(eps)), so that their entries
+are O(1) like the normalised interior rows, and then multiplied by the
+boundary weight like the Dirichlet rows; the data du/dn is scaled the same way.
+
 Reading of the symbol truncation: S_k^{-1} is replaced by 0 when
 S_k <= tau_sym^2 * max S (tau_sym = 0 gives the exact pseudo-inverse).
 """
@@ -35,7 +45,7 @@ from . import rbf
 class Operator:
     """A^c, A and Z* for one problem (approximation or Poisson collocation)."""
 
-    def __init__(self, grid, mask, kind="approx", boundary=None, weight=1.0, tau_sym=0.0, k0=0.0):
+    def __init__(self, grid, mask, kind="approx", boundary=None, weight=1.0, tau_sym=0.0, k0=0.0, normals=None):
         self.grid = grid
         self.dim = grid.dim
         self.n = tuple(int(v) for v in grid.n)
@@ -53,6 +63,10 @@ class Operator:
         self.boundary = None if boundary is None else np.asarray(boundary, dtype=np.float64)
         self.Mb = 0 if self.boundary is None else self.boundary.shape[0]
         self.weight = float(weight)
+        # (Mb, dim) outward unit normals; a zero row keeps the Dirichlet row
+        self.normals = None if normals is None else np.asarray(normals, dtype=np.float64).reshape(self.Mb, self.dim)
+        self.neumann = (np.zeros(self.Mb, bool) if self.normals is None
+                        else np.any(self.normals != 0.0, axis=1))
         self.G0 = rbf.grid_symbols(grid, 0)
         if kind == "poisson":
             self.G2 = rbf.grid_symbols(grid, 2)
@@ -102,16 +116,33 @@ class Operator:
         return v.reshape(self.Ltot, -1)
 
     def boundary_rows(self, a):
-        """w * A^b a: Dirichlet rows phi_j(p_b) at the boundary points (Sec. 6.1, 6.2)."""
+        """w * A^b a: Dirichlet rows phi_j(p_b) (Sec. 6.1, 6.2) and Neumann rows
+        n . grad phi_j(p_b) / eps (Sec. 6.3) at the boundary points."""
         a = np.asarray(a, dtype=np.float64)
+        F = self._boundary_factors()
         if self.dim == 1:
-            return self.weight * (self._boundary_factors()[0] @ a)
-        Bx, By = self._boundary_factors()
+            (B, dB), = F
+            out = B @ a
+            if self.neumann.any():
+                nb = self.neumann
+                out[nb] = (self.normals[nb, 0][:, None] * (dB[nb] @ a)) / self.eps
+            return self.weight * out
+        (Bx, dBx), (By, dBy) = F
         a2 = a.reshape(self.n[0], self.n[1], -1)
-        t = np.einsum("bi,ijc->bjc", Bx, a2)
-        return self.weight * np.einsum("bjc,bj->bc", t, By)
+
+        def sep(X, Y):
+            return np.einsum("bjc,bj->bc", np.einsum("bi,ijc->bjc", X, a2), Y)
+
+        out = sep(Bx, By)
+        if self.neumann.any():
+            nb = self.neumann
+            nx, ny = self.normals[nb, 0][:, None], self.normals[nb, 1][:, None]
+            out[nb] = (nx * sep(dBx[nb], By[nb]) + ny * sep(Bx[nb], dBy[nb])) / self.eps
+        return self.weight * out
 
     def _boundary_factors(self):
+        """Per dimension, phi_per and phi_per' between the boundary points and
+        the centers: two (Mb, n_d) arrays (Eq. periodic_rbf, image by image)."""
         out = []
         for d in range(self.dim):
             T = self.grid.T[d]
@@ -119,10 +150,38 @@ class Operator:
             P = rbf.image_count(self.eps, T)
             diff = self.boundary[:, d][:, None] - c[None, :]
             acc = np.zeros_like(diff)
+            dacc = np.zeros_like(diff)
             for p in range(-P, P + 1):
                 acc += rbf.phi(diff - 2.0 * p * T, self.eps)
-            out.append(acc)
+                dacc += rbf.dphi(diff - 2.0 * p * T, self.eps)
+            out.append((acc, dacc))
         return out
+
+    def collocation_rhs(self, f, g):
+        """b = [f / (2 eps^2); w g], the Neumann entries of g (du/dn) also divided
+        by eps: the row scalings above applied to the data (f: (M, c), g: (Mb, c))."""
+        g = self.weight * np.asarray(g, dtype=np.float64).copy()
+        g[self.neumann] /= self.eps
+        return np.concatenate([np.asarray(f, dtype=np.float64) / (2.0 * self.eps ** 2), g], axis=0)
+
+    def boundary_dense(self):
+        """The boundary block w * A^b as a dense (Mb, N) matrix, row by row."""
+        F = self._boundary_factors()
+        if self.dim == 1:
+            (B, dB), = F
+            Ab = B.copy()
+            nb = self.neumann
+            if nb.any():
+                Ab[nb] = self.normals[nb, 0][:, None] * dB[nb] / self.eps
+            return self.weight * Ab
+        (Bx, dBx), (By, dBy) = F
+        Ab = (Bx[:, :, None] * By[:, None, :]).reshape(self.Mb, -1)
+        nb = self.neumann
+        if nb.any():
+            nx, ny = self.normals[nb, 0][:, None, None], self.normals[nb, 1][:, None, None]
+            Ab[nb] = ((nx * dBx[nb][:, :, None] * By[nb][:, None, :] +
+                       ny * Bx[nb][:, :, None] * dBy[nb][:, None, :]) / self.eps).reshape(nb.sum(), -1)
+        return self.weight * Ab
 
     def A(self, a):
         """Rows of the least-squares matrix: kept grid rows, then boundary rows."""
@@ -176,12 +235,8 @@ class Operator:
 
     def A_dense(self):
         A = self.Ac_dense()[self.idx]
-        if self.Mb and self.dim == 1:
-            A = np.concatenate([A, self.weight * self._boundary_factors()[0]], axis=0)
-        elif self.Mb:
-            Bx, By = self._boundary_factors()
-            Ab = self.weight * (Bx[:, :, None] * By[:, None, :]).reshape(self.Mb, -1)
-            A = np.concatenate([A, Ab], axis=0)
+        if self.Mb:
+            A = np.concatenate([A, self.boundary_dense()], axis=0)
         return A
 
     def Zstar_dense(self, rcond=1e-14):

@@ -13,6 +13,9 @@ Paper passages:
   one real, even sequence  Ghat = DFT_L(g)  (unnormalised DFT); the paper's d_i
   are its entries regrouped by the permutation Pi.
 * Sec. 6.1 Example 6.1: phi''(r) = -2 eps^2 exp(-eps^2 r^2) (1 - 2 eps^2 r^2).
+* Sec. 6.3 (the flower-domain Helmholtz problem, du/dn = 0 on the outer
+  boundary): Neumann rows need the first derivative, the derivative of
+  Eq. (rbf): phi'(r) = -2 eps^2 r exp(-eps^2 r^2).
 
 Reading of the image sum (periodic_rbf is an infinite sum): it is truncated at
 |p| <= p_max with p_max chosen so that the first omitted image is below 1e-300
@@ -25,6 +28,12 @@ import numpy as np
 def phi(r, eps):
     """Gaussian RBF, Eq. (rbf)."""
     return np.exp(-(eps * r) ** 2)
+
+
+def dphi(r, eps):
+    """First derivative of the Gaussian RBF (for Neumann rows, Sec. 6.3)."""
+    e2 = eps * eps
+    return -2.0 * e2 * r * np.exp(-e2 * r * r)
 
 
 def d2phi(r, eps):

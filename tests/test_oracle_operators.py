@@ -190,3 +190,36 @@ def test_tau_sym_zeroes_small_groups():
     small = op0.S <= 1e-6 * op0.S.max()
     assert small.any()
     assert np.all(op1.Sinv[small] == 0) and np.all(op1.Sinv[~small] > 0)
+
+
+def _fd_neumann(op, pts, nrm, a, delta):
+    """n . grad u_a(p) / eps by central differences of Dirichlet rows at p +- delta n."""
+    plus = Operator(op.grid, op.mask, "poisson", pts + delta * nrm, op.weight, k0=op.k0)
+    minus = Operator(op.grid, op.mask, "poisson", pts - delta * nrm, op.weight, k0=op.k0)
+    return (plus.boundary_rows(a) - minus.boundary_rows(a)) / (2 * delta) / op.eps
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_neumann_rows_match_finite_differences(dim):
+    # Sec. 6.3: a Neumann row is n . grad of the expansion at the boundary point;
+    # central differences of the (independently pinned) Dirichlet rows along n.
+    rng = np.random.default_rng(5)
+    if dim == 1:
+        g = W.Grid(1, (32,), (2,), (1.5,), 0.6)
+        pts = np.array([[-1.0], [0.37], [1.0]])
+        nrm = np.array([[-1.0], [0.0], [1.0]])
+    else:
+        g = W.Grid(2, (12, 12), (2, 2), (1.0, 1.0), 0.8)
+        pts = W.star_boundary(9)
+        nrm = W.star_normals(9)
+        nrm[::3] = 0.0
+    mask = np.ones(g.Ltot, np.uint8)
+    op = Operator(g, mask, "poisson", pts, 10.0, normals=nrm)
+    a = rng.standard_normal((g.N, 3))
+    rows = op.boundary_rows(a)
+    assert np.allclose(op.boundary_dense() @ a, rows, rtol=0, atol=1e-13 * np.abs(rows).max())
+    nb = op.neumann
+    fd = _fd_neumann(op, pts[nb], nrm[nb], a, 1e-5 / op.eps)
+    assert np.abs(rows[nb] - fd).max() <= 1e-8 * np.abs(fd).max()
+    dir_only = Operator(g, mask, "poisson", pts, 10.0)
+    assert np.array_equal(rows[~nb], dir_only.boundary_rows(a)[~nb])

@@ -109,6 +109,18 @@ def star_boundary(nb=2048, r0=0.6, a=0.15, k=5) -> np.ndarray:
     return np.stack([r * np.cos(th), r * np.sin(th)], axis=1)
 
 
+def star_normals(nb=2048, r0=0.6, a=0.15, k=5) -> np.ndarray:
+    """Outward unit normals of the curve r(theta) = r0 + a cos(k theta) at the
+    points of ``star_boundary`` (the tangent rotated by -90 degrees)."""
+    th = 2.0 * np.pi * np.arange(nb) / nb
+    r = star_radius(th, r0, a, k)
+    dr = -a * k * np.sin(k * th)
+    tx = dr * np.cos(th) - r * np.sin(th)
+    ty = dr * np.sin(th) + r * np.cos(th)
+    nrm = np.hypot(tx, ty)
+    return np.stack([ty / nrm, -tx / nrm], axis=1)
+
+
 def kept_points(grid: Grid, mask: np.ndarray, refine: int = 1) -> np.ndarray:
     """Coordinates of the kept grid points in lexicographic (x-major) order: (M, dim)."""
     if grid.dim == 1:
@@ -135,15 +147,23 @@ class Problem:
     kind: str = "approx"                            # "approx" | "poisson"
     exact: list = field(default_factory=list)      # exact solutions (poisson)
     k0: float = 0.0                                 # Helmholtz wavenumber of the collocation operator
+    normals: np.ndarray | None = None               # (M_b, dim) outward unit normals; zero row = Dirichlet
+    nfuncs: list = field(default_factory=list)     # Neumann data du/dn(points, normals)
 
     def rhs(self) -> np.ndarray:
         pts = kept_points(self.grid, self.mask)
         return np.stack([f(pts) for f in self.funcs], axis=1)
 
     def boundary_rhs(self) -> np.ndarray | None:
+        """Boundary data: u on Dirichlet points, du/dn on Neumann points."""
         if self.boundary is None:
             return None
-        return np.stack([g(self.boundary) for g in self.bfuncs], axis=1)
+        out = np.stack([g(self.boundary) for g in self.bfuncs], axis=1)
+        if self.normals is not None:
+            nb = np.any(self.normals != 0.0, axis=1)
+            if nb.any():
+                out[nb] = np.stack([h(self.boundary[nb], self.normals[nb]) for h in self.nfuncs], axis=1)
+        return out
 
 
 def config1() -> Problem:
@@ -172,6 +192,63 @@ def ode(n: int = 256, T: float = 1.5, k: int = 64, k0: float | None = None, weig
     u = lambda p: np.sin(k0 * p[:, 0])
     f = lambda p: np.zeros(p.shape[0])
     return Problem(f"1d-ode-n{n}", g, m, k, [f], np.array([[-1.0], [1.0]]), [u], weight, "poisson", [u], k0)
+
+
+def ode_neumann(n: int = 256, T: float = 1.5, k: int = 64, weight: float = 10.0, tau0: float = 1e-10) -> Problem:
+    """Example 6.1 with a Neumann condition at the right end: u(-1) = sin(-k0),
+    u'(1) = k0 cos(k0); the solution is still sin(k0 x), k0 = n / 5."""
+    p = ode(n, T, k, None, weight, tau0)
+    k0 = p.k0
+    p.name = f"1d-ode-neumann-n{n}"
+    p.normals = np.array([[0.0], [1.0]])
+    p.nfuncs = [lambda q, nv: nv[:, 0] * k0 * np.cos(k0 * q[:, 0])]
+    return p
+
+
+def helmholtz_mixed_bc(n: int = 16, nb: int = 64, k: int = 600, k0: float = 6.0, weight: float = 10.0,
+                       epsh: float = 0.5) -> Problem:
+    """The Helmholtz problem on the star with Neumann data du/dn on every other
+    boundary point and Dirichlet data on the rest, u = sin(pi x)cos(pi y), at
+    eps h = 0.5 (where the collocation solution is accurate to ~1e-10 at n = 16;
+    at eps h = 1 the saturated residual leaves O(1) errors in u)."""
+    p = helmholtz(n, nb, k, k0, weight)
+    p.grid = Grid(2, (n, n), (2, 2), (1.0, 1.0), epsh)
+    p.name = f"2d-star-helmholtz-mixedbc-n{n}"
+    nrm = star_normals(nb)
+    nrm[1::2] = 0.0
+    p.normals = nrm
+    du = lambda q, nv: np.pi * (nv[:, 0] * np.cos(np.pi * q[:, 0]) * np.cos(np.pi * q[:, 1])
+                                - nv[:, 1] * np.sin(np.pi * q[:, 0]) * np.sin(np.pi * q[:, 1]))
+    p.nfuncs = [du]
+    return p
+
+
+def flower(n: int = 128, n_outer: int = 200, n_inner: int = 100, k: int = 1024, weight: float = 10.0,
+           r0: float = 0.68, a: float = 0.2, petals: int = 5, hole: float = 0.1) -> Problem:
+    """Stand-in for the flower-domain problem of Sec. 6.3: lap u + 4 u =
+    exp(-4((x+0.3)^2 + y^2)^2) on a flower r <= r0 + a cos(5 theta) with a disc
+    of diameter 0.2 removed, du/dn = 0 on the outer boundary (200 points),
+    u = 0 on the inner one (100 points), [-1,1]^2, s = 2, eps = 1/h.  The
+    paper does not give the flower's shape: r0 and a are chosen so that at
+    100 x 100 centers the kept grid has about the paper's 14771 points, and the
+    hole is centered at the origin.  In the operator's sign, -(lap + k0^2) u = f
+    with k0 = 2 and f = -exp(...)."""
+    g = Grid(2, (n, n), (2, 2), (1.0, 1.0), 1.0)
+    X, Y = _mesh(g)
+    r = np.sqrt(X * X + Y * Y)
+    th = np.arctan2(Y, X)
+    m = ((r <= star_radius(th, r0, a, petals)) & (r > hole)).astype(np.uint8)
+    outer = star_boundary(n_outer, r0, a, petals)
+    ti = 2.0 * np.pi * np.arange(n_inner) / n_inner
+    inner = np.stack([hole * np.cos(ti), hole * np.sin(ti)], axis=1)
+    bpts = np.concatenate([outer, inner], axis=0)
+    nrm = np.concatenate([star_normals(n_outer, r0, a, petals), np.zeros((n_inner, 2))], axis=0)
+    f = lambda q: -np.exp(-4.0 * ((q[:, 0] + 0.3) ** 2 + q[:, 1] ** 2) ** 2)
+    zero = lambda q: np.zeros(q.shape[0])
+    p = Problem(f"2d-flower-n{n}", g, m, k, [f], bpts, [zero], weight, "poisson", [], 2.0)
+    p.normals = nrm
+    p.nfuncs = [lambda q, nv: np.zeros(q.shape[0])]
+    return p
 
 
 def helmholtz(n: int = 16, nb: int = 64, k: int = 64, k0: float = 6.0, weight: float = 10.0) -> Problem:
