@@ -69,7 +69,9 @@ typedef struct {
   int32_t precision;    /* AZ_FP64, or AZ_MIXED: FP32 transforms/sketch, FP64 factor work and residual */
   int32_t k;            /* sketch width r + p (number of random columns, Sec. 3.2.3), 1..4096; 0 = adaptive:
                            widths 64, 128, ... until the k-th singular value of the sketch is below
-                           1e-7 (FP64) or 1e-4 (mixed) of the largest (az_get_info reports the k used) */
+                           1e-7 (FP64) or 1e-4 (mixed) of the largest (az_get_info reports the k used).
+                           A width above M + n_boundary (the number of rows of the sketch) is reduced
+                           to it; the first columns of R are kept */
   double tau_svd;       /* relative truncation of the low-rank solve (0 = default: 1e-8).  The narrow
                            (k <= 64) factorisation works on the Gram matrix and resolves singular values
                            down to about 1e-8 of the largest, so in AZ_FP64 a tau_svd below 1e-8 takes the
@@ -80,6 +82,11 @@ typedef struct {
   double k0;            /* collocation (AZ_NEG_LAPLACE_GAUSS) only: wavenumber of the Helmholtz operator
                            -(Laplacian + k0^2) of Sec. 6.2 (0 = Poisson); the interior rows are
                            -(Laplacian + k0^2) phi_j / (2 eps^2) */
+  const double* bnormal; /* collocation only: device array, n_boundary x dim (the layout of the boundary
+                           points), or NULL.  A point with a nonzero (unit, outward) normal n gets the
+                           Neumann row n . grad phi_j(p) / eps (Sec. 6.3), the others the Dirichlet row
+                           phi_j(p); both are multiplied by the boundary weight.  az_collocate scales the
+                           Neumann data du/dn by weight / eps.  Copied at setup; NULL = all Dirichlet */
 } az_options;
 
 typedef struct {

@@ -31,7 +31,7 @@ class az_grid(ctypes.Structure):
 class az_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("k", ctypes.c_int32), ("tau_svd", ctypes.c_double),
                 ("tau_sym", ctypes.c_double), ("seed", ctypes.c_uint64), ("refine_steps", ctypes.c_int32),
-                ("k0", ctypes.c_double)]
+                ("k0", ctypes.c_double), ("bnormal", ctypes.c_void_p)]
 
 
 class az_info_t(ctypes.Structure):
@@ -115,10 +115,19 @@ def make_options(precision=AZ_MIXED, k=24, tau_svd=0.0, tau_sym=0.0, seed=1, ref
     return o
 
 
-def az_setup(grid, mask, eps, kernel=AZ_GAUSS, boundary=None, boundary_weight=1.0, options=None, stream=None):
-    """mask: uint8 CUDA tensor (grid points); boundary: (Mb, 2) float64 CUDA tensor or None."""
+def az_setup(grid, mask, eps, kernel=AZ_GAUSS, boundary=None, boundary_weight=1.0, options=None, stream=None,
+             normals=None):
+    """mask: uint8 CUDA tensor (grid points); boundary: (Mb, dim) float64 CUDA tensor or None;
+    normals: (Mb, dim) float64 CUDA tensor (nonzero rows: Neumann points) or None."""
     h = ctypes.c_void_p()
     nb = 0 if boundary is None else int(boundary.shape[0])
+    if normals is not None:
+        if options is None:
+            options = make_options()
+        o = az_options()
+        ctypes.pointer(o)[0] = options
+        o.bnormal = normals.data_ptr()
+        options = o
     _check(_lib.az_setup(ctypes.byref(grid), _ptr(mask), _ptr(boundary), nb, float(eps), int(kernel),
                          float(boundary_weight), ctypes.byref(options) if options is not None else None,
                          _stream(stream), ctypes.byref(h)), "az_setup")

@@ -37,6 +37,7 @@ struct az_setup_t {
   int32_t* pos2m = nullptr;
   int32_t* idx = nullptr;
   double* bpts = nullptr;
+  double* bnrm = nullptr;   // Mb x dim outward normals (null: all Dirichlet)
   double* Ghat = nullptr;
   double* S = nullptr;
   double* H64 = nullptr;
@@ -126,16 +127,13 @@ int ilog2(int64_t v) { int l = 0; while ((int64_t(1) << l) < v) ++l; return l; }
 // delta * g(0): the Gaussian exp(-(eps m h_L)^2) decays below delta past
 // m = sqrt(ln(1/delta)) / (eps h_L); for phi'' the polynomial factor is covered by
 // two extra points.
+// A width that reaches half the period stops at W = Ld/2: the window then
+// covers the whole period, and the taps at m = +-Ld/2 (one grid offset seen
+// from both ends) carry half the sample each.
 int stencil_halfwidth(double eps, double hL, double delta, int64_t Ld, bool deriv) {
   int W = (int)std::ceil(std::sqrt(std::log(1.0 / delta)) / (eps * hL)) + (deriv ? 2 : 0);
-  int64_t lim = (Ld - 1) / 2;
+  int64_t lim = Ld / 2;
   return (int)std::min<int64_t>(W, lim);
-}
-
-int image_count(double eps, double T) {
-  int p = 1;
-  while ((eps * (2 * p - 1) * T) * (eps * (2 * p - 1) * T) < 700.0) ++p;
-  return p + 1;
 }
 
 az_status make_geom(const az_grid* gr, Geom& g) {
@@ -379,7 +377,7 @@ az_status apply_rows(az_setup_t* h, const TZ* z, int64_t ldz, const TB* b, int64
   AZ_TRY((launch_stencil_rows<T, TZ, TB, TO>(h->g, h->kind, h->eps, h->idx, h->M, tp, z, ldz, b, ldb, alpha, beta,
                                              out, ldo, ncols, st)));
   if (h->Mb) {
-    AZ_TRY((launch_boundary_rows<T, TZ, TB, TO>(h->g, h->eps, h->bweight, h->bpts, h->Mb, z, ldz,
+    AZ_TRY((launch_boundary_rows<T, TZ, TB, TO>(h->g, h->eps, h->bweight, h->bpts, h->bnrm, h->Mb, z, ldz,
                                                 b ? b + h->M : nullptr, ldb, alpha, beta, out + h->M, ldo, ncols, st)));
   }
   return AZ_OK;
@@ -507,7 +505,7 @@ az_status solve_impl(az_setup_t* h, const double* b, int64_t ldb, int64_t nrhs, 
         AZ_TRY(launch_resid_df(h->g, h->kind, h->eps, h->idx, h->M, th, tl, h->W64[0], h->W64[1], x1f,
                                h->g.N, bc, ldb, (float*)res, h->Mtot, nc, st));
         if (h->Mb) {
-          AZ_TRY((launch_boundary_rows<double, double, double, T>(h->g, h->eps, h->bweight, h->bpts, h->Mb, xc, ldx,
+          AZ_TRY((launch_boundary_rows<double, double, double, T>(h->g, h->eps, h->bweight, h->bpts, h->bnrm, h->Mb, xc, ldx,
                                                                   bc + h->M, ldb, 1.0, -1.0, res + h->M, h->Mtot, nc, st)));
         }
       } else {
@@ -677,7 +675,7 @@ static az_status setup_fixed(const az_grid* gr, const uint8_t* mask, const doubl
   if (n_boundary < 0 || (n_boundary > 0 && !bpts)) { set_error("az_setup: boundary points"); return AZ_ERR_ARG; }
   az_options o;
   if (opt) o = *opt;
-  else { o.precision = AZ_MIXED; o.k = 24; o.tau_svd = 0; o.tau_sym = 0; o.seed = 1; o.refine_steps = -1; o.k0 = 0; }
+  else { o.precision = AZ_MIXED; o.k = 24; o.tau_svd = 0; o.tau_sym = 0; o.seed = 1; o.refine_steps = -1; o.k0 = 0; o.bnormal = nullptr; }
   if (!std::isfinite(o.k0)) { set_error("az_setup: k0 must be finite"); return AZ_ERR_ARG; }
   if (o.precision != AZ_FP64 && o.precision != AZ_MIXED) { set_error("az_setup: precision"); return AZ_ERR_ARG; }
   if (o.k < 1 || o.k > 4096) { set_error("az_setup: k must be in [1, 4096]"); return AZ_ERR_ARG; }
@@ -719,6 +717,9 @@ static az_status setup_fixed(const az_grid* gr, const uint8_t* mask, const doubl
     h->Mtot = M + h->Mb;
     h->ldm = (h->Mtot + 31) / 32 * 32;
     if (h->Mtot < 1) { set_error("az_setup: Omega contains no grid point"); rc = AZ_ERR_ARG; break; }
+    // Y = A W (Mtot x k) has rank <= Mtot: a wider sketch adds no direction,
+    // and the Householder route needs k <= Mtot; the first columns of R are kept
+    h->k = (int)std::min<int64_t>(h->k, h->Mtot);
     if (M > 0) {
       // kept points forming one run of consecutive grid indices (a 1D
       // interval): the gather then needs no index-map lookups
@@ -732,6 +733,10 @@ static az_status setup_fixed(const az_grid* gr, const uint8_t* mask, const doubl
     if (h->Mb) {
       rc = dalloc_t(h, &h->bpts, (size_t)g.dim * h->Mb); if (rc) break;   // Mb x dim
       if (cudaMemcpyAsync(h->bpts, bpts, (size_t)g.dim * h->Mb * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess) { rc = AZ_ERR_CUDA; break; }
+      if (o.bnormal) {
+        rc = dalloc_t(h, &h->bnrm, (size_t)g.dim * h->Mb); if (rc) break;
+        if (cudaMemcpyAsync(h->bnrm, o.bnormal, (size_t)g.dim * h->Mb * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess) { rc = AZ_ERR_CUDA; break; }
+      }
     }
     // twiddle tables (host-built constants)
     {
@@ -828,7 +833,7 @@ az_status az_collocate(az_handle h, const double* f, int64_t ldf, const double* 
   double* b;
   AZ_CUDA(cudaMalloc((void**)&b, (size_t)h->Mtot * nrhs * sizeof(double)));
   az_status rc = launch_scale_rows(f, ldf, h->M, (int)nrhs, 1.0 / (2.0 * h->eps * h->eps), b, h->Mtot, st);
-  if (rc == AZ_OK) rc = launch_scale_rows(gb, ldg, h->Mb, (int)nrhs, h->bweight, b + h->M, h->Mtot, st);
+  if (rc == AZ_OK) rc = launch_boundary_rhs(h->g.dim, gb, ldg, h->Mb, (int)nrhs, h->bnrm, h->bweight, h->eps, b + h->M, h->Mtot, st);
   if (rc == AZ_OK) rc = az_solve(h, b, h->Mtot, nrhs, x, ldx, stream, relres);
   cudaStreamSynchronize(st);
   cudaFree(b);

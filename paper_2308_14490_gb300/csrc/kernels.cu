@@ -11,6 +11,12 @@
 
 namespace az {
 
+int image_count(double eps, double T) {
+  int p = 1;
+  while ((eps * (2 * p - 1) * T) * (eps * (2 * p - 1) * T) < 700.0) ++p;
+  return p + 1;
+}
+
 static constexpr int TW_N = 4096;  // master twiddle table length
 static inline size_t padix_host(size_t e, int sh) { return e + (e >> sh); }
 
@@ -168,14 +174,20 @@ az_status launch_samples(double* g, int64_t L, double hL, double eps, int deriv,
   AZ_LAUNCH_CHECK();
   return AZ_OK;
 }
+// a window of half-width L/2 sees offset L/2 from both ends: half the sample each
+__device__ __forceinline__ double edge_half(int64_t m, int64_t L) { return 2 * (m < 0 ? -m : m) == L ? 0.5 : 1.0; }
 __global__ void k_taps(const double* g, int64_t L, int W64, double* t64, int W32, float* t32, float* th, float* tl) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i <= 2 * W64) {
-    const double v = g[fmod_pos((int64_t)i - W64, L)];
+    const int64_t m = (int64_t)i - W64;
+    const double v = g[fmod_pos(m, L)] * edge_half(m, L);
     t64[i] = v;
     if (th) { const float h = (float)v; th[i] = h; tl[i] = (float)(v - (double)h); }
   }
-  if (i <= 2 * W32) t32[i] = (float)g[fmod_pos((int64_t)i - W32, L)];
+  if (i <= 2 * W32) {
+    const int64_t m = (int64_t)i - W32;
+    t32[i] = (float)(g[fmod_pos(m, L)] * edge_half(m, L));
+  }
 }
 // Taps straight from the image sum (1D: the L samples themselves are not needed)
 // (ode != 0: taps of the collocation kernel -(phi'' + k0^2 phi) / (2 eps^2), Example 6.1)
@@ -189,11 +201,15 @@ __global__ void k_taps_direct(int64_t L, double hL, double eps, int pimg, int W6
                               float* th, float* tl, int ode, double k0) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i <= 2 * W64) {
-    const double v = tap_value((int64_t)i - W64, L, hL, eps, pimg, ode, k0);
+    const int64_t m = (int64_t)i - W64;
+    const double v = tap_value(m, L, hL, eps, pimg, ode, k0) * edge_half(m, L);
     t64[i] = v;
     if (th) { const float h = (float)v; th[i] = h; tl[i] = (float)(v - (double)h); }
   }
-  if (i <= 2 * W32) t32[i] = (float)tap_value((int64_t)i - W32, L, hL, eps, pimg, ode, k0);
+  if (i <= 2 * W32) {
+    const int64_t m = (int64_t)i - W32;
+    t32[i] = (float)(tap_value(m, L, hL, eps, pimg, ode, k0) * edge_half(m, L));
+  }
 }
 az_status launch_taps_direct(int64_t L, double hL, double eps, int pimg, int W64, double* t64, int W32, float* t32,
                              cudaStream_t st, float* th, float* tl, int ode, double k0) {
@@ -906,68 +922,136 @@ az_status launch_resid_df(const Geom& g, int kind, double eps, const int32_t* id
   return AZ_OK;
 }
 
-// phi_per at distance d (center window handles the images): plain Gaussian here
+// phi_per at distance d (center window handles the images): plain Gaussian
+// and its first derivative, -2 eps^2 d exp(-eps^2 d^2)
 template <typename T> __device__ __forceinline__ T gauss(T d, T eps) { T e = eps * d; return exp(-e * e); }
+template <typename T> __device__ __forceinline__ T dgauss(T d, T eps) {
+  T e = eps * d;
+  return (T)-2 * eps * e * exp(-e * e);
+}
 
+// Centers within reach of a point, per dimension: the 2 Wc + 2 nearest ones,
+// one image each, while the Gaussian falls below exp(-42) inside that window;
+// otherwise (small grids, wide kernels) all n_d centers, each with its image
+// sum |p| <= P (Eq. periodic_rbf).
+struct CenterWin { int W[2]; int P[2]; };
+static CenterWin center_window(const Geom& g, double eps) {
+  CenterWin cw{};
+  for (int d = 0; d < g.dim; ++d) {
+    const double h = 2.0 * g.T[d] / (double)g.n[d];
+    const int64_t need = (int64_t)std::ceil(std::sqrt(42.0) / (eps * h)) + 1;
+    if (2 * need + 2 <= g.n[d]) { cw.W[d] = (int)need; cw.P[d] = 0; }
+    else { cw.W[d] = (int)(g.n[d] / 2 - 1); cw.P[d] = image_count(eps, g.T[d]); }
+  }
+  return cw;
+}
+template <typename T> __device__ __forceinline__ T gauss_per(T d, T eps, T twoT, int P) {
+  T a = gauss<T>(d, eps);
+  for (int p = 1; p <= P; ++p) a += gauss<T>(d - (T)p * twoT, eps) + gauss<T>(d + (T)p * twoT, eps);
+  return a;
+}
+template <typename T> __device__ __forceinline__ T dgauss_per(T d, T eps, T twoT, int P) {
+  T a = dgauss<T>(d, eps);
+  for (int p = 1; p <= P; ++p) a += dgauss<T>(d - (T)p * twoT, eps) + dgauss<T>(d + (T)p * twoT, eps);
+  return a;
+}
+
+// Boundary rows (Sec. 6.1, 6.2, 6.3): out = alpha b + beta w A^b z.  A point
+// with a nonzero normal n (nrm, Mb x dim, may be null) gives the Neumann row
+// n . grad phi_j(p) / eps; the others the Dirichlet row phi_j(p).
 template <typename T, typename TZ, typename TB, typename TO>
-__global__ void k_boundary_rows(Geom g, T eps, T w, int Wc, const double* __restrict__ pts, int64_t Mb,
+__global__ void k_boundary_rows(Geom g, T eps, T w, CenterWin cw, const double* __restrict__ pts,
+                                const double* __restrict__ nrm, int64_t Mb,
                                 const TZ* __restrict__ zb, int64_t ldz, const TB* __restrict__ bb, int64_t ldb,
                                 T alpha, T beta, TO* __restrict__ outb, int64_t ldo) {
   int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= Mb) return;
   const int c = blockIdx.y;
   const TZ* z = zb + (int64_t)c * ldz;
+  const T ieps = (T)1 / eps;
   if (g.dim == 1) {
-    // Dirichlet row of the ODE (Example 6.1): w sum_j phi_per(p - c_j) z_j
     const double px = pts[m], hx = 2.0 * g.T[0] / g.n[0];
+    const T nx = nrm ? (T)nrm[m] : (T)0, tx = (T)(2.0 * g.T[0]);
+    const int Wc = cw.W[0], P = cw.P[0];
     const int64_t cxi = (int64_t)floor((px + g.T[0]) / hx);
     T acc = 0;
-    for (int64_t jx = cxi - Wc; jx <= cxi + Wc + 1; ++jx)
-      acc += gauss<T>((T)(px - (-g.T[0] + (double)jx * hx)), eps) * (T)z[fmod_pos(jx, g.n[0])];
+    if (nx != (T)0) {
+      for (int64_t jx = cxi - Wc; jx <= cxi + Wc + 1; ++jx)
+        acc += dgauss_per<T>((T)(px - (-g.T[0] + (double)jx * hx)), eps, tx, P) * (T)z[fmod_pos(jx, g.n[0])];
+      acc *= nx * ieps;
+    } else {
+      for (int64_t jx = cxi - Wc; jx <= cxi + Wc + 1; ++jx)
+        acc += gauss_per<T>((T)(px - (-g.T[0] + (double)jx * hx)), eps, tx, P) * (T)z[fmod_pos(jx, g.n[0])];
+    }
     T r = beta * w * acc;
     if (bb) r += alpha * (T)bb[(int64_t)c * ldb + m];
     outb[(int64_t)c * ldo + m] = (TO)r;
     return;
   }
   const double px = pts[2 * m], py = pts[2 * m + 1];
+  const T nx = nrm ? (T)nrm[2 * m] : (T)0, ny = nrm ? (T)nrm[2 * m + 1] : (T)0;
+  const bool neu = nx != (T)0 || ny != (T)0;
   const double hx = 2.0 * g.T[0] / g.n[0], hy = 2.0 * g.T[1] / g.n[1];
+  const T tx = (T)(2.0 * g.T[0]), ty = (T)(2.0 * g.T[1]);
   const int64_t cxi = (int64_t)floor((px + g.T[0]) / hx), cyi = (int64_t)floor((py + g.T[1]) / hy);
   T acc = 0;
-  for (int64_t jx = cxi - Wc; jx <= cxi + Wc + 1; ++jx) {
-    T wx = gauss<T>((T)(px - (-g.T[0] + (double)jx * hx)), eps);
+  for (int64_t jx = cxi - cw.W[0]; jx <= cxi + cw.W[0] + 1; ++jx) {
+    const T dx = (T)(px - (-g.T[0] + (double)jx * hx));
+    const T wx = gauss_per<T>(dx, eps, tx, cw.P[0]);
     const TZ* zr = z + fmod_pos(jx, g.n[0]) * g.n[1];
-    T a = 0;
-    for (int64_t jy = cyi - Wc; jy <= cyi + Wc + 1; ++jy) {
-      T wy = gauss<T>((T)(py - (-g.T[1] + (double)jy * hy)), eps);
-      a += wy * (T)zr[fmod_pos(jy, g.n[1])];
+    T a0 = 0, a1 = 0;
+    for (int64_t jy = cyi - cw.W[1]; jy <= cyi + cw.W[1] + 1; ++jy) {
+      const T dy = (T)(py - (-g.T[1] + (double)jy * hy));
+      const T zv = (T)zr[fmod_pos(jy, g.n[1])];
+      a0 += gauss_per<T>(dy, eps, ty, cw.P[1]) * zv;
+      if (neu) a1 += dgauss_per<T>(dy, eps, ty, cw.P[1]) * zv;
     }
-    acc += wx * a;
+    if (neu) acc += nx * dgauss_per<T>(dx, eps, tx, cw.P[0]) * a0 + ny * wx * a1;
+    else acc += wx * a0;
   }
+  if (neu) acc *= ieps;
   T r = beta * w * acc;
   if (bb) r += alpha * (T)bb[(int64_t)c * ldb + m];
   outb[(int64_t)c * ldo + m] = (TO)r;
 }
-static int center_window(const Geom& g, double eps) {
-  double h = 2.0 * g.T[0] / (double)g.n[0];
-  int Wc = (int)std::ceil(std::sqrt(42.0) / (eps * h)) + 1;
-  int lim = (int)(g.dim == 1 ? g.n[0] : std::min<int64_t>(g.n[0], g.n[1])) / 2 - 1;
-  return std::max(0, std::min(Wc, lim));
-}
 template <typename T, typename TZ, typename TB, typename TO>
-az_status launch_boundary_rows(const Geom& g, double eps, double w, const double* pts, int64_t Mb,
+az_status launch_boundary_rows(const Geom& g, double eps, double w, const double* pts, const double* nrm, int64_t Mb,
                                const TZ* z, int64_t ldz, const TB* b, int64_t ldb, T alpha, T beta,
                                TO* out, int64_t ldo, int ncols, cudaStream_t st) {
   if (Mb == 0 || ncols == 0) return AZ_OK;
   dim3 grid((unsigned)((Mb + 127) / 128), ncols);
   ProfScope ps("boundary_rows", (double)Mb * ncols * ((b ? sizeof(TB) : 0) + sizeof(TO)) + 16.0 * Mb, st);
-  k_boundary_rows<T, TZ, TB, TO><<<grid, 128, 0, st>>>(g, (T)eps, (T)w, center_window(g, eps), pts, Mb, z, ldz, b,
-                                                       ldb, alpha, beta, out, ldo);
+  k_boundary_rows<T, TZ, TB, TO><<<grid, 128, 0, st>>>(g, (T)eps, (T)w, center_window(g, eps), pts, nrm, Mb, z, ldz,
+                                                       b, ldb, alpha, beta, out, ldo);
+  AZ_LAUNCH_CHECK();
+  return AZ_OK;
+}
+
+// Boundary data of a collocation solve: out = w g on Dirichlet points and
+// w g / eps on Neumann points (the row scalings of k_boundary_rows).
+__global__ void k_boundary_rhs(int dim, const double* __restrict__ g, int64_t ldg, int64_t Mb,
+                               const double* __restrict__ nrm, double w, double w_eps, double* __restrict__ out,
+                               int64_t ldo) {
+  const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= Mb) return;
+  const int c = blockIdx.y;
+  bool neu = false;
+  if (nrm)
+    for (int d = 0; d < dim; ++d) neu |= nrm[(int64_t)dim * m + d] != 0.0;
+  out[(int64_t)c * ldo + m] = (neu ? w_eps : w) * g[(int64_t)c * ldg + m];
+}
+az_status launch_boundary_rhs(int dim, const double* g, int64_t ldg, int64_t Mb, int ncols, const double* nrm,
+                              double w, double eps, double* out, int64_t ldo, cudaStream_t st) {
+  if (Mb == 0 || ncols == 0) return AZ_OK;
+  dim3 grid((unsigned)((Mb + 127) / 128), ncols);
+  ProfScope ps("boundary_rhs", 16.0 * Mb * ncols, st);
+  k_boundary_rhs<<<grid, 128, 0, st>>>(dim, g, ldg, Mb, nrm, w, w / eps, out, ldo);
   AZ_LAUNCH_CHECK();
   return AZ_OK;
 }
 
 // Evaluation on the s_test-refined box grid (FP64)
-__global__ void k_evaluate(Geom g, double eps, int st_, int Wc, const double* __restrict__ xb, int64_t ldx,
+__global__ void k_evaluate(Geom g, double eps, int st_, CenterWin cw, const double* __restrict__ xb, int64_t ldx,
                            double* __restrict__ outb, int64_t ldo, int64_t npts) {
   int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= npts) return;
@@ -976,21 +1060,24 @@ __global__ void k_evaluate(Geom g, double eps, int st_, int Wc, const double* __
   double acc = 0;
   if (g.dim == 1) {
     const int64_t Lt = g.n[0] * st_;
-    const double h = 2.0 * g.T[0] / g.n[0];
+    const double h = 2.0 * g.T[0] / g.n[0], tx = 2.0 * g.T[0];
     const double px = -g.T[0] + (double)q * (2.0 * g.T[0] / (double)Lt);
     const int64_t ci = (int64_t)floor((px + g.T[0]) / h);
-    for (int64_t j = ci - Wc; j <= ci + Wc + 1; ++j) acc += gauss<double>(px - (-g.T[0] + (double)j * h), eps) * x[fmod_pos(j, g.n[0])];
+    for (int64_t j = ci - cw.W[0]; j <= ci + cw.W[0] + 1; ++j)
+      acc += gauss_per<double>(px - (-g.T[0] + (double)j * h), eps, tx, cw.P[0]) * x[fmod_pos(j, g.n[0])];
   } else {
     const int64_t Lty = g.n[1] * st_;
     const int64_t ix = q / Lty, iy = q % Lty;
     const double hx = 2.0 * g.T[0] / g.n[0], hy = 2.0 * g.T[1] / g.n[1];
+    const double tx = 2.0 * g.T[0], ty = 2.0 * g.T[1];
     const double px = -g.T[0] + (double)ix * hx / st_, py = -g.T[1] + (double)iy * hy / st_;
     const int64_t cxi = (int64_t)floor((px + g.T[0]) / hx), cyi = (int64_t)floor((py + g.T[1]) / hy);
-    for (int64_t jx = cxi - Wc; jx <= cxi + Wc + 1; ++jx) {
-      double wx = gauss<double>(px - (-g.T[0] + (double)jx * hx), eps);
+    for (int64_t jx = cxi - cw.W[0]; jx <= cxi + cw.W[0] + 1; ++jx) {
+      double wx = gauss_per<double>(px - (-g.T[0] + (double)jx * hx), eps, tx, cw.P[0]);
       const double* zr = x + fmod_pos(jx, g.n[0]) * g.n[1];
       double a = 0;
-      for (int64_t jy = cyi - Wc; jy <= cyi + Wc + 1; ++jy) a += gauss<double>(py - (-g.T[1] + (double)jy * hy), eps) * zr[fmod_pos(jy, g.n[1])];
+      for (int64_t jy = cyi - cw.W[1]; jy <= cyi + cw.W[1] + 1; ++jy)
+        a += gauss_per<double>(py - (-g.T[1] + (double)jy * hy), eps, ty, cw.P[1]) * zr[fmod_pos(jy, g.n[1])];
       acc += wx * a;
     }
   }
@@ -999,16 +1086,9 @@ __global__ void k_evaluate(Geom g, double eps, int st_, int Wc, const double* __
 az_status launch_evaluate(const Geom& g, double eps, int s_test, const double* x, int64_t ldx, int nrhs,
                           double* out, int64_t ldo, cudaStream_t st) {
   int64_t npts = g.dim == 1 ? g.n[0] * s_test : g.n[0] * s_test * g.n[1] * s_test;
-  int Wc;
-  {
-    double h = 2.0 * g.T[0] / (double)g.n[0];
-    Wc = (int)std::ceil(std::sqrt(42.0) / (eps * h)) + 1;
-    int64_t lim = (g.dim == 1 ? g.n[0] : std::min(g.n[0], g.n[1])) / 2 - 1;
-    Wc = (int)std::max<int64_t>(0, std::min<int64_t>(Wc, lim));
-  }
   dim3 grid((unsigned)((npts + 255) / 256), nrhs);
   ProfScope ps("evaluate", 8.0 * npts * nrhs + 8.0 * g.N * nrhs, st);
-  k_evaluate<<<grid, 256, 0, st>>>(g, eps, s_test, Wc, x, ldx, out, ldo, npts);
+  k_evaluate<<<grid, 256, 0, st>>>(g, eps, s_test, center_window(g, eps), x, ldx, out, ldo, npts);
   AZ_LAUNCH_CHECK();
   return AZ_OK;
 }
@@ -1630,6 +1710,7 @@ INST_R(double)
                                                         const StencilTaps&, const TZ*, int64_t, const TB*,  \
                                                         int64_t, T, T, TO*, int64_t, int, cudaStream_t);     \
   template az_status launch_boundary_rows<T, TZ, TB, TO>(const Geom&, double, double, const double*,        \
+                                                         const double*,                                     \
                                                          int64_t, const TZ*, int64_t, const TB*, int64_t, T, \
                                                          T, TO*, int64_t, int, cudaStream_t);
 INST_ST(float, float, double, float)

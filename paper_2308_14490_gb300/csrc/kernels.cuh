@@ -4,6 +4,10 @@
 
 namespace az {
 
+// Images |p| <= P of Eq. periodic_rbf needed in a box of half-width T: the
+// first omitted image is below exp(-700) of the peak everywhere in the box.
+int image_count(double eps, double T);
+
 // S1: compact index map of the kept grid points.  pos2m[L] (-1 if not kept),
 // idx[M]; the count M is written to *M_dev.
 az_status launch_compact(const uint8_t* mask, int64_t L, int32_t* pos2m, int32_t* idx, int64_t* M_dev,
@@ -77,11 +81,16 @@ template <typename T, typename TZ, typename TB, typename TO>
 az_status launch_stencil_rows(const Geom& g, int kind, double eps, const int32_t* idx, int64_t M,
                               const StencilTaps& tp, const TZ* z, int64_t ldz, const TB* b, int64_t ldb,
                               T alpha, T beta, TO* out, int64_t ldo, int ncols, cudaStream_t st);
-// Boundary rows: out[m,c] = alpha*b[m,c] + beta*w*sum_j phi_j(p_m) z[j,c], m < Mb
+// Boundary rows: out[m,c] = alpha*b[m,c] + beta*w*sum_j r_j(p_m) z[j,c], m < Mb, with
+// r_j = phi_j (Dirichlet) or n_m . grad phi_j / eps where the normal n_m (nrm, Mb x dim,
+// may be null) is nonzero (Neumann)
 template <typename T, typename TZ, typename TB, typename TO>
-az_status launch_boundary_rows(const Geom& g, double eps, double w, const double* pts, int64_t Mb,
+az_status launch_boundary_rows(const Geom& g, double eps, double w, const double* pts, const double* nrm, int64_t Mb,
                                const TZ* z, int64_t ldz, const TB* b, int64_t ldb, T alpha, T beta,
                                TO* out, int64_t ldo, int ncols, cudaStream_t st);
+// Boundary data: out = w g (Dirichlet points), w g / eps (Neumann points)
+az_status launch_boundary_rhs(int dim, const double* g, int64_t ldg, int64_t Mb, int ncols, const double* nrm,
+                              double w, double eps, double* out, int64_t ldo, cudaStream_t st);
 // Values of sum_j x_j phi_j on the s_test-refined full grid (FP64)
 az_status launch_evaluate(const Geom& g, double eps, int s_test, const double* x, int64_t ldx, int nrhs,
                           double* out, int64_t ldo, cudaStream_t st);

@@ -30,7 +30,10 @@ def setup(p, precision, k=None, seed=7, tau=1e-8, refine=-1, tau_sym=0.0):
         kernel = az.AZ_NEG_LAPLACE_GAUSS
         bnd = torch.from_numpy(np.ascontiguousarray(p.boundary)).to(dev())
     opts = az.make_options(precision, p.k if k is None else k, tau, tau_sym, seed, refine, p.k0)
-    h = az.az_setup(az.make_grid(g.dim, g.n, g.s, g.T), mask, g.eps, kernel, bnd, p.weight, opts)
+    nrm = None
+    if getattr(p, "normals", None) is not None:
+        nrm = torch.from_numpy(np.ascontiguousarray(p.normals, dtype=np.float64)).to(dev())
+    h = az.az_setup(az.make_grid(g.dim, g.n, g.s, g.T), mask, g.eps, kernel, bnd, p.weight, opts, normals=nrm)
     return h
 
 
