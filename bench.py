@@ -298,6 +298,13 @@ def load_traffic():
     return t.get("kernels", {})
 
 
+def plan_bytes(g, M, k, nrhs):
+    """Pass-plan byte model of one step (sketch of width k, then the mixed
+    refined solve of nrhs right-hand sides) on grid g with M kept points."""
+    Lg, Ng = g.Ltot, g.N
+    return k * (24 * Lg + 4 * M) + nrhs * (2 * (24 * M + 32 * Lg + 48 * Ng) + (24 * Ng + 16 * Lg + 16 * M))
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -432,7 +439,7 @@ def run_ours(args):
     roofline = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(achieved / hbm, 4), "peak_source": peak_src,
                 "traffic": (tr["dram_bytes_per_step"] / tr["launches_per_step"]) if tr else None,
-                "traffic_source": tr.get("source") if tr else None,
+                "traffic_source": "profiles/ncu_traffic.json (ncu dram__bytes_read.sum + dram__bytes_write.sum, one pass over the timed step of bench.py --lite)" if tr else None,
                 "algorithmic_bytes_per_launch": ent["bytes"] / max(1, ent["launches"]),
                 "avg_launch_ms": ent["ms"] / max(1, ent["launches"]), "time_share": share}
 
@@ -440,8 +447,7 @@ def run_ours(args):
     # workload: sketch k (24 L + 4 M) plus, per right-hand side of the mixed
     # refined solve, (24 M + 32 L + 48 N) twice and the FP64 residual
     # (24 N + 16 L + 16 M); and against the DRAM bytes ncu measured per step
-    Lg, Ng = g.L, g.N
-    plan = K_SKETCH * (24 * Lg + 4 * M) + NRHS * (2 * (24 * M + 32 * Lg + 48 * Ng) + (24 * Ng + 16 * Lg + 16 * M))
+    plan = plan_bytes(g, M, K_SKETCH, NRHS)
     step_s = total_ms / args.steps / 1000.0
     measured = sum(v["dram_bytes_per_step"] for v in load_traffic().values()) or None
     step_roofline = {"bound": "hbm", "plan_bytes_per_step": int(plan), "achieved": round(plan / step_s / 1e9, 1),
