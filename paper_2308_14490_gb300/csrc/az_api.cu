@@ -84,6 +84,9 @@ struct az_setup_t {
   double* r64 = nullptr;    // Mtot x cols (relres residual), lazily
   double* bcoll = nullptr;  // Mtot x cols (scaled collocation data), lazily
   LargeK* wide = nullptr;   // k > 64: Householder QR + FP64 SVD + GEMM path
+  // Omega = the whole box, no boundary rows, exact pseudo-inverse: Z* A = I,
+  // so the perturbation is exactly zero (Sec. 3.1) and the sketch is skipped
+  bool periodic = false;
   int* tc_err = nullptr;    // set by a tensor-core pipeline wait that timed out
   cudaEvent_t info_ev = nullptr;  // recorded after each factorisation (az_get_info waits on it)
 };
@@ -392,6 +395,16 @@ az_status sketch_and_factor(az_setup_t* h, cudaStream_t st) {
   T* W = (T*)h->W;
   T* Y = (T*)h->Y;
   AZ_TRY(launch_philox_bits(h->bits, g.N, k, h->seed, st));
+  if (h->periodic) {
+    // rank 0: W = (I - Z* A) R = 0 and Y = 0 exactly; nothing to factorise
+    AZ_CUDA(cudaMemsetAsync(W, 0, (size_t)g.N * k * sizeof(T), st));
+    AZ_CUDA(cudaMemsetAsync(Y, 0, (size_t)h->Mtot * k * sizeof(T), st));
+    AZ_CUDA(cudaMemsetAsync(h->Ut, 0, (size_t)h->ldm * k * sizeof(T), st));
+    AZ_CUDA(cudaMemsetAsync(h->VS, 0, (size_t)k * k * sizeof(double), st));
+    AZ_CUDA(cudaMemsetAsync(h->sig, 0, (size_t)k * sizeof(double), st));
+    AZ_CUDA(cudaMemsetAsync(h->info, 0, sizeof(FactorInfo), st));
+    return AZ_OK;
+  }
   if (h->kind == 0) {
     // W = (I - Z* A) R through the fused FFT chain (A R by the local stencil)
     AZ_TRY((zstar_chain<T, double>(h, 1, nullptr, 0, k, W, g.N, st)));
@@ -456,6 +469,11 @@ az_status az_once(az_setup_t* h, const TB* b, int64_t ldb, int ncols, double* x,
   T* z = (T*)h->zb;
   T* gg = (T*)h->gb;
   AZ_TRY((zstar_chain<T, TB>(h, 0, b, ldb, ncols, z, g.N, st)));
+  if (h->periodic) {
+    // rank 0: x = Z* b (the update with no low-rank columns)
+    return launch_update_x<T, T>((const T*)h->W, g.N, 0, h->ub, z, g.N, g.N, ncols, x, ldx, accumulate, st,
+                                 Prec<T>::fp64 ? nullptr : xf_out, Prec<T>::fp64 ? nullptr : xbase);
+  }
   AZ_TRY((apply_rows<T, T, TB, T>(h, z, g.N, b, ldb, (T)1, (T)-1, gg, h->ldm, ncols, st)));
   if (h->wide) {
     AZ_TRY(large_project(h->wide, h->Ut, h->ldm, gg, h->ldm, ncols, h->cb, st));
@@ -720,6 +738,7 @@ static az_status setup_fixed(const az_grid* gr, const uint8_t* mask, const doubl
     // Y = A W (Mtot x k) has rank <= Mtot: a wider sketch adds no direction,
     // and the Householder route needs k <= Mtot; the first columns of R are kept
     h->k = (int)std::min<int64_t>(h->k, h->Mtot);
+    h->periodic = M == g.L && h->Mb == 0 && h->kind == 0 && h->tau_sym == 0.0;
     if (M > 0) {
       // kept points forming one run of consecutive grid indices (a 1D
       // interval): the gather then needs no index-map lookups
