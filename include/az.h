@@ -204,9 +204,16 @@ az_status az_rademacher(int64_t N, int32_t k, uint64_t seed, double* R_dev, void
 az_status az_rademacher_noalloc(int64_t N, int32_t k, uint64_t seed, double* R_dev, void* stream);
 
 /* Recompute every setup step (index map, symbol, test matrix with a new
- * seed, sketch, factorisation) on an existing handle, on `stream`, without
- * allocating and without synchronising.  A factorisation breakdown is reported
- * by the next az_get_info (status is checked lazily). */
+ * seed, sketch, factorisation) on an existing handle, without allocating and
+ * without synchronising.  The index map and symbol are computed on `stream`.
+ * For approximation setups with k <= 64 the sketch and factorisation (steps 2-3
+ * of Algorithm 1's setup) then run on the handle's own high-priority stream, so
+ * that the next az_solve's first Z* pass overlaps them: every later call on the
+ * handle that uses the factors (az_solve, az_get_array, az_get_info, the next
+ * az_refactor) waits for them on its own stream, whichever stream that is.
+ * Synchronising `stream` alone does not cover the factorisation; az_get_info
+ * does.  Other setups run every step on `stream`.  A factorisation breakdown
+ * is reported by the next az_get_info (status is checked lazily). */
 az_status az_refactor(az_handle h, uint64_t seed, void* stream);
 
 /* Instrumentation (not part of the paper's method).

@@ -89,6 +89,16 @@ struct az_setup_t {
   bool periodic = false;
   int* tc_err = nullptr;    // set by a tensor-core pipeline wait that timed out
   cudaEvent_t info_ev = nullptr;  // recorded after each factorisation (az_get_info waits on it)
+  // az_refactor runs the sketch and factorisation (S3-S7) on fst, after the
+  // index map and symbol on the caller's stream (ev_sym), so that the next
+  // solve's first Z* pass overlaps it; the solve waits on ev_fac before it
+  // uses the factors.  X1s/X3s: the sketch chain's own FFT workspace.
+  cudaStream_t fst = nullptr;
+  cudaEvent_t ev_sym = nullptr, ev_fac = nullptr;
+  bool fac_pending = false;
+  void* X1s = nullptr;
+  void* X3s = nullptr;
+  int pairs_s = 0;
 };
 
 namespace {
@@ -353,10 +363,12 @@ az_status zstar_chain(az_setup_t* h, int mode, const TB* b, int64_t ldb, int nco
   const Geom& g = h->g;
   PassTabs tb = tabs<T>(h);
   const int npairs_total = (ncols + 1) / 2;
-  for (int p0 = 0; p0 < npairs_total; p0 += h->pairs_max) {
-    const int np = std::min(h->pairs_max, npairs_total - p0);
-    V* X1 = (V*)h->X1;
-    V* X3 = (V*)h->X3;
+  const bool own = mode == 1 && h->X1s;   // the sketch chain on its own workspace
+  const int step = own ? h->pairs_s : h->pairs_max;
+  for (int p0 = 0; p0 < npairs_total; p0 += step) {
+    const int np = std::min(step, npairs_total - p0);
+    V* X1 = (V*)(own ? h->X1s : h->X1);
+    V* X3 = (V*)(own ? h->X3s : h->X3);
     if (mode == 1) {
       SketchIn<T> in;
       in.bits = h->bits; in.nw = h->nw; in.k = h->k; in.pos2m = h->pos2m;
@@ -475,6 +487,11 @@ az_status az_once(az_setup_t* h, const TB* b, int64_t ldb, int ncols, double* x,
                                  Prec<T>::fp64 ? nullptr : xf_out, Prec<T>::fp64 ? nullptr : xbase);
   }
   AZ_TRY((apply_rows<T, T, TB, T>(h, z, g.N, b, ldb, (T)1, (T)-1, gg, h->ldm, ncols, st)));
+  if (h->fac_pending) {
+    // the factors of an az_refactor still running on the setup's own stream
+    AZ_CUDA(cudaStreamWaitEvent(st, h->ev_fac, 0));
+    h->fac_pending = false;
+  }
   if (h->wide) {
     AZ_TRY(large_project(h->wide, h->Ut, h->ldm, gg, h->ldm, ncols, h->cb, st));
     AZ_TRY(launch_small_mm(h->VS, h->k, h->cb, ncols, h->ub, st));
@@ -578,6 +595,7 @@ az_status alloc_workspace(az_setup_t* h) {
 
 void destroy(az_setup_t* h) {
   if (!h) return;
+  if (h->fst) cudaStreamSynchronize(h->fst);
   for (void* p : h->allocs) cudaFree(p);
   if (h->X1d) cudaFree(h->X1d);
   if (h->X3d) cudaFree(h->X3d);
@@ -585,6 +603,9 @@ void destroy(az_setup_t* h) {
   if (h->bcoll) cudaFree(h->bcoll);
   if (h->wide) large_destroy(h->wide);
   if (h->info_ev) cudaEventDestroy(h->info_ev);
+  if (h->ev_sym) cudaEventDestroy(h->ev_sym);
+  if (h->ev_fac) cudaEventDestroy(h->ev_fac);
+  if (h->fst) cudaStreamDestroy(h->fst);
   delete h;
 }
 
@@ -632,6 +653,8 @@ az_status az_query_footprint(const az_grid* gr, int64_t M, int64_t n_boundary, c
   if (k <= 64) b += (size_t)partial_blocks(Mt) * k * std::max(k, cols) * 8;
   else b += (size_t)k * k * 8 * 5 + (size_t)Mt * k * 4 + (32u << 20);   // small FP64 factors, QR workspace, cuBLAS workspace
   b += (size_t)Mt * k * 8;                          // transient Q1 during setup
+  if (n_boundary == 0 && k <= 64 && M < g.L)        // the sketch chain's own X1, X3 (approximation)
+    b += (size_t)std::min<int64_t>(pm, (k + 1) / 2) * (g.L + g.N) * vsz;
   *bytes = b;
   return AZ_OK;
 }
@@ -790,6 +813,24 @@ static az_status setup_fixed(const az_grid* gr, const uint8_t* mask, const doubl
     rc = dalloc_t(h, &h->sig, h->k); if (rc) break;
     rc = dalloc_t(h, &h->info, 1); if (rc) break;
     rc = alloc_workspace(h); if (rc) break;
+    if (h->kind == 0 && !h->periodic && h->k <= kNarrowK && !(h->precision == AZ_FP64 && h->tau_svd < kGramTau)) {
+      // overlap of az_refactor's sketch with the next solve: own stream,
+      // events and FFT workspace for the sketch chain
+      h->pairs_s = std::min(h->pairs_max, (h->k + 1) / 2);
+      const size_t vsz = h->precision == AZ_FP64 ? 16 : 8;
+      rc = dalloc(h, &h->X1s, (size_t)h->pairs_s * g.L * vsz); if (rc) break;
+      rc = dalloc(h, &h->X3s, (size_t)h->pairs_s * g.N * vsz); if (rc) break;
+      // higher priority: the sketch-to-factor chain is the critical path, and
+      // the solve's passes fill the SMs it leaves idle (the one-CTA factor
+      // kernels)
+      int prio_lo = 0, prio_hi = 0;
+      cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+      if (cudaStreamCreateWithPriority(&h->fst, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+          cudaEventCreateWithFlags(&h->ev_sym, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&h->ev_fac, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError(); set_error("az_setup: stream or event"); rc = AZ_ERR_CUDA; break;
+      }
+    }
     // The Gram route squares the sketch's condition number, so in FP64 it
     // resolves singular values down to about 1e-8 sigma_1; a tighter tau
     // takes the Householder route whatever the width.
@@ -831,7 +872,20 @@ static az_status setup_fixed(const az_grid* gr, const uint8_t* mask, const doubl
 az_status az_refactor(az_handle h, uint64_t seed, void* stream) {
   if (!h) { set_error("az_refactor: null handle"); return AZ_ERR_ARG; }
   h->seed = seed;
-  return compute_setup(h, (cudaStream_t)stream, true);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!h->fst) return compute_setup(h, st, true);
+  // index map and symbol on the caller's stream (after any earlier
+  // factorisation); sketch and factorisation on the setup's stream
+  if (h->fac_pending) AZ_CUDA(cudaStreamWaitEvent(st, h->ev_fac, 0));
+  AZ_TRY(launch_compact(h->mask, h->g.L, h->pos2m, h->idx, h->Md, h->scan, st));
+  AZ_TRY(build_symbol(h, st));
+  AZ_CUDA(cudaEventRecord(h->ev_sym, st));
+  AZ_CUDA(cudaStreamWaitEvent(h->fst, h->ev_sym, 0));
+  AZ_TRY(h->precision == AZ_FP64 ? sketch_and_factor<double>(h, h->fst) : sketch_and_factor<float>(h, h->fst));
+  AZ_CUDA(cudaEventRecord(h->info_ev, h->fst));
+  AZ_CUDA(cudaEventRecord(h->ev_fac, h->fst));
+  h->fac_pending = true;
+  return AZ_OK;
 }
 
 az_status az_solve(az_handle h, const double* b, int64_t ldb, int64_t nrhs, double* x, int64_t ldx, void* stream,
@@ -914,6 +968,7 @@ az_status az_get_info(az_handle h, az_info_t* info) {
 az_status az_get_array(az_handle h, int32_t which, double* dst, void* stream) {
   if (!h || !dst) { set_error("az_get_array: bad arguments"); return AZ_ERR_ARG; }
   cudaStream_t st = (cudaStream_t)stream;
+  if (h->fac_pending) AZ_CUDA(cudaStreamWaitEvent(st, h->ev_fac, 0));
   const bool f64 = h->precision == AZ_FP64;
   switch (which) {
     case AZ_ARRAY_SYMBOL:
