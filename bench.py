@@ -422,8 +422,20 @@ def run_ours(args):
     info = az.az_get_info(h)
     az.az_destroy(h64)
 
-    # roofline of the dominant kernel (largest total device time in the timed region)
-    dom, ent = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    # roofline of the dominant kernel.  In the timed steps the refactor's sketch
+    # runs on the setup's own stream beside the solve's first Z* pass, so a
+    # launch's event-to-event time there includes sharing the GPU; the
+    # per-kernel durations of the roofline come from the same steps run again
+    # with the refactor finished before the solve starts (each launch alone).
+    az.az_profile_begin()
+    for i in range(3):
+        az.az_refactor(h, 1 + (i % 2), stream)
+        torch.cuda.synchronize(dev)
+        az.az_solve(h, b_dev, x_dev, stream)
+    torch.cuda.synchronize(dev)
+    prof_iso = az.az_profile_end()
+    dom, ent = max(prof_iso.items(), key=lambda kv: kv[1]["ms"])
+    ent_t = prof.get(dom, {"ms": 0.0, "launches": 1})
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -441,7 +453,11 @@ def run_ours(args):
                 "traffic": (tr["dram_bytes_per_step"] / tr["launches_per_step"]) if tr else None,
                 "traffic_source": "profiles/ncu_traffic.json (ncu dram__bytes_read.sum + dram__bytes_write.sum, one pass over the timed step of bench.py --lite)" if tr else None,
                 "algorithmic_bytes_per_launch": ent["bytes"] / max(1, ent["launches"]),
-                "avg_launch_ms": ent["ms"] / max(1, ent["launches"]), "time_share": share}
+                "avg_launch_ms": ent["ms"] / max(1, ent["launches"]),
+                "avg_launch_ms_in_timed_steps": ent_t["ms"] / max(1, ent_t["launches"]),
+                "durations": "CUDA events around each launch on its stream, 3 steps with the refactor finished before "
+                             "the solve; time_share is from the timed steps (refactor overlapping the solve)",
+                "time_share": share}
 
     # whole step against the pass-plan byte model fixed in advance for this
     # workload: sketch k (24 L + 4 M) plus, per right-hand side of the mixed

@@ -389,7 +389,11 @@ __device__ int jacobi_onesided(TJ* a, int m, int n, TJ* V, int* flag, double flo
       for (int pr = warp; pr < nn / 2; pr += nwarps) {
         // round-robin pairing: positions 0..nn-1, position 0 fixed
         int p0 = pr, p1 = nn - 1 - pr;
-        auto idx = [&](int pos) { return pos == 0 ? 0 : 1 + ((pos - 1 + step) % (nn - 1)); };
+        auto idx = [&](int pos) {   // 1 + (pos - 1 + step) mod (nn - 1), both terms < nn - 1
+          int v = pos - 1 + step;
+          if (v >= nn - 1) v -= nn - 1;
+          return pos == 0 ? 0 : 1 + v;
+        };
         int i = idx(p0), j = idx(p1);
         if (i > j) { int tt = i; i = j; j = tt; }
         if (j >= n) continue;
@@ -448,13 +452,28 @@ __global__ void k_factor1(const double* __restrict__ G1, int k, double tol, doub
   if (threadIdx.x == 0) { r1s = 0; stop = 0; }
   __syncthreads();
   for (int j = 0; j < k; ++j) {
-    if (threadIdx.x == 0) {
-      int p = j;
-      double best = G[j * k + j];
-      for (int i = j + 1; i < k; ++i) if (G[i * k + i] > best) { best = G[i * k + i]; p = i; }
-      if (j == 0) dmax = best;
-      if (!(best > tol * dmax) || !(best > floor2) || !isfinite(best)) stop = 1;
-      piv = p;
+    if (threadIdx.x < 32) {
+      // pivot: the first largest remaining diagonal entry (warp arg-max, k <= 64)
+      const int lane = threadIdx.x;
+      double best = -INFINITY;
+      int p = k;
+      for (int i = j + lane; i < k; i += 32) {
+        const double v = G[i * k + i];
+        if (v > best || (p == k && !(v == v))) { best = v == v ? v : -INFINITY; p = i; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int op = __shfl_xor_sync(0xffffffffu, p, o);
+        if (ob > best || (ob == best && op < p)) { best = ob; p = op; }
+      }
+      if (lane == 0) {
+        const double gjj = G[j * k + j];
+        if (!(gjj == gjj)) { best = gjj; p = j; }   // a NaN pivot candidate stops the pass
+        if (p >= k) p = j;
+        if (j == 0) dmax = best;
+        if (!(best > tol * dmax) || !(best > floor2) || !isfinite(best)) stop = 1;
+        piv = p;
+      }
     }
     __syncthreads();
     if (stop) break;
@@ -486,6 +505,10 @@ __global__ void k_factor1(const double* __restrict__ G1, int k, double tol, doub
   const int r1 = r1s;
   if (threadIdx.x == 0) { info->r1 = r1; info->status = isfinite(dmax) ? 0 : 2; info->pad = 0; }
   // B1 = P[:, :r1] R11^{-1}: column c solves R11 y = e_c by back substitution
+  // (the r1 reciprocal pivots are formed once, in parallel)
+  __shared__ double rdiag[64];
+  for (int i = threadIdx.x; i < r1; i += blockDim.x) rdiag[i] = 1.0 / R[i * k + i];
+  __syncthreads();
   for (int c = threadIdx.x; c < k; c += blockDim.x) {
     for (int i = 0; i < k; ++i) B1[(int64_t)c * k + i] = 0.0;
     if (c < r1) {
@@ -493,7 +516,7 @@ __global__ void k_factor1(const double* __restrict__ G1, int k, double tol, doub
       for (int i = r1 - 1; i >= 0; --i) {
         double sacc = (i == c) ? 1.0 : 0.0;
         for (int l = i + 1; l < r1; ++l) sacc -= R[i * k + l] * y[l];
-        y[i] = sacc / R[i * k + i];
+        y[i] = sacc * rdiag[i];
       }
       for (int i = 0; i < r1; ++i) B1[(int64_t)c * k + perm[i]] = y[i];
     }
