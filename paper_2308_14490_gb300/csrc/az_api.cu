@@ -881,11 +881,14 @@ az_status az_refactor(az_handle h, uint64_t seed, void* stream) {
   AZ_TRY(build_symbol(h, st));
   AZ_CUDA(cudaEventRecord(h->ev_sym, st));
   AZ_CUDA(cudaStreamWaitEvent(h->fst, h->ev_sym, 0));
-  AZ_TRY(h->precision == AZ_FP64 ? sketch_and_factor<double>(h, h->fst) : sketch_and_factor<float>(h, h->fst));
+  const az_status rc = h->precision == AZ_FP64 ? sketch_and_factor<double>(h, h->fst)
+                                               : sketch_and_factor<float>(h, h->fst);
+  // recorded whatever happened, so that later calls wait for whatever was
+  // enqueued before an error
   AZ_CUDA(cudaEventRecord(h->info_ev, h->fst));
   AZ_CUDA(cudaEventRecord(h->ev_fac, h->fst));
   h->fac_pending = true;
-  return AZ_OK;
+  return rc;
 }
 
 az_status az_solve(az_handle h, const double* b, int64_t ldb, int64_t nrhs, double* x, int64_t ldx, void* stream,
