@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparator", action="store_true")
+    ap.add_argument("--no-paper-examples", action="store_true")
     ap.add_argument("--nrhs", type=int, default=NRHS, help="right-hand sides per step (default: the workload's 64)")
     ap.add_argument("--serving-seconds", type=float, default=5.0,
                     help="length of the serving-stream sample (Poisson arrivals, 200 req/s); 0 skips it")
@@ -230,6 +231,75 @@ def fp64_torch_comparator(p, b_dev, steps=2, warmup=1):
 
 
 # --------------------------------------------------------------------------- serving sample
+def paper_examples_leg():
+    """The paper's own 1D examples at its shape parameter (Eq. constant_shapeparam,
+    tau0 = 1e-10, eps h = 0.327), all-FP64 on the GPU, at N = 2^20 for the two
+    approximation problems (Sec. 3.3: the paper notes its Matlab AZ stays under
+    10 s up to N = 1e6 on a laptop) and N = 2^16 for the ODE of Example 6.1.
+    Context beside the headline: setup and solve times and the maximum error
+    against the closed-form function on a 4x finer grid inside the domain."""
+    import math
+    import numpy as np
+    import torch
+    import paper_2308_14490_gb300 as az
+    import workloads as W
+    dev = torch.device("cuda", 0)
+    epsh = W.epsh_from_tau0(1e-10)
+    out = {}
+
+    def timed(fn):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize(dev)
+        return r, 1000.0 * (time.perf_counter() - t0)
+
+    cases = []
+    N = 1 << 20
+    fq = math.floor(N / 5)
+    g = W.Grid(1, (N,), (2,), (1.0,), epsh)
+    cases.append(("periodic_sin_fq_pi_x", g, np.ones(g.Ltot, np.uint8), lambda q: np.sin(fq * math.pi * q), 64,
+                  (-1.0, 1.0), None))
+    g = W.Grid(1, (N,), (2,), (1.5,), epsh)
+    cases.append(("nonperiodic_sin_Nx_over_5", g, W.interval_mask(g, -1.0, 1.0), lambda q: np.sin(N / 5.0 * q), 128,
+                  (-1.0, 1.0), None))
+    ode = W.ode(n=1 << 16, k=64)
+    cases.append(("ode_example_6_1", ode.grid, ode.mask, lambda q: np.sin(ode.k0 * q), 64, (-1.0, 1.0), ode))
+    for name, g, m, f, k, (a, b_), prob in cases:
+        try:
+            opts = az.make_options(az.AZ_FP64, k, 1e-12, 0.0, 1, 0, prob.k0 if prob is not None else 0.0)
+            mask = torch.from_numpy(np.ascontiguousarray(m)).to(dev)
+            grid = az.make_grid(1, g.n, g.s, g.T)
+            if prob is None:
+                pts = W.kept_points(g, m)[:, 0]
+                b = torch.from_numpy(np.ascontiguousarray(f(pts)[None, :])).to(dev)
+                h, setup_ms = timed(lambda: az.az_setup(grid, mask, g.eps, options=opts))
+                x = torch.zeros((1, g.N), dtype=torch.float64, device=dev)
+                _, solve_ms = timed(lambda: az.az_solve(h, b, x))
+            else:
+                bpts = torch.from_numpy(np.ascontiguousarray(prob.boundary)).to(dev)
+                h, setup_ms = timed(lambda: az.az_setup(grid, mask, g.eps, az.AZ_NEG_LAPLACE_GAUSS, bpts,
+                                                        prob.weight, opts))
+                fr = torch.from_numpy(np.ascontiguousarray(prob.rhs().T)).to(dev)
+                gr = torch.from_numpy(np.ascontiguousarray(prob.boundary_rhs().T)).to(dev)
+                x = torch.zeros((1, g.N), dtype=torch.float64, device=dev)
+                _, solve_ms = timed(lambda: az.az_collocate(h, fr, gr, x))
+            info = az.az_get_info(h)
+            vals = torch.zeros((1, g.N * 4), dtype=torch.float64, device=dev)
+            az.az_evaluate(h, x, 4, vals)
+            az.az_destroy(h)
+            xf = W.grid_coords(W.Grid(1, g.n, (4,), g.T, g.epsh), 0)
+            inside = (xf >= a) & (xf <= b_)
+            err = float(np.abs(vals.cpu().numpy()[0] - f(xf))[inside].max())
+            out[name] = {"N": g.N, "k": info["k"], "rank": info["rank"], "setup_ms": round(setup_ms, 2),
+                         "solve_ms": round(solve_ms, 2), "max_error": err}
+        except Exception as ex:  # context only, never the headline
+            out[name] = {"error": str(ex)[:200]}
+    out["what"] = ("the paper's 1D examples at eps h = 0.327 (tau0 = 1e-10), FP64 throughout, tau = 1e-12; "
+                   "setup = az_setup (index map, symbol, sketch, factorisation) wall time, solve = one right-hand side")
+    return out
+
+
 def serving_leg(seconds):
     """The mixed request stream: Poisson arrivals at 200/s of 1D / 2D approximations
     and 2D Poisson collocations drawn from a seeded pool of 32 setups, 1..32 RHS
@@ -493,6 +563,8 @@ def run_ours(args):
     az.az_destroy(h)
     if rank == 0 and world == 1 and args.serving_seconds > 0:
         line["serving"] = serving_leg(args.serving_seconds)
+    if rank == 0 and world == 1 and not args.no_paper_examples:
+        line["paper_examples"] = paper_examples_leg()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_leg()
     if rank == 0:
