@@ -38,7 +38,7 @@ WORKLOAD = "1d-approx N=2^20 s=2 eps=1/h Omega=[-0.7,0.3] k=24 nrhs=64 mixed(FP3
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
