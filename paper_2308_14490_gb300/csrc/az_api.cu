@@ -87,6 +87,10 @@ struct az_setup_t {
   // Omega = the whole box, no boundary rows, exact pseudo-inverse: Z* A = I,
   // so the perturbation is exactly zero (Sec. 3.1) and the sketch is skipped
   bool periodic = false;
+  // leading sketch columns (of W and Y) already valid, copied from a
+  // narrower setup with the same seed by the adaptive width; the next
+  // sketch computes only the columns after them
+  int k_done = 0;
   int* tc_err = nullptr;    // set by a tensor-core pipeline wait that timed out
   cudaEvent_t info_ev = nullptr;  // recorded after each factorisation (az_get_info waits on it)
   // az_refactor runs the sketch and factorisation (S3-S7) on fst, after the
@@ -358,14 +362,15 @@ az_status build_symbol(az_setup_t* h, cudaStream_t st) {
 //  mode 2: b = A R given as a compact vector -> W = R - Z* b
 template <typename T, typename TB>
 az_status zstar_chain(az_setup_t* h, int mode, const TB* b, int64_t ldb, int ncols, T* zout, int64_t ldz,
-                      cudaStream_t st) {
+                      cudaStream_t st, int first_col = 0) {
   using V = typename C2<T>::t;
   const Geom& g = h->g;
   PassTabs tb = tabs<T>(h);
   const int npairs_total = (ncols + 1) / 2;
   const bool own = mode == 1 && h->X1s;   // the sketch chain on its own workspace
   const int step = own ? h->pairs_s : h->pairs_max;
-  for (int p0 = 0; p0 < npairs_total; p0 += step) {
+  if (first_col & 1) { set_error("zstar_chain: odd first column"); return AZ_ERR_ARG; }
+  for (int p0 = first_col / 2; p0 < npairs_total; p0 += step) {
     const int np = std::min(step, npairs_total - p0);
     V* X1 = (V*)(own ? h->X1s : h->X1);
     V* X3 = (V*)(own ? h->X3s : h->X3);
@@ -406,6 +411,8 @@ az_status sketch_and_factor(az_setup_t* h, cudaStream_t st) {
   const int k = h->k;
   T* W = (T*)h->W;
   T* Y = (T*)h->Y;
+  const int k0 = h->k_done < k ? h->k_done : 0;   // columns [0, k0) of W and Y are current
+  h->k_done = 0;
   AZ_TRY(launch_philox_bits(h->bits, g.N, k, h->seed, st));
   if (h->periodic) {
     // rank 0: W = (I - Z* A) R = 0 and Y = 0 exactly; nothing to factorise
@@ -419,18 +426,20 @@ az_status sketch_and_factor(az_setup_t* h, cudaStream_t st) {
   }
   if (h->kind == 0) {
     // W = (I - Z* A) R through the fused FFT chain (A R by the local stencil)
-    AZ_TRY((zstar_chain<T, double>(h, 1, nullptr, 0, k, W, g.N, st)));
+    AZ_TRY((zstar_chain<T, double>(h, 1, nullptr, 0, k, W, g.N, st, k0)));
   } else {
     // Collocation: v = A R on all rows by the stencil rows (R materialised in
     // FP64), then W = R - Z* v through the gather chain (Z* has zero columns
     // for the boundary rows).
     T* v = (T*)h->gb;    // Mtot x k scratch (gb holds >= k columns)
     AZ_TRY(launch_bits_to_R(h->bits, g.N, k, h->Rd, st));
-    AZ_TRY((apply_rows<T, double, double, T>(h, h->Rd, g.N, nullptr, 0, (T)0, (T)1, v, h->ldm, k, st)));
-    AZ_TRY((zstar_chain<T, T>(h, 2, v, h->ldm, k, W, g.N, st)));
+    AZ_TRY((apply_rows<T, double, double, T>(h, h->Rd + (size_t)k0 * g.N, g.N, nullptr, 0, (T)0, (T)1,
+                                              v + (size_t)k0 * h->ldm, h->ldm, k - k0, st)));
+    AZ_TRY((zstar_chain<T, T>(h, 2, v, h->ldm, k, W, g.N, st, k0)));
   }
   // Y = A W on all rows (kept grid rows, then weighted boundary rows)
-  AZ_TRY((apply_rows<T, T, double, T>(h, W, g.N, nullptr, 0, (T)0, (T)1, Y, h->Mtot, k, st)));
+  AZ_TRY((apply_rows<T, T, double, T>(h, W + (size_t)k0 * g.N, g.N, nullptr, 0, (T)0, (T)1,
+                                      Y + (size_t)k0 * h->Mtot, h->Mtot, k - k0, st)));
   if (h->wide) {
     // wide sketch: Householder QR of Y (Q into the Q1 scratch), SVD of R
     return large_factor(h->wide, Y, h->Mtot, h->Q1, h->Ut, h->ldm, h->tau_svd, h->floor, h->VS, h->sig, h->info, st);
@@ -661,7 +670,7 @@ az_status az_query_footprint(const az_grid* gr, int64_t M, int64_t n_boundary, c
 
 static az_status setup_fixed(const az_grid* gr, const uint8_t* mask, const double* bpts, int64_t n_boundary,
                              double eps, int32_t kernel, double boundary_weight, const az_options* opt, void* stream,
-                             az_handle* out);
+                             az_handle* out, const az_setup_t* reuse = nullptr);
 
 // The mixed path inverts the symbol in FP32.  Within one alias group of the
 // Gaussian symbol (Eq. periodic_rbf, Poisson summation) the largest member
@@ -692,22 +701,26 @@ az_status az_setup(const az_grid* gr, const uint8_t* mask, const double* bpts, i
   for (int d = 0; d < gr->dim && d < 2; ++d) N *= gr->n[d];
   const double tsat = opt->precision == AZ_FP64 ? 1e-7 : 1e-4;
   az_options o = *opt;
+  az_handle prev = nullptr;   // the narrower setup, whose sketch columns are reused
   for (int k = 64;; k *= 2) {
     o.k = (int)std::min<int64_t>(std::min<int64_t>(k, 4096), std::max<int64_t>(1, N));
     az_handle h = nullptr;
-    AZ_TRY(setup_fixed(gr, mask, bpts, n_boundary, eps, kernel, boundary_weight, &o, stream, &h));
+    const az_status rs = setup_fixed(gr, mask, bpts, n_boundary, eps, kernel, boundary_weight, &o, stream, &h, prev);
+    if (prev) az_destroy(prev);
+    prev = nullptr;
+    if (rs) return rs;
     az_info_t info;
     const az_status rc = az_get_info(h, &info);
     if (rc) { az_destroy(h); return rc; }
     const bool saturated = info.rank >= o.k && info.sigma_max > 0 && info.sigma_min_kept > tsat * info.sigma_max;
     if (!saturated || o.k >= 4096 || o.k >= N) { *out = h; return AZ_OK; }
-    az_destroy(h);
+    prev = h;
   }
 }
 
 static az_status setup_fixed(const az_grid* gr, const uint8_t* mask, const double* bpts, int64_t n_boundary,
                              double eps, int32_t kernel, double boundary_weight, const az_options* opt, void* stream,
-                             az_handle* out) {
+                             az_handle* out, const az_setup_t* reuse) {
   if (!out) { set_error("az_setup: null output handle"); return AZ_ERR_ARG; }
   *out = nullptr;
   if (!mask) { set_error("az_setup: Omega mask is required"); return AZ_ERR_ARG; }
@@ -853,6 +866,17 @@ static az_status setup_fixed(const az_grid* gr, const uint8_t* mask, const doubl
       h->floor = 1e-13 * est;
     }
     // S3-S7
+    if (reuse && reuse->k < h->k && reuse->k % 2 == 0 && reuse->precision == h->precision && reuse->seed == h->seed &&
+        reuse->g.N == g.N && reuse->Mtot == h->Mtot && !h->periodic) {
+      // adaptive growth: the first reuse->k columns of R, hence of W and Y,
+      // are those of the narrower setup (same seed, same geometry)
+      const size_t tsz = h->precision == AZ_FP64 ? 8 : 4;
+      if (cudaMemcpyAsync(h->W, reuse->W, (size_t)g.N * reuse->k * tsz, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+          cudaMemcpyAsync(h->Y, reuse->Y, (size_t)h->Mtot * reuse->k * tsz, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+        cudaGetLastError(); set_error("az_setup: sketch column copy"); rc = AZ_ERR_CUDA; break;
+      }
+      h->k_done = reuse->k;
+    }
     rc = h->precision == AZ_FP64 ? sketch_and_factor<double>(h, st) : sketch_and_factor<float>(h, st);
     if (rc) break;
     FactorInfo fi;

@@ -56,3 +56,28 @@ def test_adaptive_width_reaches_the_direct_solution(az, name):
     # sit near the threshold and the residuals agree to a few per cent (1D: 1e-10)
     tol = 1e-10 if name == "config1" else 0.05 * r_d
     assert np.all(np.abs(r_g - r_d) <= tol), (info["k"], r_g.tolist(), r_d.tolist())
+
+
+@pytest.mark.parametrize("name,prec", [("disc-n32", "fp64"), ("disc-n32", "mixed"), ("poisson-n16", "fp64")])
+def test_adaptive_growth_reuses_columns_exactly(az, name, prec):
+    # each doubling keeps the narrower setup's sketch columns (same seed, so the
+    # same columns of R) and computes only the new ones: the result is the
+    # fixed-width setup at the final width, bit for bit
+    gu = _gu()
+    p = {"disc-n32": lambda: W.config3(n=32, k=0), "poisson-n16": lambda: W.config4(n=16, nb=64, k=0)}[name]()
+    P = az.AZ_FP64 if prec == "fp64" else az.AZ_MIXED
+    op, b = _op_rhs(p)
+    out = {}
+    for k in (0, None):
+        kk = k if k == 0 else out[0][1]["k"]
+        h = gu.setup(p, P, k=kk, seed=5, refine=0)
+        try:
+            info = az.az_get_info(h)
+            x = torch.zeros((b.shape[1], op.N), dtype=torch.float64, device=gu.dev())
+            az.az_solve(h, gu.to_dev_cols(b), x)
+            out[k] = (gu.from_dev_cols(x), info)
+        finally:
+            az.az_destroy(h)
+    assert out[0][1]["k"] > 64          # at least one doubling happened
+    assert out[0][1]["rank"] == out[None][1]["rank"]
+    assert np.array_equal(out[0][0], out[None][0]), np.abs(out[0][0] - out[None][0]).max()
