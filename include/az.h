@@ -69,7 +69,9 @@ typedef struct {
   int32_t precision;    /* AZ_FP64, or AZ_MIXED: FP32 transforms/sketch, FP64 factor work and residual */
   int32_t k;            /* sketch width r + p (number of random columns, Sec. 3.2.3), 1..4096; 0 = adaptive:
                            widths 64, 128, ... until the k-th singular value of the sketch is below
-                           1e-7 (FP64) or 1e-4 (mixed) of the largest (az_get_info reports the k used).
+                           1e-7 (FP64) or 1e-4 (mixed) of the largest (az_get_info reports the k used);
+                           each wider attempt keeps the narrower one's sketch columns and sketches only
+                           the new ones, so the result equals a fixed-width setup at the final width.
                            A width above M + n_boundary (the number of rows of the sketch) is reduced
                            to it; the first columns of R are kept */
   double tau_svd;       /* relative truncation of the low-rank solve (0 = default: 1e-8).  The narrow
