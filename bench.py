@@ -266,35 +266,36 @@ def paper_examples_leg():
     ode = W.ode(n=1 << 16, k=64)
     cases.append(("ode_example_6_1", ode.grid, ode.mask, lambda q: np.sin(ode.k0 * q), 64, (-1.0, 1.0), ode))
     for name, g, m, f, k, (a, b_), prob in cases:
-        try:
-            opts = az.make_options(az.AZ_FP64, k, 1e-12, 0.0, 1, 0, prob.k0 if prob is not None else 0.0)
-            mask = torch.from_numpy(np.ascontiguousarray(m)).to(dev)
-            grid = az.make_grid(1, g.n, g.s, g.T)
-            if prob is None:
-                pts = W.kept_points(g, m)[:, 0]
-                b = torch.from_numpy(np.ascontiguousarray(f(pts)[None, :])).to(dev)
-                h, setup_ms = timed(lambda: az.az_setup(grid, mask, g.eps, options=opts))
-                x = torch.zeros((1, g.N), dtype=torch.float64, device=dev)
-                _, solve_ms = timed(lambda: az.az_solve(h, b, x))
-            else:
-                bpts = torch.from_numpy(np.ascontiguousarray(prob.boundary)).to(dev)
-                h, setup_ms = timed(lambda: az.az_setup(grid, mask, g.eps, az.AZ_NEG_LAPLACE_GAUSS, bpts,
-                                                        prob.weight, opts))
-                fr = torch.from_numpy(np.ascontiguousarray(prob.rhs().T)).to(dev)
-                gr = torch.from_numpy(np.ascontiguousarray(prob.boundary_rhs().T)).to(dev)
-                x = torch.zeros((1, g.N), dtype=torch.float64, device=dev)
-                _, solve_ms = timed(lambda: az.az_collocate(h, fr, gr, x))
-            info = az.az_get_info(h)
-            vals = torch.zeros((1, g.N * 4), dtype=torch.float64, device=dev)
-            az.az_evaluate(h, x, 4, vals)
-            az.az_destroy(h)
-            xf = W.grid_coords(W.Grid(1, g.n, (4,), g.T, g.epsh), 0)
-            inside = (xf >= a) & (xf <= b_)
-            err = float(np.abs(vals.cpu().numpy()[0] - f(xf))[inside].max())
-            out[name] = {"N": g.N, "k": info["k"], "rank": info["rank"], "setup_ms": round(setup_ms, 2),
-                         "solve_ms": round(solve_ms, 2), "max_error": err}
-        except Exception as ex:  # context only, never the headline
-            out[name] = {"error": str(ex)[:200]}
+        for rep in range(2):   # the first pass loads the kernels this case uses; the second is reported
+            try:
+                opts = az.make_options(az.AZ_FP64, k, 1e-12, 0.0, 1, 0, prob.k0 if prob is not None else 0.0)
+                mask = torch.from_numpy(np.ascontiguousarray(m)).to(dev)
+                grid = az.make_grid(1, g.n, g.s, g.T)
+                if prob is None:
+                    pts = W.kept_points(g, m)[:, 0]
+                    b = torch.from_numpy(np.ascontiguousarray(f(pts)[None, :])).to(dev)
+                    h, setup_ms = timed(lambda: az.az_setup(grid, mask, g.eps, options=opts))
+                    x = torch.zeros((1, g.N), dtype=torch.float64, device=dev)
+                    _, solve_ms = timed(lambda: az.az_solve(h, b, x))
+                else:
+                    bpts = torch.from_numpy(np.ascontiguousarray(prob.boundary)).to(dev)
+                    h, setup_ms = timed(lambda: az.az_setup(grid, mask, g.eps, az.AZ_NEG_LAPLACE_GAUSS, bpts,
+                                                            prob.weight, opts))
+                    fr = torch.from_numpy(np.ascontiguousarray(prob.rhs().T)).to(dev)
+                    gr = torch.from_numpy(np.ascontiguousarray(prob.boundary_rhs().T)).to(dev)
+                    x = torch.zeros((1, g.N), dtype=torch.float64, device=dev)
+                    _, solve_ms = timed(lambda: az.az_collocate(h, fr, gr, x))
+                info = az.az_get_info(h)
+                vals = torch.zeros((1, g.N * 4), dtype=torch.float64, device=dev)
+                az.az_evaluate(h, x, 4, vals)
+                az.az_destroy(h)
+                xf = W.grid_coords(W.Grid(1, g.n, (4,), g.T, g.epsh), 0)
+                inside = (xf >= a) & (xf <= b_)
+                err = float(np.abs(vals.cpu().numpy()[0] - f(xf))[inside].max())
+                out[name] = {"N": g.N, "k": info["k"], "rank": info["rank"], "setup_ms": round(setup_ms, 2),
+                             "solve_ms": round(solve_ms, 2), "max_error": err}
+            except Exception as ex:  # context only, never the headline
+                out[name] = {"error": str(ex)[:200]}
     out["what"] = ("the paper's 1D examples at eps h = 0.327 (tau0 = 1e-10), FP64 throughout, tau = 1e-12; "
                    "setup = az_setup (index map, symbol, sketch, factorisation) wall time, solve = one right-hand side")
     return out
