@@ -4,7 +4,6 @@ solve is the plain inverse Z*.  The paper's periodic example (Sec. 3.3,
 Fig. d1_fa_per): f = sin([N/5] pi x), T = 1, tau0 = 1e-10, maximum error below
 1e-12 and ||a|| / sqrt(N) about 5 (s = 2 and 4 here; the paper uses s = 3)."""
 import math
-import os
 
 import numpy as np
 import pytest
@@ -12,19 +11,11 @@ import pytest
 import workloads as W
 from oracle.az import relres
 from oracle.operators import Operator
+from tests.paper_values import paper_value
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-GOLD = os.path.join(os.path.dirname(__file__), "golden", "paper_values.txt")
-
-
-def paper_value(key):
-    for line in open(GOLD):
-        line = line.split("#")[0].split()
-        if line and line[0] == key:
-            return float(line[1])
-    raise KeyError(key)
 
 
 @pytest.fixture(scope="module")

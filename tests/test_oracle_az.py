@@ -1,7 +1,6 @@
 """Pins for oracle.az: Algorithm 1 against the dense TSVD solve, the paper's
 printed numbers (tests/golden/paper_values.txt) and Theorem 4.6's rank bound."""
 import math
-import os
 
 import numpy as np
 import pytest
@@ -9,16 +8,8 @@ import pytest
 import workloads as W
 from oracle.az import AZ, direct_tsvd, relres
 from oracle.operators import Operator
+from tests.paper_values import paper_value
 
-GOLD = os.path.join(os.path.dirname(__file__), "golden", "paper_values.txt")
-
-
-def paper_value(key):
-    for line in open(GOLD):
-        line = line.split("#")[0].split()
-        if line and line[0] == key:
-            return float(line[1])
-    raise KeyError(key)
 
 
 epsh_from_tau0 = W.epsh_from_tau0
