@@ -57,3 +57,34 @@ def test_mixed_precision_refuses_small_eps_h():
                           C.byref(o), None, C.byref(h))
     assert st == az.AZ_ERR_ARG and not h.value
     assert "AZ_FP64" in az.az_last_error()
+
+
+def _c_struct_fields(src, name):
+    """Member (type, name) pairs of `typedef struct { ... } name;` in the header."""
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    m = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + r"\s*;", src, flags=re.S)
+    assert m, name
+    out = []
+    for decl in m.group(1).split(";"):
+        decl = " ".join(decl.split())
+        if not decl:
+            continue
+        mm = re.match(r"(.+?)\s*\b(\w+)\s*(\[\d+\])?$", decl)
+        out.append((mm.group(1).replace(" ", ""), mm.group(2) + (mm.group(3) or "")))
+    return out
+
+
+def test_ctypes_structs_match_the_header():
+    # the binding's ctypes mirrors of az_grid, az_options and az_info_t have
+    # the header's members in the header's order, with the same widths
+    import ctypes
+    import paper_2308_14490_gb300 as az
+    src = open(os.path.join(ROOT, "include", "az.h")).read()
+    width = {"int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64, "uint64_t": ctypes.c_uint64,
+             "double": ctypes.c_double, "size_t": ctypes.c_size_t, "constdouble*": ctypes.c_void_p}
+    for cname, py in (("az_grid", az.az_grid), ("az_options", az.az_options), ("az_info_t", az.az_info_t)):
+        fields = _c_struct_fields(src, cname)
+        assert [f[1].split("[")[0] for f in fields] == [f[0] for f in py._fields_], cname
+        for (ctype, cfield), (pname, ptype) in zip(fields, py._fields_):
+            n = int(cfield.split("[")[1][:-1]) if "[" in cfield else 1
+            assert ctypes.sizeof(ptype) == n * ctypes.sizeof(width[ctype]), (cname, cfield)
