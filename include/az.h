@@ -113,13 +113,19 @@ typedef struct {
  *   boundary_pts_dev  double, n_boundary x dim row-major (x, y pairs) or NULL.
  *   eps             Gaussian shape parameter (> 0).
  *   kernel          AZ_GAUSS (approximation, Sec. 2-5) or AZ_NEG_LAPLACE_GAUSS
- *                   (Poisson collocation -Lap u = f, Sec. 6.2 with k0 = 0; rows
- *                   divided by 2 eps^2, the normalisation of Example 6.1).
- *   boundary_weight weight w of the Dirichlet rows (collocation), else ignored.
+ *                   (collocation -(Lap + k0^2) u = f, Sec. 6.1-6.3, k0 from the
+ *                   options; rows divided by 2 eps^2, the normalisation of
+ *                   Example 6.1; 1D or 2D).
+ *   boundary_weight weight w of the boundary rows (collocation), else ignored.
  *   opt             options (copied); NULL = defaults.
  *   out             receives the handle.
+ * Omega = the whole box with no boundary rows (and tau_sym = 0) is the periodic
+ * problem of Sec. 3.1: the perturbation is exactly zero, the sketch is skipped
+ * and solves apply Z* alone (rank 0).
  * Synchronises `stream` once (to learn M).  Errors: AZ_ERR_ARG for bad sizes
- * or pointers, AZ_ERR_OOM, AZ_ERR_CUDA, AZ_ERR_NUMERIC. */
+ * or pointers, and for AZ_MIXED with eps h < 0.504 (the FP32 symbol inverse
+ * would amplify rounding past 1e-3; use AZ_FP64), AZ_ERR_OOM, AZ_ERR_CUDA,
+ * AZ_ERR_NUMERIC. */
 az_status az_setup(const az_grid* g, const uint8_t* omega_mask_dev, const double* boundary_pts_dev,
                    int64_t n_boundary, double eps, int32_t kernel, double boundary_weight,
                    const az_options* opt, void* stream, az_handle* out);
