@@ -66,7 +66,12 @@ typedef struct {
 } az_grid;
 
 typedef struct {
-  int32_t precision;    /* AZ_FP64, or AZ_MIXED: FP32 transforms/sketch, FP64 factor work and residual */
+  int32_t precision;    /* AZ_FP64, or AZ_MIXED: FP32 transforms and FP64 factor work and residual.
+                           In 1D the mixed sketch is FP32.  In 2D (dim = 2) the mixed setup sketches
+                           and factorises in FP64 and keeps W in FP64: an FP32 sketch misplaces the
+                           fitted subspace there (relres gaps ~1e-5).  Only the solve's transforms,
+                           stencils and projection then run in FP32, and the update x = z + W u
+                           reads the FP64 W */
   int32_t k;            /* sketch width r + p (number of random columns, Sec. 3.2.3), 1..4096; 0 = adaptive:
                            widths 64, 128, ... until the k-th singular value of the sketch is below
                            1e-7 (FP64) or 1e-4 (mixed) of the largest (az_get_info reports the k used);

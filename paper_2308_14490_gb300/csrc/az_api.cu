@@ -56,6 +56,12 @@ struct az_setup_t {
   void* W = nullptr;    // N x k   (T)
   void* Y = nullptr;    // Mtot x k (T)
   void* Ut = nullptr;   // Mtot x k (T, ld ldm), zero beyond rank
+  // 2D mixed precision: the sketch, its factorisation, W and Ut are FP64 (an
+  // FP32 sketch misplaces the fitted subspace by ~1e-4 sigma_1 in 2D), while
+  // the solve's transforms, stencils and projection run in FP32 on Ut32 and
+  // the update x = z + W u reads the FP64 W
+  bool sk64 = false;
+  float* Ut32 = nullptr; // Mtot x k (FP32 copy of Ut, ld ldm)
   double *G = nullptr, *V = nullptr, *lam = nullptr, *B1 = nullptr, *Tm = nullptr, *VS = nullptr, *sig = nullptr;
   double* partial = nullptr;
   FactorInfo* info = nullptr;
@@ -286,6 +292,16 @@ az_status to_double(const TI* in, int64_t ldi, int64_t rows, int ncols, double* 
   return AZ_OK;
 }
 
+// FP64 matrix -> FP32 copy (same leading dimension)
+__global__ void k_to_float(const double* in, int64_t ld, int64_t rows, int ncols, float* out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int c = blockIdx.y;
+  if (i < rows && c < ncols) out[(int64_t)c * ld + i] = (float)in[(int64_t)c * ld + i];
+}
+
+// precision of the stored sketch, W, Y and Ut (FP64 also for the 2D mixed path)
+bool store64(const az_setup_t* h) { return h->precision == AZ_FP64 || h->sk64; }
+
 // ------------------------------------------------------------------ setup pieces
 // Host-side stencil widths (phi and phi'' taps of one dimension share a width).
 void stencil_widths(az_setup_t* h) {
@@ -472,10 +488,23 @@ az_status sketch_and_factor(az_setup_t* h, cudaStream_t st) {
   return AZ_OK;
 }
 
+// S3-S7 in the storage precision; the 2D mixed path then rounds Ut to FP32
+// for the solve's projection.
+az_status sketch_factor_any(az_setup_t* h, cudaStream_t st) {
+  if (!store64(h)) return sketch_and_factor<float>(h, st);
+  AZ_TRY(sketch_and_factor<double>(h, st));
+  if (h->sk64) {
+    dim3 grid((unsigned)((h->ldm + 255) / 256), h->k);
+    k_to_float<<<grid, 256, 0, st>>>((const double*)h->Ut, h->ldm, h->ldm, h->k, h->Ut32);
+    AZ_CUDA(cudaGetLastError());
+  }
+  return AZ_OK;
+}
+
 az_status compute_setup(az_setup_t* h, cudaStream_t st, bool with_index_map) {
   if (with_index_map) AZ_TRY(launch_compact(h->mask, h->g.L, h->pos2m, h->idx, h->Md, h->scan, st));
   AZ_TRY(build_symbol(h, st));
-  AZ_TRY(h->precision == AZ_FP64 ? sketch_and_factor<double>(h, st) : sketch_and_factor<float>(h, st));
+  AZ_TRY(sketch_factor_any(h, st));
   if (h->info_ev) AZ_CUDA(cudaEventRecord(h->info_ev, st));
   return AZ_OK;
 }
@@ -501,20 +530,29 @@ az_status az_once(az_setup_t* h, const TB* b, int64_t ldb, int ncols, double* x,
     AZ_CUDA(cudaStreamWaitEvent(st, h->ev_fac, 0));
     h->fac_pending = false;
   }
+  // the FP32 projection basis: Ut itself, or the FP32 copy of the FP64 Ut
+  const T* Ub = h->sk64 ? (const T*)h->Ut32 : (const T*)h->Ut;
+  const bool w64 = h->sk64 || Prec<T>::fp64;
   if (h->wide) {
-    AZ_TRY(large_project(h->wide, h->Ut, h->ldm, gg, h->ldm, ncols, h->cb, st));
+    AZ_TRY(large_project(h->wide, Ub, h->ldm, gg, h->ldm, ncols, h->cb, st, !Prec<T>::fp64));
     AZ_TRY(launch_small_mm(h->VS, h->k, h->cb, ncols, h->ub, st));
-    AZ_TRY(large_update(h->wide, h->W, g.N, h->ub, z, g.N, g.N, ncols, x, ldx, accumulate, st));
+    AZ_TRY(large_update(h->wide, h->W, g.N, h->ub, z, g.N, g.N, ncols, x, ldx, accumulate, st, w64,
+                        !Prec<T>::fp64));
     return AZ_OK;
   }
-  if (!Prec<T>::fp64 && tc_tsgram_ok(h->Ut, h->ldm, h->k, gg, h->ldm, ncols)) {
+  if (!Prec<T>::fp64 && tc_tsgram_ok(Ub, h->ldm, h->k, gg, h->ldm, ncols)) {
     // c = U_tau^T g on the tensor cores (split TF32, FP32-level accuracy)
-    AZ_TRY(launch_tc_tsgram((const float*)h->Ut, h->ldm, h->k, (const float*)gg, h->ldm, ncols, h->Mtot, h->partial,
+    AZ_TRY(launch_tc_tsgram((const float*)Ub, h->ldm, h->k, (const float*)gg, h->ldm, ncols, h->Mtot, h->partial,
                             h->cb, h->tc_err, st));
   } else {
-    AZ_TRY((launch_gram<T, T>((const T*)h->Ut, h->ldm, h->k, gg, h->ldm, ncols, h->Mtot, h->partial, h->cb, st, true)));
+    AZ_TRY((launch_gram<T, T>(Ub, h->ldm, h->k, gg, h->ldm, ncols, h->Mtot, h->partial, h->cb, st, true)));
   }
   AZ_TRY(launch_small_mm(h->VS, h->k, h->cb, ncols, h->ub, st));
+  if (h->sk64 && !Prec<T>::fp64) {
+    // x = z + W u with the FP64 W (the sketch's own precision), FP32 z
+    return launch_update_x<double, float>((const double*)h->W, g.N, h->k, h->ub, (const float*)z, g.N, g.N, ncols,
+                                          x, ldx, accumulate, st);
+  }
   AZ_TRY((launch_update_x<T, T>((const T*)h->W, g.N, h->k, h->ub, z, g.N, g.N, ncols, x, ldx, accumulate, st,
                                 Prec<T>::fp64 ? nullptr : xf_out, Prec<T>::fp64 ? nullptr : xbase)));
   return AZ_OK;
@@ -532,7 +570,9 @@ az_status solve_impl(az_setup_t* h, const double* b, int64_t ldb, int64_t nrhs, 
     // its result only as the exact FP32 copy, and the second forms
     // x = x1 + dx directly (one FP64 write of x instead of a write, a read
     // and a write)
-    const bool mixed = !Prec<T>::fp64;
+    // (the 2D mixed path updates x with the FP64 W: x is not FP32 after the
+    // first pass, and its residual is the plain FP64 one below)
+    const bool mixed = !Prec<T>::fp64 && !h->sk64;
     // (the wide path leaves the FP32 first-pass result in the z buffer instead)
     const bool defer = mixed && h->refine > 0 && h->Mb == 0 && !h->wide;
     AZ_TRY((az_once<T, double>(h, bc, ldb, nc, defer ? nullptr : xc, ldx, false, st,
@@ -540,7 +580,7 @@ az_status solve_impl(az_setup_t* h, const double* b, int64_t ldb, int64_t nrhs, 
     const float* x1f = h->wide ? (const float*)h->zb : h->xfb;
     for (int it = 0; it < h->refine; ++it) {
       T* res = (T*)h->rb;
-      if (!Prec<T>::fp64 && it == 0) {
+      if (mixed && it == 0) {
         // r = b - A x, FP64-accurate: x is exactly FP32 after the first pass, so
         // double-FP32 arithmetic on the split FP64 taps reproduces the FP64
         // residual (about 48 significant bits) at FP32 throughput
@@ -584,7 +624,9 @@ az_status solve_impl(az_setup_t* h, const double* b, int64_t ldb, int64_t nrhs, 
 
 az_status alloc_workspace(az_setup_t* h) {
   const Geom& g = h->g;
-  const size_t vsz = h->precision == AZ_FP64 ? 16 : 8, tsz = vsz / 2;
+  // (sized for the storage precision: the 2D mixed path runs its sketch chain
+  // in FP64 on the same workspace as its FP32 solves)
+  const size_t vsz = store64(h) ? 16 : 8, tsz = vsz / 2;
   const size_t per_pair = (size_t)(g.L + g.N) * vsz;
   int pm = std::max(32, (h->k + 1) / 2);
   while (pm > 1 && per_pair * pm > (size_t)3 << 30) pm /= 2;
@@ -595,7 +637,7 @@ az_status alloc_workspace(az_setup_t* h) {
   AZ_TRY(dalloc(h, &h->zb, (size_t)g.N * cols * tsz));
   AZ_TRY(dalloc(h, &h->gb, (size_t)h->ldm * cols * tsz));
   AZ_TRY(dalloc(h, &h->rb, (size_t)h->Mtot * cols * tsz));
-  if (h->precision == AZ_MIXED) AZ_TRY(dalloc_t(h, &h->xfb, (size_t)g.N * cols));
+  if (h->precision == AZ_MIXED && !h->sk64) AZ_TRY(dalloc_t(h, &h->xfb, (size_t)g.N * cols));
   AZ_TRY(dalloc_t(h, &h->cb, (size_t)h->k * cols));
   AZ_TRY(dalloc_t(h, &h->ub, (size_t)h->k * cols));
   AZ_TRY(dalloc_t(h, &h->normb, (size_t)2 * cols));
@@ -647,7 +689,9 @@ az_status az_query_footprint(const az_grid* gr, int64_t M, int64_t n_boundary, c
   AZ_TRY(make_geom(gr, g));
   const int prec = opt ? opt->precision : AZ_MIXED;
   const int k = opt ? opt->k : 24;
-  const size_t vsz = prec == AZ_FP64 ? 16 : 8, tsz = vsz / 2;
+  // (2D mixed setups store the sketch and factors in FP64 and add an FP32 Ut)
+  const bool s64 = prec == AZ_FP64 || g.dim == 2;
+  const size_t vsz = s64 ? 16 : 8, tsz = vsz / 2;
   const int64_t Mt = M + n_boundary;
   int pm = (int)std::max<int64_t>(std::max<int64_t>(1, (nrhs_max + 1) / 2), (k + 1) / 2);
   size_t b = 0;
@@ -656,6 +700,7 @@ az_status az_query_footprint(const az_grid* gr, int64_t M, int64_t n_boundary, c
   b += (size_t)((g.N + 31) / 32) * 4 * k;           // bits
   const int64_t ldm = (Mt + 31) / 32 * 32;
   b += (size_t)g.N * k * tsz + (size_t)(Mt + ldm) * k * tsz;  // W, Y, Ut
+  if (prec == AZ_MIXED && g.dim == 2) b += (size_t)ldm * k * 4;  // Ut FP32 copy
   b += (size_t)pm * (g.L + g.N) * vsz;              // X1, X3
   const int cols = std::max(2 * pm, k);
   b += (size_t)g.N * cols * tsz + (size_t)(Mt + ldm) * cols * tsz;
@@ -699,7 +744,8 @@ az_status az_setup(const az_grid* gr, const uint8_t* mask, const double* bpts, i
   *out = nullptr;
   int64_t N = 1;
   for (int d = 0; d < gr->dim && d < 2; ++d) N *= gr->n[d];
-  const double tsat = opt->precision == AZ_FP64 ? 1e-7 : 1e-4;
+  // (2D mixed setups sketch in FP64, so they take the FP64 level)
+  const double tsat = (opt->precision == AZ_FP64 || (gr->dim == 2)) ? 1e-7 : 1e-4;
   az_options o = *opt;
   az_handle prev = nullptr;   // the narrower setup, whose sketch columns are reused
   for (int k = 64;; k *= 2) {
@@ -745,6 +791,7 @@ static az_status setup_fixed(const az_grid* gr, const uint8_t* mask, const doubl
   cudaStream_t st = (cudaStream_t)stream;
   h->kind = kernel == AZ_NEG_LAPLACE_GAUSS ? 1 : 0;
   h->precision = o.precision;
+  h->sk64 = o.precision == AZ_MIXED && h->g.dim == 2;
   h->k = o.k;
   h->eps = eps;
   h->tau_svd = o.tau_svd > 0 ? o.tau_svd : 1e-8;
@@ -811,10 +858,11 @@ static az_status setup_fixed(const az_grid* gr, const uint8_t* mask, const doubl
     rc = alloc_symbol(h); if (rc) break;
     h->nw = (g.N + 31) / 32;
     rc = dalloc_t(h, &h->bits, (size_t)h->nw * h->k + 4); if (rc) break;
-    const size_t tsz = h->precision == AZ_FP64 ? 8 : 4;
+    const size_t tsz = store64(h) ? 8 : 4;
     rc = dalloc(h, &h->W, (size_t)g.N * h->k * tsz); if (rc) break;
     rc = dalloc(h, &h->Y, (size_t)h->Mtot * h->k * tsz); if (rc) break;
     rc = dalloc(h, &h->Ut, (size_t)h->ldm * h->k * tsz); if (rc) break;
+    if (h->sk64) { rc = dalloc_t(h, &h->Ut32, (size_t)h->ldm * h->k); if (rc) break; }
     rc = dalloc_t(h, &h->tc_err, 1); if (rc) break;
     if (cudaEventCreateWithFlags(&h->info_ev, cudaEventDisableTiming) != cudaSuccess) { cudaGetLastError(); set_error("event"); rc = AZ_ERR_CUDA; break; }
     if (cudaMemsetAsync(h->tc_err, 0, sizeof(int), st) != cudaSuccess) { cudaGetLastError(); set_error("memset"); rc = AZ_ERR_CUDA; break; }
@@ -826,11 +874,11 @@ static az_status setup_fixed(const az_grid* gr, const uint8_t* mask, const doubl
     rc = dalloc_t(h, &h->sig, h->k); if (rc) break;
     rc = dalloc_t(h, &h->info, 1); if (rc) break;
     rc = alloc_workspace(h); if (rc) break;
-    if (h->kind == 0 && !h->periodic && h->k <= kNarrowK && !(h->precision == AZ_FP64 && h->tau_svd < kGramTau)) {
+    if (h->kind == 0 && !h->periodic && h->k <= kNarrowK && !(store64(h) && h->tau_svd < kGramTau)) {
       // overlap of az_refactor's sketch with the next solve: own stream,
       // events and FFT workspace for the sketch chain
       h->pairs_s = std::min(h->pairs_max, (h->k + 1) / 2);
-      const size_t vsz = h->precision == AZ_FP64 ? 16 : 8;
+      const size_t vsz = store64(h) ? 16 : 8;
       rc = dalloc(h, &h->X1s, (size_t)h->pairs_s * g.L * vsz); if (rc) break;
       rc = dalloc(h, &h->X3s, (size_t)h->pairs_s * g.N * vsz); if (rc) break;
       // higher priority: the sketch-to-factor chain is the critical path, and
@@ -847,9 +895,9 @@ static az_status setup_fixed(const az_grid* gr, const uint8_t* mask, const doubl
     // The Gram route squares the sketch's condition number, so in FP64 it
     // resolves singular values down to about 1e-8 sigma_1; a tighter tau
     // takes the Householder route whatever the width.
-    if (h->k > kNarrowK || (h->precision == AZ_FP64 && h->tau_svd < kGramTau)) {
+    if (h->k > kNarrowK || (store64(h) && h->tau_svd < kGramTau)) {
       size_t wb = 0;
-      rc = large_create(&h->wide, h->Mtot, h->k, h->precision == AZ_FP64, h->Q1, &wb);
+      rc = large_create(&h->wide, h->Mtot, h->k, store64(h), h->Q1, &wb);
       h->bytes += wb;
       if (rc) break;
     } else {
@@ -870,14 +918,14 @@ static az_status setup_fixed(const az_grid* gr, const uint8_t* mask, const doubl
         reuse->g.N == g.N && reuse->Mtot == h->Mtot && !h->periodic) {
       // adaptive growth: the first reuse->k columns of R, hence of W and Y,
       // are those of the narrower setup (same seed, same geometry)
-      const size_t tsz = h->precision == AZ_FP64 ? 8 : 4;
+      const size_t tsz = store64(h) ? 8 : 4;
       if (cudaMemcpyAsync(h->W, reuse->W, (size_t)g.N * reuse->k * tsz, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
           cudaMemcpyAsync(h->Y, reuse->Y, (size_t)h->Mtot * reuse->k * tsz, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
         cudaGetLastError(); set_error("az_setup: sketch column copy"); rc = AZ_ERR_CUDA; break;
       }
       h->k_done = reuse->k;
     }
-    rc = h->precision == AZ_FP64 ? sketch_and_factor<double>(h, st) : sketch_and_factor<float>(h, st);
+    rc = sketch_factor_any(h, st);
     if (rc) break;
     FactorInfo fi;
     if (cudaMemcpyAsync(&fi, h->info, sizeof(fi), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -905,8 +953,7 @@ az_status az_refactor(az_handle h, uint64_t seed, void* stream) {
   AZ_TRY(build_symbol(h, st));
   AZ_CUDA(cudaEventRecord(h->ev_sym, st));
   AZ_CUDA(cudaStreamWaitEvent(h->fst, h->ev_sym, 0));
-  const az_status rc = h->precision == AZ_FP64 ? sketch_and_factor<double>(h, h->fst)
-                                               : sketch_and_factor<float>(h, h->fst);
+  const az_status rc = sketch_factor_any(h, h->fst);
   // recorded whatever happened, so that later calls wait for whatever was
   // enqueued before an error
   AZ_CUDA(cudaEventRecord(h->info_ev, h->fst));
@@ -996,7 +1043,7 @@ az_status az_get_array(az_handle h, int32_t which, double* dst, void* stream) {
   if (!h || !dst) { set_error("az_get_array: bad arguments"); return AZ_ERR_ARG; }
   cudaStream_t st = (cudaStream_t)stream;
   if (h->fac_pending) AZ_CUDA(cudaStreamWaitEvent(st, h->ev_fac, 0));
-  const bool f64 = h->precision == AZ_FP64;
+  const bool f64 = store64(h);
   switch (which) {
     case AZ_ARRAY_SYMBOL:
       AZ_CUDA(cudaMemcpyAsync(dst, h->Ghat, h->g.L * sizeof(double), cudaMemcpyDeviceToDevice, st));

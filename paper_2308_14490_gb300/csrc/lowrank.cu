@@ -936,5 +936,6 @@ template az_status launch_tsprod<double, float>(const double*, int64_t, int, con
 template az_status launch_tsprod<float, float>(const float*, int64_t, int, const double*, int, int64_t, float*, int64_t, cudaStream_t);
 template az_status launch_update_x<float, float>(const float*, int64_t, int, const double*, const float*, int64_t, int64_t, int, double*, int64_t, bool, cudaStream_t, float*, const float*);
 template az_status launch_update_x<double, double>(const double*, int64_t, int, const double*, const double*, int64_t, int64_t, int, double*, int64_t, bool, cudaStream_t, float*, const float*);
+template az_status launch_update_x<double, float>(const double*, int64_t, int, const double*, const float*, int64_t, int64_t, int, double*, int64_t, bool, cudaStream_t, float*, const float*);
 
 }  // namespace az

@@ -204,12 +204,13 @@ __global__ void k_d2f_cols(const double* __restrict__ a, int n, float* __restric
   if (t < n) b[t] = (float)a[t];
 }
 
-// c[k x n] = Ut^T g   (FP64 result)
+// c[k x n] = Ut^T g   (FP64 result); f32: Ut and g are FP32 (the mixed
+// path's projection), else FP64
 az_status large_project(LargeK* L, const void* Ut, int64_t ldu, const void* g, int64_t ldg, int n, double* c,
-                        cudaStream_t st) {
-  ProfScope ps("wide_proj", (double)L->M * (L->k + n) * (L->fp64 ? 8 : 4), st);
+                        cudaStream_t st, bool f32) {
+  ProfScope ps("wide_proj", (double)L->M * (L->k + n) * (f32 ? 4 : 8), st);
   AZ_BLAS(cublasSetStream(L->blas, st));
-  if (L->fp64) {
+  if (!f32) {
     const double one = 1, zero = 0;
     AZ_BLAS(cublasDgemm(L->blas, CUBLAS_OP_T, CUBLAS_OP_N, L->k, n, (int)L->M, &one, (const double*)Ut, (int)ldu,
                         (const double*)g, (int)ldg, &zero, c, L->k));
@@ -235,11 +236,23 @@ __global__ void k_store_x(const float* __restrict__ zf, int64_t ldz, const doubl
 
 // z += W u (in place, in the precision of W), then x (=|+=) z.  In the mixed
 // path z then holds the exact FP32 value of the new solution increment.
+// w64 with z32 (the FP64-sketch mixed path): x (=|+=) z first, then x += W u in
+// FP64, so that the update is consistent with the FP64 sketch Y = A W.
 az_status large_update(LargeK* L, const void* W, int64_t ldw, const double* u, void* z, int64_t ldz, int64_t N, int n,
-                       double* x, int64_t ldx, bool accumulate, cudaStream_t st) {
-  ProfScope ps("wide_update", (double)N * (L->k + 2 * n) * (L->fp64 ? 8 : 4) + (double)N * n * 8 * (accumulate ? 2 : 1), st);
+                       double* x, int64_t ldx, bool accumulate, cudaStream_t st, bool w64, bool z32) {
+  ProfScope ps("wide_update", (double)N * (L->k * (w64 ? 8 : 4) + 2 * n * (z32 ? 4 : 8)) +
+                                  (double)N * n * 8 * (accumulate ? 2 : 1), st);
   AZ_BLAS(cublasSetStream(L->blas, st));
-  if (L->fp64) {
+  dim3 grid((unsigned)((N + 255) / 256), n);
+  if (w64 && z32) {
+    k_store_x<<<grid, 256, 0, st>>>((const float*)z, ldz, nullptr, N, x, ldx, accumulate ? 1 : 0);
+    AZ_CUDA(cudaGetLastError());
+    const double one = 1;
+    AZ_BLAS(cublasDgemm(L->blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)N, n, L->k, &one, (const double*)W, (int)ldw, u, L->k,
+                        &one, x, (int)ldx));
+    return AZ_OK;
+  }
+  if (w64) {
     const double one = 1;
     AZ_BLAS(cublasDgemm(L->blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)N, n, L->k, &one, (const double*)W, (int)ldw, u, L->k,
                         &one, (double*)z, (int)ldz));
@@ -249,8 +262,7 @@ az_status large_update(LargeK* L, const void* W, int64_t ldw, const double* u, v
     AZ_BLAS(cublasSgemm(L->blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)N, n, L->k, &one, (const float*)W, (int)ldw,
                         (const float*)L->u32, L->k, &one, (float*)z, (int)ldz));
   }
-  dim3 grid((unsigned)((N + 255) / 256), n);
-  k_store_x<<<grid, 256, 0, st>>>(L->fp64 ? nullptr : (const float*)z, ldz, L->fp64 ? (const double*)z : nullptr, N, x,
+  k_store_x<<<grid, 256, 0, st>>>(w64 ? nullptr : (const float*)z, ldz, w64 ? (const double*)z : nullptr, N, x,
                                   ldx, accumulate ? 1 : 0);
   AZ_CUDA(cudaGetLastError());
   return AZ_OK;

@@ -78,7 +78,8 @@ def test_sketch_2d(az, p, prec):
         ref = AZ(op, p.k, 11, 1e-8)
         Wg = gu.get_array(h, az.AZ_ARRAY_W, p.k, op.N)
         Wref = ref.R - op.Zstar(op.A(ref.R))
-        tol = 1e-11 if prec == "fp64" else 5e-6
+        # (2D mixed setups sketch in FP64 as well)
+        tol = 1e-11
         assert np.abs(Wg - Wref).max() <= tol * np.abs(Wref).max()
         Yg = gu.get_array(h, az.AZ_ARRAY_SKETCH, p.k, op.M + op.Mb)
         assert np.abs(Yg - ref.Y).max() <= tol * np.abs(ref.Y).max()
@@ -106,6 +107,31 @@ def test_solve_2d_fp64_parity(az, p):
     r_o = relres(op, AZ(op, p.k, 11, 1e-8).solve(b), b)
     r_g = relres(op, xg, b)
     assert np.all(np.abs(r_g - r_o) <= 1e-10), (r_g.tolist(), r_o.tolist())
+    assert np.allclose(rr, r_g, rtol=1e-8, atol=1e-14)
+
+
+@pytest.mark.parametrize("p", _cases(), ids=lambda p: p.name)
+def test_solve_2d_mixed_parity(az, p):
+    """The mixed path (FP64 sketch and factors in 2D, FP32 transforms, stencils
+    and projection in the solve, one FP64-residual refinement) against the
+    oracle's Algorithm 1 with the same R, k, tau and one refinement: 1e-8.
+    Collocation setups go through az_collocate (its row scaling)."""
+    gu = _gu()
+    op = _op(p)
+    b = _rhs(p, op)
+    h = gu.setup(p, az.AZ_MIXED, seed=11, refine=1)
+    try:
+        x = torch.zeros((b.shape[1], op.N), dtype=torch.float64, device=gu.dev())
+        if p.kind == "poisson":
+            rr = az.az_collocate(h, gu.to_dev_cols(p.rhs()), gu.to_dev_cols(p.boundary_rhs()), x, relres=True)
+        else:
+            rr = az.az_solve(h, gu.to_dev_cols(b), x, relres=True)
+        xg = gu.from_dev_cols(x)
+    finally:
+        az.az_destroy(h)
+    r_o = relres(op, AZ(op, p.k, 11, 1e-8).solve(b, refine=1), b)
+    r_g = relres(op, xg, b)
+    assert np.all(np.abs(r_g - r_o) <= 1e-8), (r_g.tolist(), r_o.tolist())
     assert np.allclose(rr, r_g, rtol=1e-8, atol=1e-14)
 
 

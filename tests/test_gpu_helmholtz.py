@@ -78,9 +78,10 @@ def test_helmholtz_fine_grid_error_and_mixed(az):
     err_64 = np.abs(out[az.AZ_FP64][1] - u)[inside].max()
     err_32 = np.abs(out[az.AZ_MIXED][1] - u)[inside].max()
     assert err_64 <= max(1.01 * err_o, err_o + 1e-9)
-    # k = 64 under-resolves this grid (the residual is ~1e-3), so the FP32
-    # sketch's noise enters at first order; the mixed error stays at the same level
-    assert err_32 <= 1.1 * err_64 + 1e-9
-    r64 = relres(op, out[az.AZ_FP64][0], b)
+    # 2D mixed: FP64 sketch and factors, FP32 solve + one FP64-residual
+    # refinement; against the oracle with the same refinement the residual
+    # meets the 1e-8 bar and the fine-grid error stays at the FP64 level
+    assert err_32 <= 1.01 * err_64 + 1e-8
     r32 = relres(op, out[az.AZ_MIXED][0], b)
-    assert np.all(r32 <= 1.1 * r64 + 1e-8)
+    r_o1 = relres(op, AZ(op, p.k, 11, 1e-8).solve(b, refine=1), b)
+    assert np.all(np.abs(r32 - r_o1) <= 1e-8), (r32.tolist(), r_o1.tolist())
