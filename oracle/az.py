@@ -32,18 +32,26 @@ from .philox import rademacher
 class AZ:
     """Reference AZ loop for one Operator (see oracle.operators)."""
 
-    def __init__(self, op, k: int, seed: int, tau: float = 1e-12):
+    def __init__(self, op, k: int, seed: int, tau: float = 1e-12, chunk: int = 0):
+        """chunk > 0 forms the sketch `chunk` columns at a time (the columns are
+        independent; this only bounds the host memory of the FFTs)."""
         self.op = op
         self.k = k
         self.seed = seed
         self.tau = tau
         self.R = rademacher(op.N, k, seed)
-        AR = op.A(self.R)
-        # Y = (I - A Z*) A R, one column per random vector (Sec. 3.2.3).
-        self.Y = AR - op.A(op.Zstar(AR))
+        step = chunk if chunk > 0 else k
+        self.Y = np.empty((op.M + op.Mb, k))
+        ar2 = 0.0
+        for c0 in range(0, k, step):
+            AR = op.A(self.R[:, c0:c0 + step])
+            # Y = (I - A Z*) A R, one column per random vector (Sec. 3.2.3).
+            self.Y[:, c0:c0 + step] = AR - op.A(op.Zstar(AR))
+            ar2 += float(np.sum(AR * AR))
+            del AR
         U, sig, Vt = np.linalg.svd(self.Y, full_matrices=False)
         self.sig = sig
-        floor = 1e-13 * np.linalg.norm(AR)
+        floor = 1e-13 * np.sqrt(ar2)
         self.rank = int(np.sum(sig > max(tau * sig[0], floor)))
         r = self.rank
         self.U = U[:, :r]

@@ -37,9 +37,17 @@ boundary weight like the Dirichlet rows; the data du/dn is scaled the same way.
 Reading of the symbol truncation: S_k^{-1} is replaced by 0 when
 S_k <= tau_sym^2 * max S (tau_sym = 0 gives the exact pseudo-inverse).
 """
+import os
+
 import numpy as np
+import scipy.fft as sfft
 
 from . import rbf
+
+# The DFTs of Sec. 3.1 (F, and the per-dimension transforms of Sec. 5.1) are
+# library FFTs; they run on every host core (the transform is the same one
+# numpy.fft computes, up to rounding).
+WORKERS = os.cpu_count() or 1
 
 
 class Operator:
@@ -110,9 +118,9 @@ class Operator:
         a = np.asarray(a, dtype=np.float64)
         a2 = self._to_grid(a, self.n)
         axes = tuple(range(self.dim))
-        ah = np.fft.fftn(a2, axes=axes)
+        ah = sfft.fftn(a2, axes=axes, workers=WORKERS)
         G = self.Ghat.reshape(*self.L, 1)
-        v = np.fft.ifftn(G * self._tile(ah), axes=axes).real
+        v = sfft.ifftn(G * self._tile(ah), axes=axes, workers=WORKERS).real
         return v.reshape(self.Ltot, -1)
 
     def boundary_rows(self, a):
@@ -200,10 +208,10 @@ class Operator:
     def Zstar_grid(self, yL):
         """pinv(A^c) applied to a full L-grid array (Ltot, ncol) -> (N, ncol)."""
         axes = tuple(range(self.dim))
-        Y = np.fft.fftn(self._to_grid(yL, self.L), axes=axes)
+        Y = sfft.fftn(self._to_grid(yL, self.L), axes=axes, workers=WORKERS)
         G = self.Ghat.reshape(*self.L, 1)
         ah = self._fold(G * Y) * self.Sinv.reshape(*self.n, 1)
-        return np.fft.ifftn(ah, axes=axes).real.reshape(self.N, -1)
+        return sfft.ifftn(ah, axes=axes, workers=WORKERS).real.reshape(self.N, -1)
 
     def Zstar(self, y):
         """Z* y = F B^dagger P E y (zero columns for boundary rows)."""
