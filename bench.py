@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparator", action="store_true")
-    ap.add_argument("--no-paper-examples", action="store_true")
+    ap.add_argument("--no-context", action="store_true", help="skip the config 1/3/4 context legs")
     ap.add_argument("--nrhs", type=int, default=NRHS, help="right-hand sides per step (default: the workload's 64)")
     ap.add_argument("--serving-seconds", type=float, default=5.0,
                     help="length of the serving-stream sample (Poisson arrivals, 200 req/s); 0 skips it")
@@ -110,10 +110,33 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- oracle legs
+def host_cpu():
+    """CPU model and core count of this host (lscpu), for the CPU legs."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() in ("Model name", "Model"):
+                v = ln.split(":", 1)[1].strip()
+                if v and not v.isdigit():
+                    model = v
+                    break
+    except Exception:
+        pass
+    return {"cores": os.cpu_count() or 1, "model": model or "unknown"}
+
+
+def _pool_init():
+    # every host core for the oracle: BLAS threads (set before numpy loads in
+    # this fresh process) and scipy.fft workers (oracle.operators.WORKERS)
+    n = str(os.cpu_count() or 1)
+    for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = n
+
+
 def _oracle_sample(n_rhs_timed, out_q=None):
     """Run the CPU oracle on the full workload: setup once + n_rhs_timed solves."""
-    import numpy as np
-    import workloads as W
+    import workloads as W  # noqa: F401
     from oracle.az import AZ
     from oracle.operators import Operator
     p = problem()
@@ -125,42 +148,55 @@ def _oracle_sample(n_rhs_timed, out_q=None):
     times = []
     for j in range(n_rhs_timed):
         t1 = time.perf_counter()
-        az.solve(b[:, j:j + 1], refine=1)
+        az.solve(b[:, j % b.shape[1]:j % b.shape[1] + 1], refine=1)
         times.append(time.perf_counter() - t1)
     return t_setup, times
 
 
-def cpu_baseline_leg():
+def _oracle_pool():
     import multiprocessing as mp
-    ctx = mp.get_context("spawn")
-    with ctx.Pool(1) as pool:
-        t_setup, times = pool.apply(_oracle_sample, (2,))
-    t_rhs = sum(times) / len(times)
+    return mp.get_context("spawn").Pool(1, initializer=_pool_init)
+
+
+def cpu_baseline_leg():
+    with _oracle_pool() as pool:
+        t_setup, times = pool.apply(_oracle_sample, (3,))
+    t_rhs = sum(times[1:]) / len(times[1:])
     value = NRHS / (t_setup + NRHS * t_rhs)
-    return {"value": value, "unit": "RHS/s", "cores": 1, "kind": "oracle",
-            "sample": f"full-size oracle setup ({t_setup:.1f} s) + 2 of the 64 RHS ({t_rhs:.2f} s each, 1 refinement); "
-                      f"value = 64 / (t_setup + 64 t_rhs); numpy FFT single-threaded"}
+    cpu = host_cpu()
+    return {"value": value, "unit": "RHS/s", "cores": cpu["cores"], "cpu_model": cpu["model"], "kind": "oracle",
+            "sample": f"full-size oracle setup ({t_setup:.2f} s) + 2 of the 64 RHS after one warm-up RHS "
+                      f"({t_rhs:.3f} s each, 1 refinement); value = 64 / (t_setup + 64 t_rhs), the step shape of "
+                      f"the GPU arm; scipy.fft workers and BLAS threads = {cpu['cores']} cores"}
 
 
 def run_reference(args):
+    """The oracle on the host cores.  One timed step = one of the workload's
+    right-hand sides solved and refined (what the oracle can finish in well
+    under a second); the setup (index map, symbol, sketch, factorisation) is
+    timed once before the warm-up.  value = 64 / (t_setup + 64 t_rhs): the
+    step shape of the GPU arm (setup + 64 right-hand sides) from the two
+    measured parts; ms_per_step x steps is the timed region."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    import multiprocessing as mp
-    ctx = mp.get_context("spawn")
-    with ctx.Pool(1) as pool:
+    with _oracle_pool() as pool:
         t_setup, times = pool.apply(_oracle_sample, (args.warmup + args.steps,))
     timed = times[args.warmup:]
     t_rhs = sum(timed) / len(timed)
     value = NRHS / (t_setup + NRHS * t_rhs)
-    ms_step = 1000.0 * (t_setup + NRHS * t_rhs)
+    cpu = host_cpu()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t_rhs, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD + " (oracle: FP64 throughout)", "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": value, "unit": "RHS/s", "cores": 1, "kind": "oracle",
-                             "sample": f"setup once ({t_setup:.1f} s), then one RHS per step "
-                                       f"({t_rhs:.2f} s avg over {len(timed)} steps)"},
+            "step": "one right-hand side solved + 1 refinement (setup timed once before the warm-up)",
+            "setup_ms": 1000.0 * t_setup,
+            "config": {"workload": WORKLOAD, "l2": "n/a (CPU)", "oracle": "FP64 throughout"},
+            "cpu_baseline": {"value": value, "unit": "RHS/s", "cores": cpu["cores"], "cpu_model": cpu["model"],
+                             "kind": "oracle",
+                             "sample": f"setup once ({t_setup:.2f} s), then one RHS per step "
+                                       f"({t_rhs:.3f} s avg over {len(timed)} steps); value = 64 / (t_setup + 64 t_rhs); "
+                                       f"scipy.fft workers and BLAS threads = {cpu['cores']} cores"},
             "e2e": {"value": value, "unit": "RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -231,74 +267,143 @@ def fp64_torch_comparator(p, b_dev, steps=2, warmup=1):
 
 
 # --------------------------------------------------------------------------- serving sample
-def paper_examples_leg():
-    """The paper's own 1D examples at its shape parameter (Eq. constant_shapeparam,
-    tau0 = 1e-10, eps h = 0.327), all-FP64 on the GPU, at N = 2^20 for the two
-    approximation problems (Sec. 3.3: the paper notes its Matlab AZ stays under
-    10 s up to N = 1e6 on a laptop) and N = 2^16 for the ODE of Example 6.1.
-    Context beside the headline: setup and solve times and the maximum error
-    against the closed-form function on a 4x finer grid inside the domain."""
-    import math
+def _latency(ms):
+    ms = sorted(ms)
+    return {"p50": ms[len(ms) // 2], "p99": ms[min(len(ms) - 1, int(0.99 * len(ms)))], "max": ms[-1]}
+
+
+def config1_leg(reps=100):
+    """Config 1 (1D, N = 256, Omega = [-0.5, 0.5], k = 20, FP64 only): latency of
+    one whole AZ call -- az_refactor (index map, symbol, sketch, factorisation)
+    and az_solve of its one right-hand side -- on the host clock, synchronised."""
     import numpy as np
     import torch
     import paper_2308_14490_gb300 as az
     import workloads as W
     dev = torch.device("cuda", 0)
-    epsh = W.epsh_from_tau0(1e-10)
-    out = {}
-
-    def timed(fn):
+    p = W.config1()
+    g = p.grid
+    mask = torch.from_numpy(p.mask).to(dev)
+    b = torch.from_numpy(np.ascontiguousarray(p.rhs().T)).to(dev)
+    x = torch.zeros((1, g.N), dtype=torch.float64, device=dev)
+    opts = az.make_options(az.AZ_FP64, p.k, 1e-8, 0.0, 7, 0)
+    h = az.az_setup(az.make_grid(1, g.n, g.s, g.T), mask, g.eps, options=opts)
+    ms = []
+    for i in range(reps + 5):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        r = fn()
+        az.az_refactor(h, 7, None)
+        az.az_solve(h, b, x)
         torch.cuda.synchronize(dev)
-        return r, 1000.0 * (time.perf_counter() - t0)
+        if i >= 5:
+            ms.append(1000.0 * (time.perf_counter() - t0))
+    rr = az.az_solve(h, b, x, relres=True)
+    az.az_destroy(h)
+    return {"what": "1D N=256 Omega=[-0.5,0.5] k=20 FP64: az_refactor + az_solve (1 RHS), host clock, synchronised",
+            "latency_ms": _latency(ms), "calls": reps, "relres": rr[0]}
 
-    cases = []
-    N = 1 << 20
-    fq = math.floor(N / 5)
-    g = W.Grid(1, (N,), (2,), (1.0,), epsh)
-    cases.append(("periodic_sin_fq_pi_x", g, np.ones(g.Ltot, np.uint8), lambda q: np.sin(fq * math.pi * q), 64,
-                  (-1.0, 1.0), None))
-    g = W.Grid(1, (N,), (2,), (1.5,), epsh)
-    cases.append(("nonperiodic_sin_Nx_over_5", g, W.interval_mask(g, -1.0, 1.0), lambda q: np.sin(N / 5.0 * q), 128,
-                  (-1.0, 1.0), None))
-    ode = W.ode(n=1 << 16, k=64)
-    cases.append(("ode_example_6_1", ode.grid, ode.mask, lambda q: np.sin(ode.k0 * q), 64, (-1.0, 1.0), ode))
-    for name, g, m, f, k, (a, b_), prob in cases:
-        for rep in range(2):   # the first pass loads the kernels this case uses; the second is reported
-            try:
-                opts = az.make_options(az.AZ_FP64, k, 1e-12, 0.0, 1, 0, prob.k0 if prob is not None else 0.0)
-                mask = torch.from_numpy(np.ascontiguousarray(m)).to(dev)
-                grid = az.make_grid(1, g.n, g.s, g.T)
-                if prob is None:
-                    pts = W.kept_points(g, m)[:, 0]
-                    b = torch.from_numpy(np.ascontiguousarray(f(pts)[None, :])).to(dev)
-                    h, setup_ms = timed(lambda: az.az_setup(grid, mask, g.eps, options=opts))
-                    x = torch.zeros((1, g.N), dtype=torch.float64, device=dev)
-                    _, solve_ms = timed(lambda: az.az_solve(h, b, x))
-                else:
-                    bpts = torch.from_numpy(np.ascontiguousarray(prob.boundary)).to(dev)
-                    h, setup_ms = timed(lambda: az.az_setup(grid, mask, g.eps, az.AZ_NEG_LAPLACE_GAUSS, bpts,
-                                                            prob.weight, opts))
-                    fr = torch.from_numpy(np.ascontiguousarray(prob.rhs().T)).to(dev)
-                    gr = torch.from_numpy(np.ascontiguousarray(prob.boundary_rhs().T)).to(dev)
-                    x = torch.zeros((1, g.N), dtype=torch.float64, device=dev)
-                    _, solve_ms = timed(lambda: az.az_collocate(h, fr, gr, x))
-                info = az.az_get_info(h)
-                vals = torch.zeros((1, g.N * 4), dtype=torch.float64, device=dev)
-                az.az_evaluate(h, x, 4, vals)
-                az.az_destroy(h)
-                xf = W.grid_coords(W.Grid(1, g.n, (4,), g.T, g.epsh), 0)
-                inside = (xf >= a) & (xf <= b_)
-                err = float(np.abs(vals.cpu().numpy()[0] - f(xf))[inside].max())
-                out[name] = {"N": g.N, "k": info["k"], "rank": info["rank"], "setup_ms": round(setup_ms, 2),
-                             "solve_ms": round(solve_ms, 2), "max_error": err}
-            except Exception as ex:  # context only, never the headline
-                out[name] = {"error": str(ex)[:200]}
-    out["what"] = ("the paper's 1D examples at eps h = 0.327 (tau0 = 1e-10), FP64 throughout, tau = 1e-12; "
-                   "setup = az_setup (index map, symbol, sketch, factorisation) wall time, solve = one right-hand side")
+
+def config_2d_leg(name, nrhs=64):
+    """Configs 3 and 4 at full size, at the sketch width the adaptive setup
+    settles on (disc n = 256: k = 4096; star Poisson n = 128: k = 2048):
+    setup time, solve throughput of a batch of 64 right-hand sides (the
+    workload's function repeated), and the mixed path against the FP64 path
+    (relres; config 4 also the maximum error of u on the 1024 x 1024 test grid
+    inside the star, s_test = 8)."""
+    import numpy as np
+    import torch
+    import paper_2308_14490_gb300 as az
+    import workloads as W
+    dev = torch.device("cuda", 0)
+    if name == "config3":
+        p = W.config3(n=256, k=4096)
+    else:
+        p = W.config4(n=128, nb=2048, k=2048)
+    g = p.grid
+    mask = torch.from_numpy(np.ascontiguousarray(p.mask.reshape(-1))).to(dev)
+    kernel, bnd = az.AZ_GAUSS, None
+    if p.kind == "poisson":
+        kernel = az.AZ_NEG_LAPLACE_GAUSS
+        bnd = torch.from_numpy(np.ascontiguousarray(p.boundary)).to(dev)
+        f = torch.from_numpy(np.ascontiguousarray(np.repeat(p.rhs().T, nrhs, 0))).to(dev)
+        gb = torch.from_numpy(np.ascontiguousarray(np.repeat(p.boundary_rhs().T, nrhs, 0))).to(dev)
+    else:
+        b = torch.from_numpy(np.ascontiguousarray(np.repeat(p.rhs().T, nrhs, 0))).to(dev)
+    out = {"N": g.N, "k": p.k}
+    xs = {}
+    for prec, tag in ((az.AZ_FP64, "fp64"), (az.AZ_MIXED, "mixed")):
+        opts = az.make_options(prec, p.k, 1e-8, 0.0, 13, -1)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        h = az.az_setup(az.make_grid(2, g.n, g.s, g.T), mask, g.eps, kernel, bnd, p.weight, opts)
+        info = az.az_get_info(h)
+        setup_ms = 1000.0 * (time.perf_counter() - t0)
+        x = torch.zeros((nrhs, g.N), dtype=torch.float64, device=dev)
+
+        def solve(rel=False):
+            if p.kind == "poisson":
+                return az.az_collocate(h, f, gb, x, relres=rel)
+            return az.az_solve(h, b, x, relres=rel)
+
+        solve()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            solve()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        solve_ms = e0.elapsed_time(e1) / 3
+        rr = solve(True)
+        xs[tag] = x[:1].clone()
+        ent = {"setup_ms": round(setup_ms, 1), "rank": info["rank"], "M": info["M"], "Mb": info["Mb"],
+               "solve_ms_per_batch": round(solve_ms, 3), "solve_rhs_per_s": nrhs / (solve_ms / 1000.0),
+               "relres": rr[0], "device_bytes": info["device_bytes"]}
+        if p.kind == "poisson":
+            st = 8
+            vals = torch.zeros((1, g.N * st * st), dtype=torch.float64, device=dev)
+            az.az_evaluate(h, x[:1], st, vals)
+            gf = W.Grid(2, g.n, (st, st), g.T, g.epsh)
+            inside = W.star_mask(gf).reshape(-1).astype(bool)
+            X, Y = np.meshgrid(W.grid_coords(gf, 0), W.grid_coords(gf, 1), indexing="ij")
+            u = p.exact[0](np.stack([X.reshape(-1), Y.reshape(-1)], 1))
+            v = vals.cpu().numpy()[0]
+            ent["max_error_1024"] = float(np.abs(v - u)[inside].max())
+            xs[tag + "_vals"] = v[inside]
+        az.az_destroy(h)
+        torch.cuda.empty_cache()
+        out[tag] = ent
+    out["relres_gap_mixed_vs_fp64"] = abs(out["mixed"]["relres"] - out["fp64"]["relres"])
+    if p.kind == "poisson":
+        out["max_abs_diff_u_mixed_vs_fp64_1024"] = float(np.abs(xs["mixed_vals"] - xs["fp64_vals"]).max())
+    out["what"] = (f"{p.name}: az_setup wall time, az_solve/az_collocate of {nrhs} copies of the workload RHS "
+                   "(CUDA events, mean of 3 batches), relres of the first; mixed = FP64 sketch and factors, "
+                   "FP32 solve transforms, 1 FP64-residual refinement")
     return out
+
+
+def fp64_step_leg(h_grid, mask, b_dev, x_dev, stream, steps=5):
+    """The library's own all-FP64 config-2 step (az_refactor + az_solve of 64 RHS)."""
+    import torch
+    import paper_2308_14490_gb300 as az
+    g = problem().grid
+    o64 = az.make_options(az.AZ_FP64, K_SKETCH, 1e-8, 0.0, 1, 0)
+    h = az.az_setup(h_grid, mask, g.eps, options=o64)
+    for i in range(2):
+        az.az_refactor(h, 1 + i, stream)
+        az.az_solve(h, b_dev, x_dev, stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(steps):
+        az.az_refactor(h, 1 + (i % 2), stream)
+        az.az_solve(h, b_dev, x_dev, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    az.az_destroy(h)
+    return {"value": NRHS / (ms / 1000.0), "unit": "RHS/s", "ms_per_step": ms, "steps": steps,
+            "what": "same step, library all-FP64 path (FP64 sketch, transforms, factor and solve, no refinement)"}
 
 
 def serving_leg(seconds):
@@ -570,11 +675,20 @@ def run_ours(args):
             line["fp64_gpu_torch"] = comp
         except Exception as ex:  # the comparator is context, never the headline
             line["fp64_gpu_torch"] = {"error": str(ex)[:200]}
+        try:
+            line["fp64_library_step"] = fp64_step_leg(az.make_grid(1, g.n, g.s, g.T), mask, b_dev, x_dev, stream)
+        except Exception as ex:
+            line["fp64_library_step"] = {"error": str(ex)[:200]}
     az.az_destroy(h)
     if rank == 0 and world == 1 and args.serving_seconds > 0:
         line["serving"] = serving_leg(args.serving_seconds)
-    if rank == 0 and world == 1 and not args.no_paper_examples:
-        line["paper_examples"] = paper_examples_leg()
+    if rank == 0 and world == 1 and not args.no_context:
+        for nm, fn in (("config1", config1_leg), ("config3", lambda: config_2d_leg("config3")),
+                       ("config4", lambda: config_2d_leg("config4"))):
+            try:
+                line[nm] = fn()
+            except Exception as ex:  # context, never the headline
+                line[nm] = {"error": str(ex)[:300]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_leg()
     if rank == 0:

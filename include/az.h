@@ -139,7 +139,9 @@ az_status az_setup(const az_grid* g, const uint8_t* omega_mask_dev, const double
  * `refine_steps` steps x += AZ(b - A x) with the residual in FP64).
  *   b_dev  (M [+ Mb]) x nrhs, leading dimension ldb, FP64.
  *   x_dev  N x nrhs, leading dimension ldx, FP64 (overwritten).
- *   relres_host  optional host array of nrhs: ||A x - b|| / ||b|| (forces a sync). */
+ *   relres_host  optional host array of nrhs: ||A x - b|| / ||b|| (forces a sync;
+ *                then also reports AZ_ERR_TIMEOUT, once, if a tensor-core
+ *                pipeline wait of this handle timed out). */
 az_status az_solve(az_handle h, const double* b_dev, int64_t ldb, int64_t nrhs, double* x_dev,
                    int64_t ldx, void* stream, double* relres_host);
 
@@ -147,7 +149,11 @@ az_status az_solve(az_handle h, const double* b_dev, int64_t ldb, int64_t nrhs, 
  * and Dirichlet data g at the Mb boundary points; the interior rows and f are
  * divided by 2 eps^2 and the boundary rows and g multiplied by the setup's
  * boundary weight before the least-squares solve.  Requires a setup with
- * kernel = AZ_NEG_LAPLACE_GAUSS. */
+ * kernel = AZ_NEG_LAPLACE_GAUSS.  The scaled data go through a buffer the
+ * handle owns (M + Mb rows by one solve chunk): stream-ordered, no allocation
+ * and, without relres_host, no synchronisation, so the call can be captured
+ * in a CUDA graph; calls on one handle from overlapping streams race on that
+ * buffer. */
 az_status az_collocate(az_handle h, const double* f_int_dev, int64_t ldf, const double* g_bnd_dev,
                        int64_t ldg, int64_t nrhs, double* x_dev, int64_t ldx, void* stream,
                        double* relres_host);
@@ -181,8 +187,9 @@ az_status az_get_array(az_handle h, int32_t which, double* dst_dev, void* stream
 
 /* Sizes and factorisation results of a handle.  Waits (on the host) for the
  * handle's latest factorisation (az_setup or az_refactor) only, not for solves
- * in flight on other streams.  Returns AZ_ERR_CUDA if a solve that has
- * completed raised the tensor-core pipeline's wait-timeout flag. */
+ * in flight on other streams.  Returns AZ_ERR_TIMEOUT (once; the flag is then
+ * cleared) if a launch that has completed raised the tensor-core pipeline's
+ * wait-timeout flag. */
 az_status az_get_info(az_handle h, az_info_t* info);
 
 /* Device bytes a setup of this size would hold (symbols, maps, sketch and
@@ -197,7 +204,8 @@ const char* az_last_error(void);
 
 /* The Rademacher test matrix alone: R (N x k, ld = N, FP64 +1/-1) from the
  * Philox4x32-10 layout counter = (row/128, column, 0, 0), key = (seed low,
- * seed high), bit (row % 32) of word ((row % 128)/32), set = +1. */
+ * seed high), bit (row % 32) of word ((row % 128)/32), set = +1.
+ * k <= 65535; larger k returns AZ_ERR_ARG. */
 az_status az_rademacher(int64_t N, int32_t k, uint64_t seed, double* R_dev, void* stream);
 
 /* az_rademacher without any device allocation, for callers that cannot call
@@ -207,11 +215,14 @@ az_status az_rademacher(int64_t N, int32_t k, uint64_t seed, double* R_dev, void
  * and cudaFree may synchronise the device.  The paper has no counterpart; it is
  * a deployment variant of az_rademacher with identical output.
  *   Scratch: a fixed 4 MiB device array inside the library (kept by every GPU
- *   that loads it until the process exits).  Limit: k * ceil(N/32) <= 2^20,
- *   i.e. at most 2^25 entries of R; larger sizes return AZ_ERR_ARG.
- *   The first call on each device (with that device current) looks up the
- *   array's device address once; make that first call before any stream
- *   capture.  All calls share the one array, so calls that overlap on the GPU
+ *   that loads it until the process exits).  Limits: k * ceil(N/32) <= 2^20,
+ *   i.e. at most 2^25 entries of R, and k <= 65535; larger sizes return
+ *   AZ_ERR_ARG.
+ *   Each call made outside stream capture looks up the array's device address
+ *   for the current device (so an address from a context that cudaDeviceReset
+ *   destroyed is never reused); a call under capture reuses the address of the
+ *   last uncaptured call on that device.  Make the first call on each device
+ *   before any stream capture, and again after a cudaDeviceReset.  All calls share the one array, so calls that overlap on the GPU
  *   (different streams or threads without ordering) race on it and must be
  *   serialised by the caller.  Stream-ordered, no synchronisation. */
 az_status az_rademacher_noalloc(int64_t N, int32_t k, uint64_t seed, double* R_dev, void* stream);
@@ -238,6 +249,17 @@ az_status az_refactor(az_handle h, uint64_t seed, void* stream);
  * returns entry i (name, launches, total milliseconds, total bytes) or
  * AZ_ERR_ARG past the last entry. */
 int64_t az_launch_count(void);
+
+/* Test hook for the failure path of the tensor-core projection (not part of
+ * the paper's method): the next launch of that kernel (in any handle) stops
+ * issuing its TMA copies at pipeline iteration `iteration` and bounds each of
+ * its waits by wait_ns nanoseconds instead of one second.  Its consumers' waits
+ * then run out; every CTA stops issuing work, waits (bounded) for its own
+ * copies and MMAs, frees its tensor memory and returns, and the call that
+ * reads the handle's status (az_solve with relres_host, or az_get_info)
+ * returns AZ_ERR_TIMEOUT once.  One-shot; AZ_ERR_ARG for iteration < 0 or
+ * wait_ns <= 0. */
+az_status az_debug_tc_withhold(int32_t iteration, int64_t wait_ns);
 void az_profile_begin(void);
 az_status az_profile_end(void);
 az_status az_profile_query(int32_t i, char* name, int32_t name_len, int64_t* launches, double* ms,

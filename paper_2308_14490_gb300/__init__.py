@@ -64,6 +64,7 @@ _SIGS = {
     "az_refactor": [_P, ctypes.c_uint64, _P],
     "az_rademacher_noalloc": [_I64, _I32, ctypes.c_uint64, _P, _P],
     "az_launch_count": [],
+    "az_debug_tc_withhold": [_I32, _I64],
     "az_profile_begin": [],
     "az_profile_end": [],
     "az_profile_query": [_I32, ctypes.c_char_p, _I32, ctypes.POINTER(_I64), ctypes.POINTER(_D), ctypes.POINTER(_D)],
@@ -90,6 +91,14 @@ def _check(status, where):
 
 def _ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _ld(t):
+    """Leading dimension of a (ncols, rows) tensor viewed column-major: its row
+    stride (the stride of a single row is arbitrary; the row length then)."""
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError("expected a 2D tensor with contiguous rows")
+    return t.stride(0) if t.shape[0] > 1 else t.shape[1]
 
 
 def _stream(stream):
@@ -144,9 +153,11 @@ def az_solve(h, b, x, stream=None, relres=False):
 
 
 def az_collocate(h, f, g, x, stream=None, relres=False):
-    nrhs, ldf = f.shape
+    """f: (nrhs, >= M) interior data, g: (nrhs, >= Mb) boundary data, x: (nrhs, >= N);
+    the leading dimensions are the tensors' row strides (views are allowed)."""
+    nrhs = f.shape[0]
     rr = (ctypes.c_double * nrhs)() if relres else None
-    _check(_lib.az_collocate(h, _ptr(f), ldf, _ptr(g), g.shape[1], nrhs, _ptr(x), x.shape[1], _stream(stream), rr),
+    _check(_lib.az_collocate(h, _ptr(f), _ld(f), _ptr(g), _ld(g), nrhs, _ptr(x), _ld(x), _stream(stream), rr),
            "az_collocate")
     return list(rr) if relres else None
 
@@ -195,6 +206,12 @@ def az_rademacher_noalloc(N, k, seed, R, stream=None):
     """Same output as az_rademacher, but uses the library's fixed device scratch
     instead of allocating (for callers that cannot allocate device memory)."""
     _check(_lib.az_rademacher_noalloc(int(N), int(k), int(seed), _ptr(R), _stream(stream)), "az_rademacher_noalloc")
+
+
+def az_debug_tc_withhold(iteration, wait_ns):
+    """Test hook: the next tensor-core projection launch withholds its TMA copies
+    from `iteration` on, with waits bounded by wait_ns (see include/az.h)."""
+    _check(_lib.az_debug_tc_withhold(int(iteration), int(wait_ns)), "az_debug_tc_withhold")
 
 
 def az_last_error():

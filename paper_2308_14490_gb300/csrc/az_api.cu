@@ -88,7 +88,7 @@ struct az_setup_t {
   double* Q1 = nullptr;     // Mtot x k
   double* Rd = nullptr;     // N x k (collocation sketch)
   double* r64 = nullptr;    // Mtot x cols (relres residual), lazily
-  double* bcoll = nullptr;  // Mtot x cols (scaled collocation data), lazily
+  double* bcoll = nullptr;  // Mtot x 2 pairs_max (scaled collocation data of az_collocate)
   LargeK* wide = nullptr;   // k > 64: Householder QR + FP64 SVD + GEMM path
   // Omega = the whole box, no boundary rows, exact pseudo-inverse: Z* A = I,
   // so the perturbation is exactly zero (Sec. 3.1) and the sketch is skipped
@@ -615,7 +615,12 @@ az_status solve_impl(az_setup_t* h, const double* b, int64_t ldb, int64_t nrhs, 
       cudaError_t e2 = cudaStreamSynchronize(st);
       if (rc) return rc;
       if (e != cudaSuccess || e1 != cudaSuccess || e2 != cudaSuccess) { set_error("relres readback failed"); return AZ_ERR_CUDA; }
-      if (tcerr) { set_error(tc_wait_message(tcerr)); return AZ_ERR_CUDA; }
+      if (tcerr) {
+        // reported once: the flag is cleared so that later calls start clean
+        cudaMemsetAsync(h->tc_err, 0, sizeof(int), st);
+        set_error(tc_wait_message(tcerr));
+        return AZ_ERR_TIMEOUT;
+      }
       for (int c = 0; c < nc; ++c) relres[c0 + c] = hv[nc + c] > 0 ? std::sqrt(hv[c] / hv[nc + c]) : 0.0;
     }
   }
@@ -651,7 +656,6 @@ void destroy(az_setup_t* h) {
   if (h->X1d) cudaFree(h->X1d);
   if (h->X3d) cudaFree(h->X3d);
   if (h->r64) cudaFree(h->r64);
-  if (h->bcoll) cudaFree(h->bcoll);
   if (h->wide) large_destroy(h->wide);
   if (h->info_ev) cudaEventDestroy(h->info_ev);
   if (h->ev_sym) cudaEventDestroy(h->ev_sym);
@@ -671,6 +675,7 @@ void az_destroy(az_handle h) { destroy(h); }
 
 az_status az_rademacher(int64_t N, int32_t k, uint64_t seed, double* R_dev, void* stream) {
   if (N <= 0 || k <= 0 || !R_dev) { set_error("az_rademacher: bad arguments"); return AZ_ERR_ARG; }
+  if (k > 65535) { set_error("az_rademacher: k exceeds 65535 columns"); return AZ_ERR_ARG; }
   cudaStream_t st = (cudaStream_t)stream;
   uint32_t* bits;
   int64_t nw = (N + 31) / 32;
@@ -680,6 +685,12 @@ az_status az_rademacher(int64_t N, int32_t k, uint64_t seed, double* R_dev, void
   cudaStreamSynchronize(st);
   cudaFree(bits);
   return rc;
+}
+
+az_status az_debug_tc_withhold(int32_t iteration, int64_t wait_ns) {
+  if (iteration < 0 || wait_ns <= 0) { set_error("az_debug_tc_withhold: bad arguments"); return AZ_ERR_ARG; }
+  tc_tsgram_debug_withhold(iteration, (uint64_t)wait_ns);
+  return AZ_OK;
 }
 
 az_status az_query_footprint(const az_grid* gr, int64_t M, int64_t n_boundary, const az_options* opt, int64_t nrhs_max,
@@ -874,6 +885,7 @@ static az_status setup_fixed(const az_grid* gr, const uint8_t* mask, const doubl
     rc = dalloc_t(h, &h->sig, h->k); if (rc) break;
     rc = dalloc_t(h, &h->info, 1); if (rc) break;
     rc = alloc_workspace(h); if (rc) break;
+    if (h->kind == 1) { rc = dalloc_t(h, &h->bcoll, (size_t)h->Mtot * 2 * h->pairs_max); if (rc) break; }
     if (h->kind == 0 && !h->periodic && h->k <= kNarrowK && !(store64(h) && h->tau_svd < kGramTau)) {
       // overlap of az_refactor's sketch with the next solve: own stream,
       // events and FFT workspace for the sketch chain
@@ -977,14 +989,18 @@ az_status az_collocate(az_handle h, const double* f, int64_t ldf, const double* 
   if (!f || !gb || !x || nrhs < 0 || ldf < h->M || ldg < h->Mb || ldx < h->g.N) { set_error("az_collocate: bad arguments"); return AZ_ERR_ARG; }
   if (nrhs == 0) return AZ_OK;
   cudaStream_t st = (cudaStream_t)stream;
-  double* b;
-  AZ_CUDA(cudaMalloc((void**)&b, (size_t)h->Mtot * nrhs * sizeof(double)));
-  az_status rc = launch_scale_rows(f, ldf, h->M, (int)nrhs, 1.0 / (2.0 * h->eps * h->eps), b, h->Mtot, st);
-  if (rc == AZ_OK) rc = launch_boundary_rhs(h->g.dim, gb, ldg, h->Mb, (int)nrhs, h->bnrm, h->bweight, h->eps, b + h->M, h->Mtot, st);
-  if (rc == AZ_OK) rc = az_solve(h, b, h->Mtot, nrhs, x, ldx, stream, relres);
-  cudaStreamSynchronize(st);
-  cudaFree(b);
-  return rc;
+  // the scaled data [f / (2 eps^2); w g] in the handle's buffer, one solve
+  // chunk at a time (stream-ordered: no allocation, no synchronisation)
+  const int chunk = 2 * h->pairs_max;
+  for (int64_t c0 = 0; c0 < nrhs; c0 += chunk) {
+    const int nc = (int)std::min<int64_t>(chunk, nrhs - c0);
+    double* b = h->bcoll;
+    AZ_TRY(launch_scale_rows(f + c0 * ldf, ldf, h->M, nc, 1.0 / (2.0 * h->eps * h->eps), b, h->Mtot, st));
+    AZ_TRY(launch_boundary_rhs(h->g.dim, gb + c0 * ldg, ldg, h->Mb, nc, h->bnrm, h->bweight, h->eps, b + h->M,
+                               h->Mtot, st));
+    AZ_TRY(az_solve(h, b, h->Mtot, nc, x + c0 * ldx, ldx, stream, relres ? relres + c0 : nullptr));
+  }
+  return AZ_OK;
 }
 
 az_status az_evaluate(az_handle h, const double* x, int64_t ldx, int64_t nrhs, int32_t s_test, double* out, int64_t ldo,
@@ -1030,7 +1046,12 @@ az_status az_get_info(az_handle h, az_info_t* info) {
   AZ_CUDA(cudaEventSynchronize(h->info_ev));
   AZ_CUDA(cudaMemcpy(&fi, h->info, sizeof(fi), cudaMemcpyDeviceToHost));
   AZ_CUDA(cudaMemcpy(&tcerr, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
-  if (tcerr) { set_error(tc_wait_message(tcerr)); return AZ_ERR_CUDA; }
+  if (tcerr) {
+    // reported once: the flag is cleared so that later calls start clean
+    AZ_CUDA(cudaMemset(h->tc_err, 0, sizeof(int)));
+    set_error(tc_wait_message(tcerr));
+    return AZ_ERR_TIMEOUT;
+  }
   info->N = h->g.N; info->L = h->g.L; info->M = h->M; info->Mb = h->Mb; info->k = h->k;
   info->rank = fi.r; info->rank_gram = fi.r1; info->precision = h->precision;
   info->sigma_max = fi.sigma_max; info->sigma_min_kept = fi.sigma_min_kept;

@@ -24,6 +24,11 @@ using namespace az;
 
 extern "C" az_status az_rademacher_noalloc(int64_t N, int32_t k, uint64_t seed, double* R_dev, void* stream) {
   if (N <= 0 || k <= 0 || !R_dev) { set_error("az_rademacher_noalloc: bad arguments"); return AZ_ERR_ARG; }
+  if (k > 65535) {
+    // one grid row per column in both kernels (gridDim.y <= 65535)
+    set_error("az_rademacher_noalloc: k = " + std::to_string(k) + " exceeds 65535 columns");
+    return AZ_ERR_ARG;
+  }
   const int64_t words = (int64_t)k * ((N + 31) / 32);
   if (words > kNoallocWords) {
     set_error("az_rademacher_noalloc: k * ceil(N/32) = " + std::to_string(words) + " words exceeds the fixed scratch of " +
@@ -36,12 +41,23 @@ extern "C" az_status az_rademacher_noalloc(int64_t N, int32_t k, uint64_t seed, 
     set_error(std::string("az_rademacher_noalloc: cudaGetDevice: ") + cudaGetErrorString(e));
     return AZ_ERR_CUDA;
   }
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(st, &cap);
+  if (e != cudaSuccess) {
+    set_error(std::string("az_rademacher_noalloc: cudaStreamIsCapturing: ") + cudaGetErrorString(e));
+    return AZ_ERR_CUDA;
+  }
   uint32_t* bits = nullptr;
   {
-    // One-time set-up per device (with that device current): the host-side
-    // name of the array is not a device address, so look the address up.
+    // The host-side name of the array is not a device address: look the
+    // address up with this device current.  Outside stream capture it is
+    // looked up on every call (cheap once the module is loaded), so a context
+    // destroyed and re-created (cudaDeviceReset) never leaves a stale address;
+    // during capture the address of the last uncaptured call on this device
+    // is used (a first call that is being captured still looks it up).
     std::lock_guard<std::mutex> g(g_mu);
-    if (!g_bits_addr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone || !g_bits_addr[dev]) {
       void* p = nullptr;
       e = cudaGetSymbolAddress(&p, g_noalloc_bits);
       if (e != cudaSuccess || !p) {
@@ -52,7 +68,6 @@ extern "C" az_status az_rademacher_noalloc(int64_t N, int32_t k, uint64_t seed, 
     }
     bits = g_bits_addr[dev];
   }
-  cudaStream_t st = (cudaStream_t)stream;
   // The Philox kernel writes every word the expansion reads, so nothing left
   // in the array by an earlier call needs clearing.
   AZ_TRY(launch_philox_bits(bits, N, k, seed, st));

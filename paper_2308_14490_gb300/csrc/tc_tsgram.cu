@@ -39,7 +39,7 @@ constexpr int KBLK = 32;                    // rows of M per stage: 128 bytes of
 constexpr int P_BYTES = 128 * 128;          // B' tile: 128 MMA rows x 128 bytes
 constexpr int XCH_BYTES = 64 * 64 * 4;      // epilogue exchange of the B_lo rows
 constexpr int TMEM_COLS = 128;              // >= 2 NB accumulator columns
-constexpr uint64_t WAIT_NS = 1000000000ull; // bound of every wait
+constexpr uint64_t WAIT_NS = 1000000000ull; // bound of every wait (a test hook may shorten it)
 
 __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -65,15 +65,15 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
   return ok != 0;
 }
 
-// Wait for the phase of the given parity; false on timeout or (when abort is
-// given) once another role has given up.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, const volatile int* abort) {
+// Wait for the phase of the given parity; false after limit_ns or (when abort
+// is given) once another role has given up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, const volatile int* abort, uint64_t limit_ns) {
   if (mbar_try(b, parity)) return true;
   const uint64_t t0 = gtimer();
   while (true) {
     if (mbar_try(b, parity)) return true;
     if (abort && *abort) return false;
-    if (gtimer() - t0 > WAIT_NS) return false;
+    if (gtimer() - t0 > limit_ns) return false;
   }
 }
 
@@ -161,9 +161,12 @@ __device__ __forceinline__ void give_up(int* err, volatile int* abort, int code)
 
 // P = B (np <= 64 columns -> MMA rows), Q = A (nq <= 64 columns -> N rows).
 // partial[blockIdx.x * nq * np + j + i * nq] = sum_m Q[m, j] P[m, i].
+// wait_ns bounds every wait; withhold >= 0 (test hook only) makes the TMA
+// producer stop issuing at that iteration, so the consumers' waits run out.
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_tsgram(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUtensorMap mapQ, int np, int nq,
-                int NB, int stages, int64_t nkb, double* __restrict__ partial, int* __restrict__ err) {
+                int NB, int stages, int64_t nkb, double* __restrict__ partial, int* __restrict__ err,
+                uint64_t wait_ns, int withhold) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // tiles start on a 1024-byte boundary of the shared address space (the
   // 128-byte swizzle pattern repeats every 8 rows of 128 bytes)
@@ -214,7 +217,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       int issued = 0;
       for (int it = 0; it < nit; ++it) {
         const int s = it % stages;
-        if (it >= stages && !mbar_wait(&empty[s], ((it / stages) + 1) & 1, abort)) {
+        if (it == withhold) break;   // test hook: this stage never arrives
+        if (it >= stages && !mbar_wait(&empty[s], ((it / stages) + 1) & 1, abort, wait_ns)) {
           give_up(err, abort, 1);
           break;
         }
@@ -227,7 +231,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
       // never leave with copies in flight
       for (int it = issued > stages ? issued - stages : 0; it < issued; ++it)
-        if (!mbar_wait(&full[it % stages], (it / stages) & 1, nullptr)) give_up(err, abort, 4);
+        if (!mbar_wait(&full[it % stages], (it / stages) & 1, nullptr, wait_ns)) give_up(err, abort, 4);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -235,7 +239,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const uint32_t idesc = idesc_tf32(128, 2 * NB);
       for (int it = 0; it < nit; ++it) {
         const int s = it % stages;
-        if (!mbar_wait(&conv[s], (it / stages) & 1, abort)) {
+        if (!mbar_wait(&conv[s], (it / stages) & 1, abort, wait_ns)) {
           give_up(err, abort, 2);
           break;
         }
@@ -254,7 +258,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int nP = np * 8, nQ = nq * 8;  // 16-byte chunks of the loaded rows
     for (int it = 0; it < nit; ++it) {
       const int s = it % stages;
-      if (!mbar_wait(&full[s], (it / stages) & 1, abort)) {
+      if (!mbar_wait(&full[s], (it / stages) & 1, abort, wait_ns)) {
         give_up(err, abort, 3);
         break;
       }
@@ -276,7 +280,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __syncwarp();
   bool have = false;
   if (warp < 4) {
-    const bool ok = nit > 0 && mbar_wait(done, 0, nullptr) && !*abort;
+    const bool ok = nit > 0 && mbar_wait(done, 0, nullptr, wait_ns) && !*abort;
     have = __all_sync(0xffffffffu, ok);
     tc_fence_after();
   }
@@ -375,6 +379,17 @@ size_t smem_bytes(int NB, int* stages_out) {
 
 }  // namespace
 
+// test hook (az_debug_tc_withhold): one-shot, read by the next launch
+static std::mutex g_hook_mu;
+static int g_hook_withhold = -1;
+static uint64_t g_hook_wait_ns = WAIT_NS;
+
+void tc_tsgram_debug_withhold(int iteration, uint64_t wait_ns) {
+  std::lock_guard<std::mutex> g(g_hook_mu);
+  g_hook_withhold = iteration;
+  g_hook_wait_ns = wait_ns;
+}
+
 int tc_tsgram_blocks() { return sm_count(); }
 
 bool tc_tsgram_ok(const void* A, int64_t lda, int ka, const void* B, int64_t ldb, int kb) {
@@ -408,7 +423,17 @@ az_status launch_tc_tsgram(const float* A, int64_t lda, int ka, const float* B, 
       set_bytes = sm;
     }
   }
-  k_tc_tsgram<<<grid, TC_THREADS, sm, st>>>(mP, mQ, kb, ka, NB, stages, nkb, partial, err);
+  uint64_t wait_ns = WAIT_NS;
+  int withhold = -1;
+  {
+    std::lock_guard<std::mutex> g(g_hook_mu);
+    if (g_hook_withhold >= 0) {
+      withhold = g_hook_withhold;
+      wait_ns = g_hook_wait_ns;
+      g_hook_withhold = -1;
+    }
+  }
+  k_tc_tsgram<<<grid, TC_THREADS, sm, st>>>(mP, mQ, kb, ka, NB, stages, nkb, partial, err, wait_ns, withhold);
   {
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {

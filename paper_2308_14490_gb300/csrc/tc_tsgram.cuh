@@ -20,5 +20,8 @@ bool tc_tsgram_ok(const void* A, int64_t lda, int ka, const void* B, int64_t ldb
 az_status launch_tc_tsgram(const float* A, int64_t lda, int ka, const float* B, int64_t ldb, int kb, int64_t M,
                            double* partial, double* G, int* err, cudaStream_t st);
 int tc_tsgram_blocks();
+// Test hook: the next launch stops issuing TMA copies at `iteration` (so its
+// consumers' waits run out) and bounds every wait by wait_ns.  One-shot.
+void tc_tsgram_debug_withhold(int iteration, uint64_t wait_ns);
 
 }  // namespace az

@@ -34,8 +34,8 @@ from dataclasses import dataclass, field
 import numpy as np
 import torch
 
-from . import (AZ_ERR_ADMISSION, AZ_FP64, AZ_GAUSS, AZ_MIXED, AZ_NEG_LAPLACE_GAUSS, AZError, az_destroy, az_get_info,
-               az_query_footprint, az_setup, az_solve, make_grid, make_options)
+from . import (AZ_ERR_ADMISSION, AZ_FP64, AZ_GAUSS, AZ_MIXED, AZ_NEG_LAPLACE_GAUSS, AZError, az_collocate, az_destroy,
+               az_get_info, az_query_footprint, az_setup, az_solve, make_grid, make_options)
 
 BUCKETS = (2, 4, 8, 16, 32, 64)
 
@@ -209,26 +209,43 @@ class Server:
             self._evict(st)
 
     # ------------------------------------------------------------------ solves
-    def _rhs(self, st: _Setup, reqs, out):
-        """Fill out[:ncols] with each request's right-hand sides (cos(w.x + phi))."""
-        col = 0
+    @staticmethod
+    def _offsets(reqs):
+        """First column of each request in a batch, and the batch width.  Every
+        request starts on an even column: the solver packs two real columns into
+        one complex transform, so a request's columns then pair with each other
+        (and an odd last column with a zero column) exactly as when it runs
+        alone, and its result does not depend on the rest of the batch."""
+        offs, col = [], 0
         for r in reqs:
+            offs.append(col)
+            col += r.nrhs + (r.nrhs & 1)
+        return offs, col
+
+    def _rhs(self, st: _Setup, reqs, out):
+        """Fill out with each request's right-hand sides (cos(w.x + phi)) at its
+        column offset; returns the batch width."""
+        offs, width = self._offsets(reqs)
+        for r, col in zip(reqs, offs):
             g = np.random.default_rng(r.seed)
             w = torch.from_numpy(g.uniform(1.0, 20.0, (r.nrhs, st.spec.dim))).to(self.dev)
             ph = torch.from_numpy(g.uniform(0.0, 2 * math.pi, r.nrhs)).to(self.dev)
             vals = torch.cos(st.coords @ w.T + ph[None, :])            # (M, nrhs)
             if st.spec.kind == "poisson":
-                eps = st.spec.epsh / (2 * st.spec.T[0] / st.spec.n[0])
-                lap = (w * w).sum(1)                                     # -Lap cos = |w|^2 cos
-                interior = vals * lap[None, :] / (2 * eps * eps)
-                bvals = torch.cos(st.bnd @ w.T + ph[None, :]) * st.spec.weight
-                vals = torch.cat([interior, bvals], 0)
+                # interior data f = -Lap u = |w|^2 cos, then the Dirichlet data
+                # u on the boundary points; az_collocate applies the row scaling
+                lap = (w * w).sum(1)
+                bvals = torch.cos(st.bnd @ w.T + ph[None, :])
+                vals = torch.cat([vals * lap[None, :], bvals], 0)
             out[col:col + r.nrhs, :vals.shape[0]] = vals.T
-            col += r.nrhs
-        return col
+        return width
 
     def _solve_fn(self, st, b_buf, x_buf, stream):
-        az_solve(st.h, b_buf, x_buf, stream)
+        if st.spec.kind == "poisson":
+            M = st.info["M"]
+            az_collocate(st.h, b_buf[:, :M], b_buf[:, M:], x_buf, stream)
+        else:
+            az_solve(st.h, b_buf, x_buf, stream)
 
     def _graph(self, st: _Setup, bucket: int, stream, capture: bool = True):
         """(graph or None, b_buf, x_buf) of a bucket; captures only when asked."""
@@ -276,10 +293,10 @@ class Server:
                 del self.queue[key]
                 return
         reqs, ncols = [], 0
-        while q and ncols + q[0].nrhs <= BUCKETS[-1]:
+        while q and ncols + q[0].nrhs + (q[0].nrhs & 1) <= BUCKETS[-1]:
             r = q.popleft()
             reqs.append(r)
-            ncols += r.nrhs
+            ncols += r.nrhs + (r.nrhs & 1)
         if not q:
             del self.queue[key]
         bucket = next(b for b in BUCKETS if b >= ncols)
@@ -303,12 +320,11 @@ class Server:
             if busy is not None and busy[0].query():
                 ev, st, reqs, x_buf, ncols = busy
                 t = now_fn()
-                col = 0
-                for r in reqs:
+                offs, _ = self._offsets(reqs)
+                for r, col in zip(reqs, offs):
                     r.t_done = t
                     if self.keep_results:
                         self.results[r.rid] = x_buf[col:col + r.nrhs].clone()
-                    col += r.nrhs
                 st.inflight -= 1
                 self.slot_busy[i] = None
 
