@@ -512,9 +512,11 @@ az_status compute_setup(az_setup_t* h, cudaStream_t st, bool with_index_map) {
 // One AZ solve of ncols columns (T precision): x (=|+=) Z* b + W VS U^T (b - A Z* b).
 // Mixed path: xf_out receives the (exactly FP32) result, x may then be null;
 // xbase (FP32, ld N) makes the update x = xbase + (...).
+// last: the solve's final pass (its projection error is not refined away):
+// the wide path then projects with exact products instead of split TF32.
 template <typename T, typename TB>
 az_status az_once(az_setup_t* h, const TB* b, int64_t ldb, int ncols, double* x, int64_t ldx, bool accumulate,
-                  cudaStream_t st, float* xf_out = nullptr, const float* xbase = nullptr) {
+                  cudaStream_t st, float* xf_out = nullptr, const float* xbase = nullptr, bool last = true) {
   const Geom& g = h->g;
   T* z = (T*)h->zb;
   T* gg = (T*)h->gb;
@@ -534,7 +536,8 @@ az_status az_once(az_setup_t* h, const TB* b, int64_t ldb, int ncols, double* x,
   const T* Ub = h->sk64 ? (const T*)h->Ut32 : (const T*)h->Ut;
   const bool w64 = h->sk64 || Prec<T>::fp64;
   if (h->wide) {
-    AZ_TRY(large_project(h->wide, Ub, h->ldm, gg, h->ldm, ncols, h->cb, st, !Prec<T>::fp64));
+    AZ_TRY(large_project(h->wide, Ub, h->ldm, gg, h->ldm, ncols, h->cb, st, !Prec<T>::fp64,
+                         last ? nullptr : h->tc_err));
     AZ_TRY(launch_small_mm(h->VS, h->k, h->cb, ncols, h->ub, st));
     AZ_TRY(large_update(h->wide, h->W, g.N, h->ub, z, g.N, g.N, ncols, x, ldx, accumulate, st, w64,
                         !Prec<T>::fp64));
@@ -576,7 +579,7 @@ az_status solve_impl(az_setup_t* h, const double* b, int64_t ldb, int64_t nrhs, 
     // (the wide path leaves the FP32 first-pass result in the z buffer instead)
     const bool defer = mixed && h->refine > 0 && h->Mb == 0 && !h->wide;
     AZ_TRY((az_once<T, double>(h, bc, ldb, nc, defer ? nullptr : xc, ldx, false, st,
-                               mixed && h->refine > 0 && !h->wide ? h->xfb : nullptr)));
+                               mixed && h->refine > 0 && !h->wide ? h->xfb : nullptr, nullptr, h->refine == 0)));
     const float* x1f = h->wide ? (const float*)h->zb : h->xfb;
     for (int it = 0; it < h->refine; ++it) {
       T* res = (T*)h->rb;
@@ -596,8 +599,9 @@ az_status solve_impl(az_setup_t* h, const double* b, int64_t ldb, int64_t nrhs, 
         // r = b - A x with the residual computed in FP64
         AZ_TRY((apply_rows<double, double, double, T>(h, xc, ldx, bc, ldb, 1.0, -1.0, res, h->Mtot, nc, st)));
       }
-      if (defer && it == 0) AZ_TRY((az_once<T, T>(h, res, h->Mtot, nc, xc, ldx, false, st, nullptr, h->xfb)));
-      else AZ_TRY((az_once<T, T>(h, res, h->Mtot, nc, xc, ldx, true, st)));
+      const bool last = it + 1 == h->refine;
+      if (defer && it == 0) AZ_TRY((az_once<T, T>(h, res, h->Mtot, nc, xc, ldx, false, st, nullptr, h->xfb, last)));
+      else AZ_TRY((az_once<T, T>(h, res, h->Mtot, nc, xc, ldx, true, st, nullptr, nullptr, last)));
     }
     if (relres) {
       if (!h->r64) {
@@ -736,6 +740,16 @@ static az_status setup_fixed(const az_grid* gr, const uint8_t* mask, const doubl
 // 2^-24 exp((pi / (2 eps h))^2), is below 1e-3, i.e. eps h >= 0.504 (the
 // eps h = 1 regime of the large workloads passes; the tau0 = 1e-10 regime of
 // Eq. constant_shapeparam, eps h = 0.33, does not and needs AZ_FP64).
+// The wide path's double-float (48-bit) tall products see the same
+// amplification: FP64 setups use them while 2^-48 exp((pi / (2 eps h))^2)
+// stays near 1e-12 (eps h >= 0.66, amplification <= 300), else FP64 arithmetic.
+static bool df_resolves(const Geom& g, double eps) {
+  double epsh = 1e300;
+  for (int d = 0; d < g.dim; ++d) epsh = std::min(epsh, eps * 2.0 * g.T[d] / (double)(g.Ld[d] / g.s[d]));
+  const double a = M_PI / (2.0 * epsh);
+  return a * a <= std::log(300.0);
+}
+
 static bool mixed_resolves(const Geom& g, double eps) {
   double epsh = 1e300;
   for (int d = 0; d < g.dim; ++d) epsh = std::min(epsh, eps * 2.0 * g.T[d] / (double)(g.Ld[d] / g.s[d]));
@@ -909,7 +923,7 @@ static az_status setup_fixed(const az_grid* gr, const uint8_t* mask, const doubl
     // takes the Householder route whatever the width.
     if (h->k > kNarrowK || (store64(h) && h->tau_svd < kGramTau)) {
       size_t wb = 0;
-      rc = large_create(&h->wide, h->Mtot, h->k, store64(h), h->Q1, &wb);
+      rc = large_create(&h->wide, h->Mtot, h->k, store64(h), h->Q1, &wb, 2 * h->pairs_max, !df_resolves(g, eps));
       h->bytes += wb;
       if (rc) break;
     } else {

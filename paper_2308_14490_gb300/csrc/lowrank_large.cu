@@ -1,16 +1,20 @@
 // Low-rank step for wide sketches (k > 64): Householder QR of the sketch
-// (cuSOLVER geqrf / orgqr: backward stable, no Gram squaring), FP64 SVD of the
-// k x k triangular factor, and cuBLAS GEMMs for the tall products
-// (U_tau = Q U_R, c = U_tau^T g, x = z + W u).  Same outputs as the narrow
-// path: U_tau ((M+Mb) x k, zero beyond the rank), VS = V_R Sigma^{-1}
-// (k x k), sigma, and the FactorInfo record.
+// (cuSOLVER geqrf / orgqr: backward stable, no Gram squaring; the Gram routes
+// cannot resolve the singular values near tau = 1e-8 sigma_1 that resolved 2D
+// sketches have), FP64 SVD of the k x k triangular factor (cuSOLVER gesvd),
+// and hand-written double-float kernels for the tall products U_tau = Q U_R,
+// c = U_tau^T g and x = z + W u (dfgemm.cu).  Same outputs as the narrow path:
+// U_tau ((M+Mb) x k, zero beyond the rank), VS = V_R Sigma^{-1} (k x k), sigma,
+// and the FactorInfo record.
 #include <cublas_v2.h>
 #include <cusolverDn.h>
 
 #include <algorithm>
 #include <string>
 
+#include "dfgemm.cuh"
 #include "lowrank.cuh"
+#include "tc_tsgram.cuh"
 #include "lowrank_large.cuh"
 #include "profile.cuh"
 
@@ -49,8 +53,9 @@ struct LargeK {
   double* VT = nullptr;      // k x k
   double* S = nullptr;       // k
   void* UR = nullptr;        // k x k, T: U_R with columns >= rank zeroed
-  void* c32 = nullptr;       // k x 64 (mixed: FP32 projection)
-  void* u32 = nullptr;       // k x 64 (mixed: FP32 copy of u)
+  double* part = nullptr;    // split-K partials of the double-float projection
+  int cols_max = 0;          // right-hand sides per projection call
+  bool prod64 = false;       // tall products in FP64 arithmetic (else double-float)
 };
 
 static az_status lk_alloc(void** p, size_t bytes) {
@@ -62,12 +67,15 @@ static az_status lk_alloc(void** p, size_t bytes) {
   return AZ_OK;
 }
 
-az_status large_create(LargeK** out, int64_t M, int k, bool fp64, void* A_probe, size_t* bytes) {
+az_status large_create(LargeK** out, int64_t M, int k, bool fp64, void* A_probe, size_t* bytes, int cols_max,
+                       bool prod64) {
   LargeK* L = new LargeK();
   *out = L;
+  L->prod64 = prod64;
   L->fp64 = fp64;
   L->M = M;
   L->k = k;
+  L->cols_max = cols_max;
   AZ_SOL(cusolverDnCreate(&L->sol));
   AZ_BLAS(cublasCreate(&L->blas));
   size_t tot = 0;
@@ -94,9 +102,15 @@ az_status large_create(LargeK** out, int64_t M, int k, bool fp64, void* A_probe,
   AZ_TRY(lk_alloc((void**)&L->VT, (size_t)k * k * 8));
   AZ_TRY(lk_alloc((void**)&L->S, (size_t)k * 8));
   AZ_TRY(lk_alloc(&L->UR, (size_t)k * k * ts));
-  AZ_TRY(lk_alloc(&L->c32, (size_t)k * 64 * 4));
-  AZ_TRY(lk_alloc(&L->u32, (size_t)k * 64 * 4));
-  tot += (size_t)k * (4 * k * 8 + 8 + k * ts + 2 * 64 * 4 + ts);
+  tot += (size_t)k * (4 * k * 8 + 8 + k * ts + ts);
+  // the projection's split-K partials for every column count up to cols_max
+  size_t pmax = 0;
+  for (int nb = 1; nb <= cols_max; nb = nb < 64 ? nb + 1 : nb + 64)
+    pmax = std::max(pmax, (size_t)df_tn_splits(M, k, std::min(nb, cols_max)) * k * std::min(nb, cols_max));
+  pmax = std::max(pmax, (size_t)df_tn_splits(M, k, cols_max) * k * cols_max);
+  for (int nb = 1; nb <= std::min(64, cols_max); ++nb) pmax = std::max(pmax, tc_tsgram_wide_partial(M, k, nb));
+  AZ_TRY(lk_alloc((void**)&L->part, pmax * 8));
+  tot += pmax * 8;
   *bytes = tot;
   return AZ_OK;
 }
@@ -106,7 +120,7 @@ void large_destroy(LargeK* L) {
   if (L->sol) cusolverDnDestroy(L->sol);
   if (L->blas) cublasDestroy(L->blas);
   for (void* p : {L->work, L->blas_ws, (void*)L->devinfo, L->tau, (void*)L->R, (void*)L->U, (void*)L->VT,
-                  (void*)L->S, L->UR, L->c32, L->u32})
+                  (void*)L->S, L->UR, (void*)L->part})
     if (p) cudaFree(p);
   delete L;
 }
@@ -180,8 +194,8 @@ az_status large_factor_t(LargeK* L, const T* Y, int64_t ldy, T* A, T* Ut, int64_
   // U_tau = Q U_R (columns beyond the rank are zero)
   const T one = 1, zero = 0;
   if (sizeof(T) == 8) {
-    AZ_BLAS(cublasDgemm(L->blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)M, k, k, (const double*)&one, (const double*)A, (int)M,
-                        (const double*)L->UR, k, (const double*)&zero, (double*)Ut, (int)ldu));
+    AZ_TRY((launch_df_update<double, double>((const double*)A, M, k, (const double*)L->UR, k, nullptr, M, M,
+                                             (double*)Ut, ldu, false, st, nullptr, L->prod64)));
   } else {
     AZ_BLAS(cublasSgemm(L->blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)M, k, k, (const float*)&one, (const float*)A, (int)M,
                         (const float*)L->UR, k, (const float*)&zero, (float*)Ut, (int)ldu));
@@ -195,77 +209,36 @@ az_status large_factor(LargeK* L, const void* Y, int64_t ldy, void* A, void* Ut,
                  : large_factor_t<float>(L, (const float*)Y, ldy, (float*)A, (float*)Ut, ldu, tau, floor, VS, sig, info, st);
 }
 
-__global__ void k_f2d_cols(const float* __restrict__ a, int n, double* __restrict__ b) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) b[t] = (double)a[t];
-}
-__global__ void k_d2f_cols(const double* __restrict__ a, int n, float* __restrict__ b) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) b[t] = (float)a[t];
-}
-
-// c[k x n] = Ut^T g   (FP64 result); f32: Ut and g are FP32 (the mixed
-// path's projection), else FP64
+// c[k x n] = Ut^T g   (FP64 result).  f32: Ut and g are FP32 (the mixed
+// path's projection): on the tensor cores (split TF32, FP32-level accuracy)
+// for n <= 64, else in double-float; FP64: double-float (or FP64 arithmetic).
+// tc_err: the tensor-core pipeline's wait-timeout flag.
 az_status large_project(LargeK* L, const void* Ut, int64_t ldu, const void* g, int64_t ldg, int n, double* c,
-                        cudaStream_t st, bool f32) {
-  ProfScope ps("wide_proj", (double)L->M * (L->k + n) * (f32 ? 4 : 8), st);
-  AZ_BLAS(cublasSetStream(L->blas, st));
-  if (!f32) {
-    const double one = 1, zero = 0;
-    AZ_BLAS(cublasDgemm(L->blas, CUBLAS_OP_T, CUBLAS_OP_N, L->k, n, (int)L->M, &one, (const double*)Ut, (int)ldu,
-                        (const double*)g, (int)ldg, &zero, c, L->k));
-  } else {
-    const float one = 1, zero = 0;
-    AZ_BLAS(cublasSgemm(L->blas, CUBLAS_OP_T, CUBLAS_OP_N, L->k, n, (int)L->M, &one, (const float*)Ut, (int)ldu,
-                        (const float*)g, (int)ldg, &zero, (float*)L->c32, L->k));
-    k_f2d_cols<<<(L->k * n + 255) / 256, 256, 0, st>>>((const float*)L->c32, L->k * n, c);
-    AZ_CUDA(cudaGetLastError());
-  }
-  return AZ_OK;
+                        cudaStream_t st, bool f32, int* tc_err) {
+  if (n > L->cols_max) { set_error("wide projection: more columns than the setup's chunk"); return AZ_ERR_ARG; }
+  if (f32 && n <= 64 && tc_err && tc_tsgram_wide_ok(Ut, ldu, L->k, g, ldg, n))
+    return launch_tc_tsgram_wide((const float*)Ut, ldu, L->k, (const float*)g, ldg, n, L->M, L->part, c, tc_err, st);
+  if (f32)
+    return launch_df_tn<float, float>((const float*)Ut, ldu, L->k, (const float*)g, ldg, n, L->M, L->part, c, st);
+  return launch_df_tn<double, double>((const double*)Ut, ldu, L->k, (const double*)g, ldg, n, L->M, L->part, c, st,
+                                      L->prod64);
 }
 
-__global__ void k_store_x(const float* __restrict__ zf, int64_t ldz, const double* __restrict__ zd, int64_t N,
-                          double* __restrict__ x, int64_t ldx, int accumulate) {
-  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int c = blockIdx.y;
-  if (j >= N) return;
-  const double v = zf ? cvt<double>(zf[(int64_t)c * ldz + j]) : zd[(int64_t)c * ldz + j];
-  double* xp = x + (int64_t)c * ldx + j;
-  *xp = accumulate ? *xp + v : v;
-}
-
-// z += W u (in place, in the precision of W), then x (=|+=) z.  In the mixed
-// path z then holds the exact FP32 value of the new solution increment.
-// w64 with z32 (the FP64-sketch mixed path): x (=|+=) z first, then x += W u in
-// FP64, so that the update is consistent with the FP64 sketch Y = A W.
+// x (=|+=) z + W u in double-float.  w64 with z32 (the FP64-sketch mixed path)
+// and w64 alone (FP64): x from the FP64-accurate sum.  FP32 W (the FP32-sketch
+// mixed path): the sum is rounded to FP32 and also written back to z, so that
+// x is exactly the FP32 value z holds (the first pass's residual is formed
+// from that FP32 solution).
 az_status large_update(LargeK* L, const void* W, int64_t ldw, const double* u, void* z, int64_t ldz, int64_t N, int n,
                        double* x, int64_t ldx, bool accumulate, cudaStream_t st, bool w64, bool z32) {
-  ProfScope ps("wide_update", (double)N * (L->k * (w64 ? 8 : 4) + 2 * n * (z32 ? 4 : 8)) +
-                                  (double)N * n * 8 * (accumulate ? 2 : 1), st);
-  AZ_BLAS(cublasSetStream(L->blas, st));
-  dim3 grid((unsigned)((N + 255) / 256), n);
-  if (w64 && z32) {
-    k_store_x<<<grid, 256, 0, st>>>((const float*)z, ldz, nullptr, N, x, ldx, accumulate ? 1 : 0);
-    AZ_CUDA(cudaGetLastError());
-    const double one = 1;
-    AZ_BLAS(cublasDgemm(L->blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)N, n, L->k, &one, (const double*)W, (int)ldw, u, L->k,
-                        &one, x, (int)ldx));
-    return AZ_OK;
-  }
-  if (w64) {
-    const double one = 1;
-    AZ_BLAS(cublasDgemm(L->blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)N, n, L->k, &one, (const double*)W, (int)ldw, u, L->k,
-                        &one, (double*)z, (int)ldz));
-  } else {
-    k_d2f_cols<<<(L->k * n + 255) / 256, 256, 0, st>>>(u, L->k * n, (float*)L->u32);
-    const float one = 1;
-    AZ_BLAS(cublasSgemm(L->blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)N, n, L->k, &one, (const float*)W, (int)ldw,
-                        (const float*)L->u32, L->k, &one, (float*)z, (int)ldz));
-  }
-  k_store_x<<<grid, 256, 0, st>>>(w64 ? nullptr : (const float*)z, ldz, w64 ? (const double*)z : nullptr, N, x,
-                                  ldx, accumulate ? 1 : 0);
-  AZ_CUDA(cudaGetLastError());
-  return AZ_OK;
+  if (w64 && z32)
+    return launch_df_update<double, float>((const double*)W, ldw, L->k, u, n, (const float*)z, ldz, N, x, ldx,
+                                           accumulate, st);
+  if (w64)
+    return launch_df_update<double, double>((const double*)W, ldw, L->k, u, n, (const double*)z, ldz, N, x, ldx,
+                                            accumulate, st, nullptr, L->prod64);
+  return launch_df_update<float, float>((const float*)W, ldw, L->k, u, n, (const float*)z, ldz, N, x, ldx, accumulate,
+                                        st, (float*)z);
 }
 
 }  // namespace az

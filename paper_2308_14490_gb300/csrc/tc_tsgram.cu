@@ -11,7 +11,8 @@
 //   * one thread issues four tcgen05.mma (K = 8 each), D += B' A'^T, so D holds
 //     B_hi A_hi, B_hi A_lo, B_lo A_hi and B_lo A_lo in four quadrants.
 // The sum of the first three quadrants is the product to about 2^-21 relative
-// per term (lo is itself read as TF32), against 2^-11 for plain TF32.  The
+// per term (lo is itself rounded to TF32, so the errors take either sign),
+// against 2^-11 for plain TF32.  The
 // epilogue adds the quadrants in FP64 and writes one partial per CTA; a warp
 // per entry then sums the partials in a fixed order.
 //
@@ -138,11 +139,15 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
   v[4] = __uint_as_float(r4); v[5] = __uint_as_float(r5); v[6] = __uint_as_float(r6); v[7] = __uint_as_float(r7);
 }
 
-// x = hi + lo with hi = x rounded to the nearest TF32 (10 stored mantissa
-// bits, ties away from zero); lo is exact in FP32 and |lo| <= 2^-11 |x|.
+// x ~ hi + lo with hi = x rounded to the nearest TF32 (10 stored mantissa
+// bits, ties away from zero) and lo = x - hi (exact in FP32, |lo| <= 2^-11 |x|)
+// rounded to the nearest TF32 as well: the tensor core would otherwise
+// truncate lo's extra bits, an error of one sign that grows linearly over a
+// long contraction; rounded, |x - hi - lo| <= 2^-22 |x| with either sign.
 __device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
   hi = __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
   lo = x - hi;
+  lo = __uint_as_float((__float_as_uint(lo) + 0x1000u) & 0xFFFFE000u);
 }
 
 __device__ __forceinline__ float4 split4(float4 v, float4& lo) {
@@ -159,14 +164,17 @@ __device__ __forceinline__ void give_up(int* err, volatile int* abort, int code)
   *abort = 1;
 }
 
-// P = B (np <= 64 columns -> MMA rows), Q = A (nq <= 64 columns -> N rows).
-// partial[blockIdx.x * nq * np + j + i * nq] = sum_m Q[m, j] P[m, i].
+// P = B (np <= 64 columns -> MMA rows), Q = A (nq columns -> N rows, loaded
+// in boxes of qbox <= 64 columns: grid row blockIdx.y takes columns
+// [blockIdx.y qbox, +qbox) of A).
+// partial[(blockIdx.y gridDim.x + blockIdx.x) qstride np + j + i qstride] =
+// sum_m Q[m, y0 + j] P[m, i] over this CTA's rows.
 // wait_ns bounds every wait; withhold >= 0 (test hook only) makes the TMA
 // producer stop issuing at that iteration, so the consumers' waits run out.
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_tsgram(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUtensorMap mapQ, int np, int nq,
                 int NB, int stages, int64_t nkb, double* __restrict__ partial, int* __restrict__ err,
-                uint64_t wait_ns, int withhold) {
+                uint64_t wait_ns, int withhold, int qbox, int qstride) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // tiles start on a 1024-byte boundary of the shared address space (the
   // 128-byte swizzle pattern repeats every 8 rows of 128 bytes)
@@ -213,7 +221,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (warp == 0) {
     if (lane == 0) {
       // TMA producer
-      const uint32_t bytes = (uint32_t)(np + nq) * 128u;
+      const uint32_t bytes = (uint32_t)(np + qbox) * 128u;
       int issued = 0;
       for (int it = 0; it < nit; ++it) {
         const int s = it % stages;
@@ -226,7 +234,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         mbar_expect_tx(&full[s], bytes);
         const int x = (int)((kb0 + it) * KBLK);
         tma_load_2d(t, &mapP, x, 0, &full[s]);
-        tma_load_2d(t + P_BYTES, &mapQ, x, 0, &full[s]);
+        tma_load_2d(t + P_BYTES, &mapQ, x, (int)blockIdx.y * qbox, &full[s]);
         issued = it + 1;
       }
       // never leave with copies in flight
@@ -255,7 +263,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   } else if (warp >= 4) {
     // converters: B rows r < np -> lo at row 64 + r; A rows r < nq -> lo at row NB + r
     const int ct = threadIdx.x - 128;
-    const int nP = np * 8, nQ = nq * 8;  // 16-byte chunks of the loaded rows
+    const int nP = np * 8, nQ = qbox * 8;  // 16-byte chunks of the loaded rows
     for (int it = 0; it < nit; ++it) {
       const int s = it % stages;
       if (!mbar_wait(&full[s], (it / stages) & 1, abort, wait_ns)) {
@@ -297,7 +305,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
   __syncthreads();
   if (warp < 2) {
-    double* out = partial + (int64_t)blockIdx.x * nq * np;
+    double* out = partial + ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * qstride * np;
+    const int nqe = min(nq - (int)blockIdx.y * qbox, qbox);   // columns of A in this box
     if (have) {
       for (int j0 = 0; j0 < NB; j0 += 8) {
         float a[8], b[8];
@@ -307,12 +316,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
             const int j = j0 + q;
-            if (j < nq) out[j + row * nq] = (double)a[q] + (double)b[q] + (double)xch[row * 64 + j];
+            if (j < nqe) out[j + row * qstride] = (double)a[q] + (double)b[q] + (double)xch[row * 64 + j];
           }
         }
       }
     } else if (row < np) {
-      for (int j = 0; j < nq; ++j) out[j + row * nq] = 0.0;
+      for (int j = 0; j < nqe; ++j) out[j + row * qstride] = 0.0;
     }
   }
   tc_fence_before();
@@ -338,14 +347,14 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 2D map over a column-major M x ncols FP32 matrix: 32-row x ncols boxes,
+// 2D map over a column-major M x ncols FP32 matrix: 32-row x boxcols boxes,
 // 128-byte swizzle (the tcgen05 K-major layout), zero fill past row M.
-bool make_map(CUtensorMap* m, const float* p, int64_t M, int64_t ld, int ncols) {
+bool make_map(CUtensorMap* m, const float* p, int64_t M, int64_t ld, int ncols, int boxcols) {
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {(cuuint64_t)M, (cuuint64_t)ncols};
   cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
-  cuuint32_t box[2] = {(cuuint32_t)KBLK, (cuuint32_t)ncols};
+  cuuint32_t box[2] = {(cuuint32_t)KBLK, (cuuint32_t)boxcols};
   cuuint32_t es[2] = {1, 1};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)p, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
@@ -405,7 +414,7 @@ az_status launch_tc_tsgram(const float* A, int64_t lda, int ka, const float* B, 
   }
   ProfScope ps("proj_tc", (double)M * (ka + kb) * 4.0, st);
   CUtensorMap mP, mQ;
-  if (!make_map(&mP, B, M, ldb, kb) || !make_map(&mQ, A, M, lda, ka)) {
+  if (!make_map(&mP, B, M, ldb, kb, kb) || !make_map(&mQ, A, M, lda, ka, ka)) {
     set_error("tensor-core tall product: cuTensorMapEncodeTiled failed");
     return AZ_ERR_CUDA;
   }
@@ -433,7 +442,7 @@ az_status launch_tc_tsgram(const float* A, int64_t lda, int ka, const float* B, 
       g_hook_withhold = -1;
     }
   }
-  k_tc_tsgram<<<grid, TC_THREADS, sm, st>>>(mP, mQ, kb, ka, NB, stages, nkb, partial, err, wait_ns, withhold);
+  k_tc_tsgram<<<grid, TC_THREADS, sm, st>>>(mP, mQ, kb, ka, NB, stages, nkb, partial, err, wait_ns, withhold, ka, ka);
   {
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
@@ -442,6 +451,92 @@ az_status launch_tc_tsgram(const float* A, int64_t lda, int ka, const float* B, 
     }
   }
   return launch_gram_reduce(partial, grid, ka, kb, G, st);
+}
+
+// ---------------------------------------------------------------- wide A (ka > 64)
+namespace {
+
+// CTAs per 64-column chunk of A: about two waves over the SMs in total
+int wide_splits(int64_t M, int ka) {
+  const int64_t chunks = (ka + 63) / 64;
+  const int64_t nkb = (M + KBLK - 1) / KBLK;
+  const int64_t want = (2 * (int64_t)tc_tsgram_blocks() + chunks - 1) / chunks;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(want, nkb));
+}
+
+// G[(64 c + j) + i ka] = sum over the chunk's CTAs x of partial[(c gx + x) 64 kb + j + 64 i]
+__global__ void k_tc_wide_reduce(const double* __restrict__ partial, int gx, int ka, int kb, double* __restrict__ G) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)ka * kb) return;
+  const int r = (int)(t % ka), i = (int)(t / ka);
+  const int c = r / 64, j = r % 64;
+  const double* p = partial + ((int64_t)c * gx) * 64 * kb + j + 64 * i;
+  double s = 0.0;
+  for (int x = 0; x < gx; ++x) s += p[(int64_t)x * 64 * kb];
+  G[t] = s;
+}
+
+}  // namespace
+
+bool tc_tsgram_wide_ok(const void* A, int64_t lda, int ka, const void* B, int64_t ldb, int kb) {
+  return ka >= 1 && kb >= 1 && kb <= 64 && lda % 4 == 0 && ldb % 4 == 0 && ((uintptr_t)A & 15) == 0 &&
+         ((uintptr_t)B & 15) == 0 && encode_fn() != nullptr;
+}
+
+size_t tc_tsgram_wide_partial(int64_t M, int ka, int kb) {
+  return (size_t)wide_splits(M, ka) * (size_t)((ka + 63) / 64) * 64 * (size_t)kb;
+}
+
+az_status launch_tc_tsgram_wide(const float* A, int64_t lda, int ka, const float* B, int64_t ldb, int kb, int64_t M,
+                                double* partial, double* G, int* err, cudaStream_t st) {
+  if (!tc_tsgram_wide_ok(A, lda, ka, B, ldb, kb) || M < 1) {
+    set_error("tensor-core wide product: unsupported shape or alignment");
+    return AZ_ERR_ARG;
+  }
+  ProfScope ps("proj_tc_wide", (double)M * (ka + kb) * 4.0, st);
+  CUtensorMap mP, mQ;
+  if (!make_map(&mP, B, M, ldb, kb, kb) || !make_map(&mQ, A, M, lda, ka, 64)) {
+    set_error("tensor-core wide product: cuTensorMapEncodeTiled failed");
+    return AZ_ERR_CUDA;
+  }
+  const int NB = 64;
+  int stages = 0;
+  const size_t sm = smem_bytes(NB, &stages);
+  const int64_t nkb = (M + KBLK - 1) / KBLK;
+  const int gx = wide_splits(M, ka);
+  const int chunks = (ka + 63) / 64;
+  {
+    static std::mutex mu;
+    static size_t set_bytes = 0;
+    std::lock_guard<std::mutex> g(mu);
+    if (sm > set_bytes) {
+      AZ_CUDA(cudaFuncSetAttribute(k_tc_tsgram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      set_bytes = sm;
+    }
+  }
+  uint64_t wait_ns = WAIT_NS;
+  int withhold = -1;
+  {
+    std::lock_guard<std::mutex> g(g_hook_mu);
+    if (g_hook_withhold >= 0) {
+      withhold = g_hook_withhold;
+      wait_ns = g_hook_wait_ns;
+      g_hook_withhold = -1;
+    }
+  }
+  k_tc_tsgram<<<dim3(gx, chunks), TC_THREADS, sm, st>>>(mP, mQ, kb, ka, NB, stages, nkb, partial, err, wait_ns,
+                                                        withhold, 64, 64);
+  {
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      set_error(std::string("tensor-core wide product launch: ") + cudaGetErrorString(e));
+      return AZ_ERR_CUDA;
+    }
+  }
+  const int64_t n = (int64_t)ka * kb;
+  k_tc_wide_reduce<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(partial, gx, ka, kb, G);
+  AZ_CUDA(cudaGetLastError());
+  return AZ_OK;
 }
 
 }  // namespace az

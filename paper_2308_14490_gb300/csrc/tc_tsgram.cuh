@@ -20,6 +20,14 @@ bool tc_tsgram_ok(const void* A, int64_t lda, int ka, const void* B, int64_t ldb
 az_status launch_tc_tsgram(const float* A, int64_t lda, int ka, const float* B, int64_t ldb, int kb, int64_t M,
                            double* partial, double* G, int* err, cudaStream_t st);
 int tc_tsgram_blocks();
+
+// The same product for wide A (any ka; kb <= 64): grid rows take 64-column
+// chunks of A, so A is read once and B once per chunk (from L2).  partial:
+// >= tc_tsgram_wide_partial(M, ka, kb) doubles.
+bool tc_tsgram_wide_ok(const void* A, int64_t lda, int ka, const void* B, int64_t ldb, int kb);
+size_t tc_tsgram_wide_partial(int64_t M, int ka, int kb);
+az_status launch_tc_tsgram_wide(const float* A, int64_t lda, int ka, const float* B, int64_t ldb, int kb, int64_t M,
+                                double* partial, double* G, int* err, cudaStream_t st);
 // Test hook: the next launch stops issuing TMA copies at `iteration` (so its
 // consumers' waits run out) and bounds every wait by wait_ns.  One-shot.
 void tc_tsgram_debug_withhold(int iteration, uint64_t wait_ns);
