@@ -1258,19 +1258,49 @@ template <typename T> struct EPT {
   static constexpr int LOGE = E == 16 ? 4 : (E == 8 ? 3 : 2);
 };
 
+// Cache hints of the register passes' single-use traffic (the b gather, and the
+// X1 / X3 intermediates, each written once and read once by the next pass):
+// AZ_STREAM_LD loads them evict-first, AZ_STREAM_ST stores them as streaming.
+#ifndef AZ_STREAM_LD
+#define AZ_STREAM_LD 0
+#endif
+#ifndef AZ_STREAM_ST
+#define AZ_STREAM_ST 0
+#endif
+template <typename V> __device__ __forceinline__ V ld1(const V* p) {
+  if constexpr (AZ_STREAM_LD) return __ldcs(p);
+  else return *p;
+}
+template <typename V> __device__ __forceinline__ void st1(V* p, V v) {
+  if constexpr (AZ_STREAM_ST) __stcs(p, v);
+  else *p = v;
+}
+
 // Compile-time shapes for the register passes.  ShapeRT leaves every size to
 // the Geom at run time; Shape1D<LL, LS, LC> fixes a 1D grid with L = 2^LL,
 // s = 2^LS and 2^LC lines per CTA, so that all FFT index arithmetic folds to
 // constants (the passes are issue-bound, about half of it integer work).
+// THR, MINB: block size and minimum resident blocks of the column passes
+// (FP32, 16 values per thread: 2^LC columns of length D0 need 2^LC D0 / 16
+// threads).
 struct ShapeRT {
   static constexpr bool fixed = false;
   static constexpr int logD1 = 0, logD0 = 0, logN1 = 0, logC = 0;
+  static constexpr int THR = REG_THREADS, MINB = REG_MINB;
 };
 template <int LL, int LS, int LC>
 struct Shape1D {
   static constexpr bool fixed = true;
   static constexpr int logD1 = (LL + 1) / 2, logD0 = LL - logD1, logN1 = logD1 - LS, logC = LC;
+  static constexpr int THR = (1 << LC) * ((1 << logD0) / 16);
+  static constexpr int MINB = THR >= 1024 ? 1 : 1024 / THR;
 };
+// Columns per CTA of the compile-time column passes (L = 2^21, s = 2):
+// 2^AZ_COL_LC columns of 1024, i.e. 8 * 2^AZ_COL_LC bytes of every grid row per
+// CTA for the complex FP32 intermediates.
+#ifndef AZ_COL_LC
+#define AZ_COL_LC 3
+#endif
 template <class S>
 __device__ __forceinline__ Geom fix_geom(const Geom& g) {
   Geom r = g;
@@ -1299,7 +1329,7 @@ __device__ __forceinline__ int kept_row(const Geom& g, const int32_t* __restrict
 static bool is_shape_21_1(const Geom& g) { return g.dim == 1 && g.L == ((int64_t)1 << 21) && g.s[0] == 2; }
 
 template <typename T, int MODE, typename TB, class S>
-__global__ void __launch_bounds__(REG_THREADS, S::fixed ? 4 : REG_MINB) k_colfwd_r(Geom g_in, const int32_t* __restrict__ pos2m, const TB* __restrict__ b,
+__global__ void __launch_bounds__(S::THR, S::MINB) k_colfwd_r(Geom g_in, const int32_t* __restrict__ pos2m, const TB* __restrict__ b,
                                                   int64_t ldb, int ncols, SketchIn<T> in, int pair0, int logC_in,
                                                   typename C2<T>::t* X1base, PassTabs tb) {
   const Geom g = fix_geom<S>(g_in);
@@ -1402,8 +1432,8 @@ __global__ void __launch_bounds__(REG_THREADS, S::fixed ? 4 : REG_MINB) k_colfwd
     V v; v.x = 0; v.y = 0;
     const int m = kept_row(g, pos2m, pos);
     if (m < 0) return v;
-    v.x = cvt<T>(bA[m]);
-    if (colB < ncols) v.y = cvt<T>(bB[m]);
+    v.x = cvt<T>(ld1(bA + m));
+    if (colB < ncols) v.y = cvt<T>(ld1(bB + m));
     return v;
   };
   // four-step twiddle w_L^(n1 k0) (1D), formed from per-butterfly powers
@@ -1417,7 +1447,7 @@ __global__ void __launch_bounds__(REG_THREADS, S::fixed ? 4 : REG_MINB) k_colfwd
   }
   auto epi = [&](int k0, V v, int u, int o0, int Ns) {
     if (g.dim == 1) v = cmul(v, tw.at(twA, twB, n1, u, o0, false));
-    X1[(k0 << g.logD1) + n1] = v;
+    st1(X1 + (k0 << g.logD1) + n1, v);
   };
   fft_reg<V, E, false, PADC>(sm, g.logD0, true, line, tl, 1, C, twp, TW_N >> g.logD0, pro, epi, MODE == 1);
 }
@@ -1452,7 +1482,7 @@ __global__ void __launch_bounds__(REG_THREADS, REG_MINB) k_rowfold_r(Geom g_in, 
     const V* xr = X1 + ((int64_t)row << g.logD1);
     V fwd[16];
     {
-      auto pro = [&](int p) -> V { return xr[p]; };
+      auto pro = [&](int p) -> V { return ld1(xr + p); };
       auto epi = [&](int o, V v, int u, int o0, int Ns) { fwd[u] = v; };
       fft_reg<V, E, false, PADC>(smX, g.logD1, true, lr, tl, g.D1, 1, twp, TW_N >> g.logD1, pro, epi);
     }
@@ -1476,7 +1506,7 @@ __global__ void __launch_bounds__(REG_THREADS, REG_MINB) k_rowfold_r(Geom g_in, 
     };
     auto epi = [&](int n1, V v, int u, int o0, int Ns) {
       v = cmul(v, tw.at(nA, nB, row, u, o0, true));
-      X3[(row << g.logN1) + n1] = v;
+      st1(X3 + (row << g.logN1) + n1, v);
     };
     fft_reg<V, E2, true, PADC>(smF, g.logN1, true, lr, tl, g.N1, 1, twp, TW_N >> g.logN1, pro, epi);
     return;
@@ -1488,7 +1518,7 @@ __global__ void __launch_bounds__(REG_THREADS, REG_MINB) k_rowfold_r(Geom g_in, 
     const int gg = lr >> g.logRg, q = lr & (g.Rg - 1);
     const int row = G0 + gg + q * g.Rstride;
     const V* xr = X1 + ((int64_t)row << g.logD1);
-    auto pro = [&](int p) -> V { return xr[p]; };
+    auto pro = [&](int p) -> V { return ld1(xr + p); };
     auto epi = [&](int o, V v) { smX[padix<PADC>((lr << g.logD1) + o)] = v; };
     fft_reg<V, E, false, PADC>(smX, g.logD1, true, lr, tl, g.D1, 1, twp, TW_N >> g.logD1, pro, epi);
   }
@@ -1526,14 +1556,14 @@ __global__ void __launch_bounds__(REG_THREADS, REG_MINB) k_rowfold_r(Geom g_in, 
     }
     auto epi = [&](int n1, V v, int u, int o0, int Ns) {
       if (g.dim == 1) v = cmul(v, tw.at(nA, nB, k0, u, o0, true));
-      X3[(k0 << g.logN1) + n1] = v;
+      st1(X3 + (k0 << g.logN1) + n1, v);
     };
     fft_reg<V, E2, true, PADC>(smF, g.logN1, true, gg, tl, g.N1, 1, twp, TW_N >> g.logN1, pro, epi);
   }
 }
 
 template <typename T, typename TO, bool WMODE, class S>
-__global__ void __launch_bounds__(REG_THREADS, S::fixed ? 4 : REG_MINB) k_colinv_r(Geom g_in, const typename C2<T>::t* __restrict__ X3base, int pair0,
+__global__ void __launch_bounds__(S::THR, S::MINB) k_colinv_r(Geom g_in, const typename C2<T>::t* __restrict__ X3base, int pair0,
                                                   int ncols, int logC_in, TO* __restrict__ out, int64_t ldo,
                                                   const uint32_t* __restrict__ bits, int64_t nw, PassTabs tb) {
   const Geom g = fix_geom<S>(g_in);
@@ -1553,7 +1583,7 @@ __global__ void __launch_bounds__(REG_THREADS, S::fixed ? 4 : REG_MINB) k_colinv
   TO* oA = out + (int64_t)colA * ldo;
   TO* oB = out + (int64_t)colB * ldo;
   const T sc = (T)(1.0 / (double)g.N);
-  auto pro = [&](int k0) -> V { return X3[(k0 << g.logN1) + n1]; };
+  auto pro = [&](int k0) -> V { return ld1(X3 + (k0 << g.logN1) + n1); };
   auto epi = [&](int n0, V v) {
     const int j = (n0 << g.logN1) + n1;
     T za = v.x * sc, zb = v.y * sc;
@@ -1588,11 +1618,12 @@ az_status launch_colfwd_stencil(const Geom& g, const SketchIn<T>& in, int pair0,
                                 typename C2<T>::t* X1, const PassTabs& tb, cudaStream_t st) {
   using V = typename C2<T>::t;
   if (!reg_ok<T>(g)) return launch_colfwd_stencil_v1<T>(g, in, pair0, npairs, X1, tb, st);
-  const int C = reg_cols<T>(g.D0, g.D1);
+  const bool fx = sizeof(T) == 4 && is_shape_21_1(g);
+  const int C = fx ? 1 << AZ_COL_LC : reg_cols<T>(g.D0, g.D1);
   const int threads = C * (g.D0 / EPT<T>::E);
   size_t sm = ((size_t)padix_host(g.D0 * C, PADC) + 32 + (g.dim == 2 ? (size_t)g.n[0] * C : 0)) * sizeof(V);
   auto kern = k_colfwd_r<T, 1, double, ShapeRT>;
-  if (sizeof(T) == 4 && is_shape_21_1(g) && C == 4) kern = k_colfwd_r<T, 1, double, Shape1D<21, 1, 2>>;
+  if (fx) kern = k_colfwd_r<T, 1, double, Shape1D<21, 1, AZ_COL_LC>>;
   if (set_smem(kern, sm) != cudaSuccess) { set_error("smem attribute"); return AZ_ERR_CUDA; }
   dim3 grid(g.D1 / C, npairs);
   ProfScope ps(sizeof(T) == 4 ? "colfwd_sketch_f32" : "colfwd_sketch_f64", (double)npairs * g.L * sizeof(V) + npairs * 2.0 * g.N / 8 + 4.0 * g.L, st);
@@ -1606,11 +1637,12 @@ az_status launch_colfwd_gather(const Geom& g, const int32_t* pos2m, const TB* b,
                                cudaStream_t st, int64_t M_rows) {
   using V = typename C2<T>::t;
   if (!reg_ok<T>(g)) return launch_colfwd_gather_v1<T, TB>(g, pos2m, b, ldb, ncols, pair0, npairs, X1, tb, st, M_rows);
-  const int C = reg_cols<T>(g.D0, g.D1);
+  const bool fx = sizeof(T) == 4 && is_shape_21_1(g);
+  const int C = fx ? 1 << AZ_COL_LC : reg_cols<T>(g.D0, g.D1);
   const int threads = C * (g.D0 / EPT<T>::E);
   size_t sm = ((size_t)padix_host(g.D0 * C, PADC) + 32) * sizeof(V);
   auto kern = k_colfwd_r<T, 0, TB, ShapeRT>;
-  if (sizeof(T) == 4 && is_shape_21_1(g) && C == 4) kern = k_colfwd_r<T, 0, TB, Shape1D<21, 1, 2>>;
+  if (fx) kern = k_colfwd_r<T, 0, TB, Shape1D<21, 1, AZ_COL_LC>>;
   if (set_smem(kern, sm) != cudaSuccess) { set_error("smem attribute"); return AZ_ERR_CUDA; }
   dim3 grid(g.D1 / C, npairs);
   SketchIn<T> none{};
@@ -1664,19 +1696,20 @@ az_status launch_colinv(const Geom& g, const typename C2<T>::t* X3, int pair0, i
                         cudaStream_t st) {
   using V = typename C2<T>::t;
   if (!reg_ok<T>(g)) return launch_colinv_v1<T, TO>(g, X3, pair0, npairs, ncols, out, ldo, bits, nw, tb, st);
-  const int C = reg_cols<T>(g.G0, g.N1);
+  const bool fx = sizeof(T) == 4 && is_shape_21_1(g);
+  const int C = fx ? 1 << AZ_COL_LC : reg_cols<T>(g.G0, g.N1);
   const int threads = C * (g.G0 / EPT<T>::E);
   size_t sm = ((size_t)padix_host(g.G0 * C, PADC) + 32) * sizeof(V);
   dim3 grid(g.N1 / C, npairs);
   ProfScope ps(sizeof(T) == 4 ? "colinv_f32" : "colinv_f64", (double)npairs * g.N * sizeof(V) + (double)std::min(ncols - 2 * pair0, 2 * npairs) * g.N * sizeof(TO), st);
   if (bits) {
     auto kern = k_colinv_r<T, TO, true, ShapeRT>;
-    if (sizeof(T) == 4 && is_shape_21_1(g) && C == 4) kern = k_colinv_r<T, TO, true, Shape1D<21, 1, 2>>;
+    if (fx) kern = k_colinv_r<T, TO, true, Shape1D<21, 1, AZ_COL_LC>>;
     if (set_smem(kern, sm) != cudaSuccess) { set_error("smem attribute"); return AZ_ERR_CUDA; }
     kern<<<grid, threads, sm, st>>>(g, X3, pair0, ncols, ilog2i(C), out, ldo, bits, nw, tb);
   } else {
     auto kern = k_colinv_r<T, TO, false, ShapeRT>;
-    if (sizeof(T) == 4 && is_shape_21_1(g) && C == 4) kern = k_colinv_r<T, TO, false, Shape1D<21, 1, 2>>;
+    if (fx) kern = k_colinv_r<T, TO, false, Shape1D<21, 1, AZ_COL_LC>>;
     if (set_smem(kern, sm) != cudaSuccess) { set_error("smem attribute"); return AZ_ERR_CUDA; }
     kern<<<grid, threads, sm, st>>>(g, X3, pair0, ncols, ilog2i(C), out, ldo, bits, nw, tb);
   }
