@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--nrhs", type=int, default=NRHS, help="right-hand sides per step (default: the workload's 64)")
     ap.add_argument("--serving-seconds", type=float, default=60.0,
                     help="length of the serving-stream sample (Poisson arrivals, 200 req/s); 0 skips it")
+    ap.add_argument("--traffic-from", default=None,
+                    help="write profiles/ncu_traffic.json from an ncu DRAM-counter CSV of bench.py --lite, then exit")
     ap.add_argument("--lite", action="store_true",
                     help="timed steps only (no e2e, parity, comparator or CPU legs): the small case for profiler captures")
     return ap.parse_args()
@@ -490,6 +492,66 @@ def load_traffic():
     return t.get("kernels", {})
 
 
+# ncu kernel names -> the library's kernel-class labels (ProfScope names)
+TRAFFIC_LABELS = [
+    (r"^k_colfwd_r<float, 0", "colfwd_gather_f32"), (r"^k_colfwd_r<float, 1", "colfwd_sketch_f32"),
+    (r"^k_rowfold_r<float", "rowfold_f32"), (r"^k_colinv_r<float", "colinv_f32"),
+    (r"^k_stencil_rows<float", "stencil_rows_f32"), (r"^k_resid_df", "resid_df"),
+    (r"^k_update_x", "update_x"), (r"^k_tc_tsgram", "proj_tc"), (r"^k_gram_reduce", "gram_reduce"),
+    (r"^k_gram_partial", "gram_df32"), (r"^k_tsprod_df", "tsprod_df32"),
+    (r"^k_small_mm", "small_mm"), (r"^k_factor1", "factor1"), (r"^k_factor2", "factor2"),
+    (r"^k_count|^k_scan_blocks|^k_scatter", "compact"), (r"^k_taps", "taps"),
+    (r"^k_symbol_closed_1d|^k_fold_S|^k_max_abs|^k_H", "symbol"), (r"^k_philox_bits", "philox_bits"),
+]
+
+
+def traffic_from_csv(csv_path, steps=1):
+    """profiles/ncu_traffic.json from the CSV of
+    ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none
+        --csv --log-file <csv> python bench.py --lite --steps <steps> --warmup 3
+    (the launches of the last `steps` timed steps are the run's final launches)."""
+    import csv
+    import re
+    rows = [r for r in csv.reader(open(csv_path)) if len(r) > 10]
+    head = rows[0]
+    ci, cn, cm, cv = head.index("ID"), head.index("Kernel Name"), head.index("Metric Name"), head.index("Metric Value")
+    per = {}
+    for r in rows[1:]:
+        ent = per.setdefault(int(r[ci]), {"name": r[cn]})
+        ent[r[cm]] = float(r[cv].replace(",", ""))
+    ids = sorted(per)
+    # the timed steps' launches: the step's launch count from the run's last az_refactor (k_count)
+    starts = [i for i in ids if per[i]["name"].startswith("k_count")]
+    first = starts[-steps] if len(starts) >= steps else ids[0]
+    kern = {}
+    for i in ids:
+        if i < first:
+            continue
+        nm = per[i]["name"]
+        lab = next((l for rx, l in TRAFFIC_LABELS if re.search(rx, nm)), nm.split("<")[0])
+        e = kern.setdefault(lab, {"dram_bytes_per_step": 0.0, "launches_per_step": 0, "kernels": []})
+        e["dram_bytes_per_step"] += (per[i].get("dram__bytes_read.sum", 0) + per[i].get("dram__bytes_write.sum", 0)) / steps
+        e["launches_per_step"] += 1
+        short = nm.split("(")[0]
+        if short not in e["kernels"]:
+            e["kernels"].append(short)
+    for e in kern.values():
+        e["launches_per_step"] //= steps
+        e["dram_bytes_per_step"] = int(e["dram_bytes_per_step"])
+    out = {"what": "DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per kernel label over the timed step of "
+                   "bench.py --lite (1D N=2^20, k=24, 64 RHS, mixed); a projection label includes its partial-sum "
+                   "reduction launch",
+           "command": "python -c \"import __graft_entry__ as g; g.build()\" && python bench.py --lite --steps 1 --warmup 3 "
+                      "&& ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
+                      "--clock-control none --csv --log-file traffic_lite.csv python bench.py --lite --steps 1 --warmup 3 "
+                      "&& python bench.py --traffic-from traffic_lite.csv",
+           "csrc_sha1": csrc_digest(), "source": "ncu DRAM counters, timed step of bench.py --lite", "kernels": kern}
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
+    return path
+
+
 def plan_bytes(g, M, k, nrhs):
     """Pass-plan byte model of one step (sketch of width k, then the mixed
     refined solve of nrhs right-hand sides) on grid g with M kept points."""
@@ -715,7 +777,9 @@ def run_ours(args):
 
 if __name__ == "__main__":
     a = parse()
-    if a.impl == "reference":
+    if a.traffic_from:
+        print(traffic_from_csv(a.traffic_from))
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_ours(a)
