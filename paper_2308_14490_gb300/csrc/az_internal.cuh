@@ -90,6 +90,20 @@ __device__ __forceinline__ void d2ff_int(double d, float& hi, float& lo) {
   lo = __fmul_rn(sign ? -lf : lf, __uint_as_float((unsigned)(fe - 52) << 23));
 }
 
+// FP64 -> FP32 without branches (integer pipe): round to nearest with ties
+// away from zero on the magnitude; FP32-subnormal inputs flush to a signed
+// zero and values beyond the FP32 range become infinities.  Branch-free, so
+// a caller's loads can all be in flight before any conversion.
+__device__ __forceinline__ float d2f_fast(double d) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+  const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
+  const unsigned sign = hi & 0x80000000u;
+  const unsigned e = (hi >> 20) & 0x7ffu;
+  const unsigned mag = ((((hi & 0x7fffffffu) - 0x38000000u) << 3) | (lo >> 29)) + ((lo >> 28) & 1u);
+  const unsigned r = e < 897u ? 0u : (e > 1150u ? 0x7f800000u : mag);
+  return __uint_as_float(sign | r);
+}
+
 template <typename TO, typename TI> __device__ __forceinline__ TO cvt(TI v) { return (TO)v; }
 template <> __device__ __forceinline__ float cvt<float, double>(double v) { return d2f_int(v); }
 template <> __device__ __forceinline__ double cvt<double, float>(float v) { return f2d_int(v); }

@@ -1426,14 +1426,25 @@ __global__ void __launch_bounds__(S::THR, S::MINB) k_colfwd_r(Geom g_in, const i
   }
   const TB* bA = b ? b + (int64_t)colA * ldb : nullptr;
   const TB* bB = b ? b + (int64_t)colB * ldb : nullptr;
+  const bool hasB = colB < ncols;
   auto pro = [&](int p) -> V {
     if (MODE == 1) return sm[padix<PADC>((p << logC) + line)];
     const int pos = (p << g.logD1) + n1;
-    V v; v.x = 0; v.y = 0;
+    // unconditional loads (row 0 stands in for points outside Omega) and
+    // branch-free conversions, so that all of a thread's loads are in flight
+    // together; the selects then zero the points outside Omega
     const int m = kept_row(g, pos2m, pos);
-    if (m < 0) return v;
-    v.x = cvt<T>(ld1(bA + m));
-    if (colB < ncols) v.y = cvt<T>(ld1(bB + m));
+    const int mc = m < 0 ? 0 : m;
+    const TB a = ld1(bA + mc);
+    const TB c = ld1((hasB ? bB : bA) + mc);
+    V v;
+    if constexpr (sizeof(T) == 4 && sizeof(TB) == 8) {
+      v.x = m < 0 ? 0.f : d2f_fast(a);
+      v.y = (m < 0 || !hasB) ? 0.f : d2f_fast(c);
+    } else {
+      v.x = m < 0 ? (T)0 : cvt<T>(a);
+      v.y = (m < 0 || !hasB) ? (T)0 : cvt<T>(c);
+    }
     return v;
   };
   // four-step twiddle w_L^(n1 k0) (1D), formed from per-butterfly powers

@@ -166,7 +166,7 @@ az_status large_factor_t(LargeK* L, const T* Y, int64_t ldy, T* A, T* Ut, int64_
                          double* sig, FactorInfo* info, cudaStream_t st) {
   const int64_t M = L->M;
   const int k = L->k;
-  ProfScope ps(sizeof(T) == 8 ? "wide_qr_svd_f64" : "wide_qr_svd_f32", 2.0 * M * k * sizeof(T) * 3, st);
+  ProfScope ps(sizeof(T) == 8 ? "wide_geqrf_f64" : "wide_geqrf_f32", 2.0 * M * k * sizeof(T), st, 0);
   AZ_SOL(cusolverDnSetStream(L->sol, st));
   AZ_BLAS(cublasSetStream(L->blas, st));
   AZ_CUDA(cudaMemcpy2DAsync(A, M * sizeof(T), Y, ldy * sizeof(T), M * sizeof(T), k, cudaMemcpyDeviceToDevice, st));
@@ -178,8 +178,10 @@ az_status large_factor_t(LargeK* L, const T* Y, int64_t ldy, T* A, T* Ut, int64_
     AZ_SOL(cusolverDnSgeqrf(L->sol, (int)M, k, (float*)A, (int)M, (float*)L->tau, (float*)L->work, L->lwork_qr,
                             L->devinfo));
   }
+  ps.close();
   k_extract_R<T><<<(k * k + 255) / 256, 256, 0, st>>>(A, M, k, L->R);
   AZ_CUDA(cudaGetLastError());
+  ProfScope ps2(sizeof(T) == 8 ? "wide_orgqr_f64" : "wide_orgqr_f32", 2.0 * M * k * sizeof(T), st, 0);
   if (sizeof(T) == 8) {
     AZ_SOL(cusolverDnDorgqr(L->sol, (int)M, k, k, (double*)A, (int)M, (double*)L->tau, (double*)L->work,
                             L->lwork_qr, L->devinfo + 1));
@@ -187,8 +189,11 @@ az_status large_factor_t(LargeK* L, const T* Y, int64_t ldy, T* A, T* Ut, int64_
     AZ_SOL(cusolverDnSorgqr(L->sol, (int)M, k, k, (float*)A, (int)M, (float*)L->tau, (float*)L->work, L->lwork_qr,
                             L->devinfo + 1));
   }
+  ps2.close();
+  ProfScope ps3("wide_gesvd_f64", 8.0 * 4 * k * k, st, 0);
   AZ_SOL(cusolverDnDgesvd(L->sol, 'A', 'A', k, k, L->R, k, L->S, L->U, k, L->VT, k, (double*)L->work, L->lwork_svd,
                           nullptr, L->devinfo + 2));
+  ps3.close();
   k_svd_outputs<T><<<1, 256, 0, st>>>(L->S, L->U, L->VT, k, tau, floor, L->devinfo, (T*)L->UR, VS, sig, info);
   AZ_CUDA(cudaGetLastError());
   // U_tau = Q U_R (columns beyond the rank are zero)

@@ -1,7 +1,8 @@
 // Launch counting and optional per-kernel CUDA-event timing.
 //
 // Every launcher wraps its launches in a ProfScope.  The launch counter is
-// always maintained; when profiling is enabled (az_profile_begin) the scope
+// always maintained (library calls are timed with nlaunch = 0: they are not
+// this library's kernels); when profiling is enabled (az_profile_begin) the scope
 // also records a start/stop event pair on the launching stream and the
 // algorithmic bytes of the launch (each input read once, each output written
 // once), so that achieved bandwidth = bytes / event time per kernel class.
@@ -26,9 +27,12 @@ struct ProfScope {
     prof_count(nlaunch);
     if (prof_enabled()) { a = prof_event(); b = prof_event(); cudaEventRecord(a, st); }
   }
-  ~ProfScope() {
+  // ends the timed region before the scope does
+  void close() {
     if (a) { cudaEventRecord(b, st); prof_record(name, a, b, bytes, n); }
+    a = nullptr;
   }
+  ~ProfScope() { close(); }
 };
 
 }  // namespace az
