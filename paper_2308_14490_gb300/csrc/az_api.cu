@@ -6,6 +6,7 @@
 #include <string>
 #include <vector>
 
+#include "dfgemm.cuh"
 #include "kernels.cuh"
 #include "lowrank.cuh"
 #include "lowrank_large.cuh"
@@ -62,6 +63,9 @@ struct az_setup_t {
   // the update x = z + W u reads the FP64 W
   bool sk64 = false;
   float* Ut32 = nullptr; // Mtot x k (FP32 copy of Ut, ld ldm)
+  bool prod64 = false;   // FP64-accurate tall products in FP64 arithmetic (eps h < 0.66), else double-float
+  float* xsh = nullptr;  // 2D mixed: x split into FP32 hi + lo for the residual (N x 2 pairs_max each)
+  float* xsl = nullptr;
   double *G = nullptr, *V = nullptr, *lam = nullptr, *B1 = nullptr, *Tm = nullptr, *VS = nullptr, *sig = nullptr;
   double* partial = nullptr;
   FactorInfo* info = nullptr;
@@ -297,6 +301,17 @@ __global__ void k_to_float(const double* in, int64_t ld, int64_t rows, int ncols
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int c = blockIdx.y;
   if (i < rows && c < ncols) out[(int64_t)c * ld + i] = (float)in[(int64_t)c * ld + i];
+}
+
+// x = hi + lo (FP32 pair, 48 bits), column by column
+__global__ void k_split_x(const double* x, int64_t ldx, int64_t N, int ncols, float* hi, float* lo, int64_t ldo) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.y;
+  if (i >= N || c >= ncols) return;
+  float h, l;
+  d2ff_int(x[(int64_t)c * ldx + i], h, l);
+  hi[(int64_t)c * ldo + i] = h;
+  lo[(int64_t)c * ldo + i] = l;
 }
 
 // precision of the stored sketch, W, Y and Ut (FP64 also for the 2D mixed path)
@@ -552,9 +567,10 @@ az_status az_once(az_setup_t* h, const TB* b, int64_t ldb, int ncols, double* x,
   }
   AZ_TRY(launch_small_mm(h->VS, h->k, h->cb, ncols, h->ub, st));
   if (h->sk64 && !Prec<T>::fp64) {
-    // x = z + W u with the FP64 W (the sketch's own precision), FP32 z
-    return launch_update_x<double, float>((const double*)h->W, g.N, h->k, h->ub, (const float*)z, g.N, g.N, ncols,
-                                          x, ldx, accumulate, st);
+    // x = z + W u with the FP64 W (the sketch's own precision), FP32 z, in
+    // double-float (FP64 arithmetic where eps h < 0.66)
+    return launch_df_update<double, float>((const double*)h->W, g.N, h->k, h->ub, ncols, (const float*)z, g.N, g.N,
+                                           x, ldx, accumulate, st, nullptr, h->prod64);
   }
   AZ_TRY((launch_update_x<T, T>((const T*)h->W, g.N, h->k, h->ub, z, g.N, g.N, ncols, x, ldx, accumulate, st,
                                 Prec<T>::fp64 ? nullptr : xf_out, Prec<T>::fp64 ? nullptr : xbase)));
@@ -591,6 +607,26 @@ az_status solve_impl(az_setup_t* h, const double* b, int64_t ldb, int64_t nrhs, 
         const float* tl[4] = {h->tapsL[0], h->tapsL[1], h->tapsL[2], h->tapsL[3]};
         AZ_TRY(launch_resid_df(h->g, h->kind, h->eps, h->idx, h->M, th, tl, h->W64[0], h->W64[1], x1f,
                                h->g.N, bc, ldb, (float*)res, h->Mtot, nc, st));
+        if (h->Mb) {
+          AZ_TRY((launch_boundary_rows<double, double, double, T>(h->g, h->eps, h->bweight, h->bpts, h->bnrm, h->Mb, xc, ldx,
+                                                                  bc + h->M, ldb, 1.0, -1.0, res + h->M, h->Mtot, nc, st)));
+        }
+      } else if (h->sk64 && it == 0) {
+        // 2D mixed: x = x_hi + x_lo (FP32 pair); r = b - A x_hi to about 48
+        // bits on the FP32 pipe (as above), then - A x_lo in FP32 (x_lo is
+        // 2^-24 of x, so its FP32 product is FP64-accurate in the sum)
+        dim3 sg((unsigned)((h->g.N + 255) / 256), nc);
+        k_split_x<<<sg, 256, 0, st>>>(xc, ldx, h->g.N, nc, h->xsh, h->xsl, h->g.N);
+        AZ_CUDA(cudaGetLastError());
+        const float* th[4] = {h->tapsH[0], h->tapsH[1], h->tapsH[2], h->tapsH[3]};
+        const float* tl[4] = {h->tapsL[0], h->tapsL[1], h->tapsL[2], h->tapsL[3]};
+        float* rhi = (float*)h->gb;   // b - A x_hi (the g workspace is free between passes)
+        AZ_TRY(launch_resid_df(h->g, h->kind, h->eps, h->idx, h->M, th, tl, h->W64[0], h->W64[1], h->xsh, h->g.N, bc,
+                               ldb, rhi, h->ldm, nc, st));
+        StencilTaps tp = taps<float>(h);
+        AZ_TRY((launch_stencil_rows<float, float, float, float>(h->g, h->kind, h->eps, h->idx, h->M, tp, h->xsl, h->g.N,
+                                                                rhi, h->ldm, 1.0f, -1.0f, (float*)res, h->Mtot, nc,
+                                                                st)));
         if (h->Mb) {
           AZ_TRY((launch_boundary_rows<double, double, double, T>(h->g, h->eps, h->bweight, h->bpts, h->bnrm, h->Mb, xc, ldx,
                                                                   bc + h->M, ldb, 1.0, -1.0, res + h->M, h->Mtot, nc, st)));
@@ -647,6 +683,10 @@ az_status alloc_workspace(az_setup_t* h) {
   AZ_TRY(dalloc(h, &h->gb, (size_t)h->ldm * cols * tsz));
   AZ_TRY(dalloc(h, &h->rb, (size_t)h->Mtot * cols * tsz));
   if (h->precision == AZ_MIXED && !h->sk64) AZ_TRY(dalloc_t(h, &h->xfb, (size_t)g.N * cols));
+  if (h->sk64) {
+    AZ_TRY(dalloc_t(h, &h->xsh, (size_t)g.N * cols));
+    AZ_TRY(dalloc_t(h, &h->xsl, (size_t)g.N * cols));
+  }
   AZ_TRY(dalloc_t(h, &h->cb, (size_t)h->k * cols));
   AZ_TRY(dalloc_t(h, &h->ub, (size_t)h->k * cols));
   AZ_TRY(dalloc_t(h, &h->normb, (size_t)2 * cols));
@@ -817,6 +857,7 @@ static az_status setup_fixed(const az_grid* gr, const uint8_t* mask, const doubl
   h->kind = kernel == AZ_NEG_LAPLACE_GAUSS ? 1 : 0;
   h->precision = o.precision;
   h->sk64 = o.precision == AZ_MIXED && h->g.dim == 2;
+  h->prod64 = !df_resolves(h->g, eps);
   h->k = o.k;
   h->eps = eps;
   h->tau_svd = o.tau_svd > 0 ? o.tau_svd : 1e-8;
@@ -923,7 +964,7 @@ static az_status setup_fixed(const az_grid* gr, const uint8_t* mask, const doubl
     // takes the Householder route whatever the width.
     if (h->k > kNarrowK || (store64(h) && h->tau_svd < kGramTau)) {
       size_t wb = 0;
-      rc = large_create(&h->wide, h->Mtot, h->k, store64(h), h->Q1, &wb, 2 * h->pairs_max, !df_resolves(g, eps));
+      rc = large_create(&h->wide, h->Mtot, h->k, store64(h), h->Q1, &wb, 2 * h->pairs_max, h->prod64);
       h->bytes += wb;
       if (rc) break;
     } else {

@@ -388,6 +388,20 @@ size_t smem_bytes(int NB, int* stages_out) {
 
 }  // namespace
 
+// The kernel's dynamic shared-memory limit, shared by both launchers and
+// only ever raised (a lower value would break a launch that relies on an
+// earlier, larger setting).
+static az_status ensure_smem(size_t sm) {
+  static std::mutex mu;
+  static size_t set_bytes = 0;
+  std::lock_guard<std::mutex> g(mu);
+  if (sm > set_bytes) {
+    AZ_CUDA(cudaFuncSetAttribute(k_tc_tsgram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    set_bytes = sm;
+  }
+  return AZ_OK;
+}
+
 // test hook (az_debug_tc_withhold): one-shot, read by the next launch
 static std::mutex g_hook_mu;
 static int g_hook_withhold = -1;
@@ -423,15 +437,7 @@ az_status launch_tc_tsgram(const float* A, int64_t lda, int ka, const float* B, 
   const size_t sm = smem_bytes(NB, &stages);
   const int64_t nkb = (M + KBLK - 1) / KBLK;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(nkb, tc_tsgram_blocks()));
-  {
-    static std::mutex mu;
-    static size_t set_bytes = 0;
-    std::lock_guard<std::mutex> g(mu);
-    if (sm > set_bytes) {
-      AZ_CUDA(cudaFuncSetAttribute(k_tc_tsgram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      set_bytes = sm;
-    }
-  }
+  AZ_TRY(ensure_smem(sm));
   uint64_t wait_ns = WAIT_NS;
   int withhold = -1;
   {
@@ -505,15 +511,7 @@ az_status launch_tc_tsgram_wide(const float* A, int64_t lda, int ka, const float
   const int64_t nkb = (M + KBLK - 1) / KBLK;
   const int gx = wide_splits(M, ka);
   const int chunks = (ka + 63) / 64;
-  {
-    static std::mutex mu;
-    static size_t set_bytes = 0;
-    std::lock_guard<std::mutex> g(mu);
-    if (sm > set_bytes) {
-      AZ_CUDA(cudaFuncSetAttribute(k_tc_tsgram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      set_bytes = sm;
-    }
-  }
+  AZ_TRY(ensure_smem(sm));
   uint64_t wait_ns = WAIT_NS;
   int withhold = -1;
   {
