@@ -13,6 +13,7 @@
 #include <string>
 
 #include "dfgemm.cuh"
+#include "hqr.cuh"
 #include "lowrank.cuh"
 #include "tc_tsgram.cuh"
 #include "lowrank_large.cuh"
@@ -56,6 +57,7 @@ struct LargeK {
   double* part = nullptr;    // split-K partials of the double-float projection
   int cols_max = 0;          // right-hand sides per projection call
   bool prod64 = false;       // tall products in FP64 arithmetic (else double-float)
+  HQR* hqr = nullptr;        // FP64 storage: the hand-written blocked Householder QR
 };
 
 static az_status lk_alloc(void** p, size_t bytes) {
@@ -82,8 +84,9 @@ az_status large_create(LargeK** out, int64_t M, int k, bool fp64, void* A_probe,
   const size_t ts = fp64 ? 8 : 4;
   int lq = 0, lo = 0, ls = 0;
   if (fp64) {
-    AZ_SOL(cusolverDnDgeqrf_bufferSize(L->sol, (int)M, k, (double*)A_probe, (int)M, &lq));
-    AZ_SOL(cusolverDnDorgqr_bufferSize(L->sol, (int)M, k, k, (double*)A_probe, (int)M, (double*)A_probe, &lo));
+    size_t hb = 0;
+    AZ_TRY(hqr_create(&L->hqr, M, k, prod64, &hb));
+    tot += hb;
   } else {
     AZ_SOL(cusolverDnSgeqrf_bufferSize(L->sol, (int)M, k, (float*)A_probe, (int)M, &lq));
     AZ_SOL(cusolverDnSorgqr_bufferSize(L->sol, (int)M, k, k, (float*)A_probe, (int)M, (float*)A_probe, &lo));
@@ -117,6 +120,7 @@ az_status large_create(LargeK** out, int64_t M, int k, bool fp64, void* A_probe,
 
 void large_destroy(LargeK* L) {
   if (!L) return;
+  if (L->hqr) hqr_destroy(L->hqr);
   if (L->sol) cusolverDnDestroy(L->sol);
   if (L->blas) cublasDestroy(L->blas);
   for (void* p : {L->work, L->blas_ws, (void*)L->devinfo, L->tau, (void*)L->R, (void*)L->U, (void*)L->VT,
@@ -166,30 +170,26 @@ az_status large_factor_t(LargeK* L, const T* Y, int64_t ldy, T* A, T* Ut, int64_
                          double* sig, FactorInfo* info, cudaStream_t st) {
   const int64_t M = L->M;
   const int k = L->k;
-  ProfScope ps(sizeof(T) == 8 ? "wide_geqrf_f64" : "wide_geqrf_f32", 2.0 * M * k * sizeof(T), st, 0);
   AZ_SOL(cusolverDnSetStream(L->sol, st));
   AZ_BLAS(cublasSetStream(L->blas, st));
   AZ_CUDA(cudaMemcpy2DAsync(A, M * sizeof(T), Y, ldy * sizeof(T), M * sizeof(T), k, cudaMemcpyDeviceToDevice, st));
   AZ_CUDA(cudaMemsetAsync(L->devinfo, 0, 4 * sizeof(int), st));
-  if (sizeof(T) == 8) {
-    AZ_SOL(cusolverDnDgeqrf(L->sol, (int)M, k, (double*)A, (int)M, (double*)L->tau, (double*)L->work, L->lwork_qr,
-                            L->devinfo));
+  if constexpr (sizeof(T) == 8) {
+    // hand-written blocked Householder QR (R above the diagonal of A)
+    AZ_TRY(hqr_factor(L->hqr, (double*)A, M, st));
+    k_extract_R<T><<<(k * k + 255) / 256, 256, 0, st>>>(A, M, k, L->R);
+    AZ_CUDA(cudaGetLastError());
   } else {
+    ProfScope ps("wide_geqrf_f32", 2.0 * M * k * sizeof(T), st, 0);
     AZ_SOL(cusolverDnSgeqrf(L->sol, (int)M, k, (float*)A, (int)M, (float*)L->tau, (float*)L->work, L->lwork_qr,
                             L->devinfo));
-  }
-  ps.close();
-  k_extract_R<T><<<(k * k + 255) / 256, 256, 0, st>>>(A, M, k, L->R);
-  AZ_CUDA(cudaGetLastError());
-  ProfScope ps2(sizeof(T) == 8 ? "wide_orgqr_f64" : "wide_orgqr_f32", 2.0 * M * k * sizeof(T), st, 0);
-  if (sizeof(T) == 8) {
-    AZ_SOL(cusolverDnDorgqr(L->sol, (int)M, k, k, (double*)A, (int)M, (double*)L->tau, (double*)L->work,
-                            L->lwork_qr, L->devinfo + 1));
-  } else {
+    ps.close();
+    k_extract_R<T><<<(k * k + 255) / 256, 256, 0, st>>>(A, M, k, L->R);
+    AZ_CUDA(cudaGetLastError());
+    ProfScope ps2("wide_orgqr_f32", 2.0 * M * k * sizeof(T), st, 0);
     AZ_SOL(cusolverDnSorgqr(L->sol, (int)M, k, k, (float*)A, (int)M, (float*)L->tau, (float*)L->work, L->lwork_qr,
                             L->devinfo + 1));
   }
-  ps2.close();
   ProfScope ps3("wide_gesvd_f64", 8.0 * 4 * k * k, st, 0);
   AZ_SOL(cusolverDnDgesvd(L->sol, 'A', 'A', k, k, L->R, k, L->S, L->U, k, L->VT, k, (double*)L->work, L->lwork_svd,
                           nullptr, L->devinfo + 2));
@@ -198,9 +198,12 @@ az_status large_factor_t(LargeK* L, const T* Y, int64_t ldy, T* A, T* Ut, int64_
   AZ_CUDA(cudaGetLastError());
   // U_tau = Q U_R (columns beyond the rank are zero)
   const T one = 1, zero = 0;
-  if (sizeof(T) == 8) {
-    AZ_TRY((launch_df_update<double, double>((const double*)A, M, k, (const double*)L->UR, k, nullptr, M, M,
-                                             (double*)Ut, ldu, false, st, nullptr, L->prod64)));
+  if constexpr (sizeof(T) == 8) {
+    // Q [U_R; 0] by the reflectors, in reverse panel order
+    AZ_CUDA(cudaMemsetAsync(Ut, 0, (size_t)ldu * k * sizeof(T), st));
+    AZ_CUDA(cudaMemcpy2DAsync(Ut, ldu * sizeof(T), L->UR, (size_t)k * sizeof(T), (size_t)k * sizeof(T), k,
+                              cudaMemcpyDeviceToDevice, st));
+    AZ_TRY(hqr_apply_q(L->hqr, (const double*)A, M, (double*)Ut, ldu, k, st));
   } else {
     AZ_BLAS(cublasSgemm(L->blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)M, k, k, (const float*)&one, (const float*)A, (int)M,
                         (const float*)L->UR, k, (const float*)&zero, (float*)Ut, (int)ldu));
