@@ -29,6 +29,10 @@
  *    synchronisation).
  *  - No exception crosses the ABI.  Every failure returns a status and sets a
  *    thread-local message readable with az_last_error().
+ *  - Environment: AZ_SKETCH_CLUSTER=1 runs the FP64 Z* chain of square 2D grids
+ *    (L = 64, 128, 256 per dimension, s = 2) as one cluster-resident kernel per
+ *    column pair (16-CTA clusters, the grid in distributed shared memory)
+ *    instead of three passes through device memory; read at az_setup.
  *  - Supported sizes: dim 1 or 2; n[d] and s[d] powers of two; s[d] <= 8;
  *    L per dimension <= 2^24 (1D) or <= 4096 (2D).  Other sizes return
  *    AZ_ERR_ARG.

@@ -15,9 +15,9 @@ CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libaz.so")
 SOURCES = ["kernels.cu", "lowrank.cu", "lowrank_large.cu", "tc_tsgram.cu", "az_api.cu", "profile.cu", "noalloc.cu",
-           "dfgemm.cu", "hqr.cu"]
+           "dfgemm.cu", "hqr.cu", "cluster_sketch.cu"]
 HEADERS = ["az_internal.cuh", "fft.cuh", "fft_reg.cuh", "kernels.cuh", "lowrank.cuh", "lowrank_large.cuh", "profile.cuh",
-           "tc_tsgram.cuh", "dfgemm.cuh", "hqr.cuh"]
+           "tc_tsgram.cuh", "dfgemm.cuh", "hqr.cuh", "cluster_sketch.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]

@@ -2,10 +2,12 @@
 // orchestration of the kernels, all stream-ordered.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
 
+#include "cluster_sketch.cuh"
 #include "dfgemm.cuh"
 #include "kernels.cuh"
 #include "lowrank.cuh"
@@ -64,6 +66,9 @@ struct az_setup_t {
   bool sk64 = false;
   float* Ut32 = nullptr; // Mtot x k (FP32 copy of Ut, ld ldm)
   bool prod64 = false;   // FP64-accurate tall products in FP64 arithmetic (eps h < 0.66), else double-float
+  // 2D FP64 Z* chains (sketch, FP64 solves) as one cluster-resident kernel
+  // where the grid allows it (square, L = 64..256, s = 2) and it is enabled
+  bool use_cluster = false;
   float* xsh = nullptr;  // 2D mixed: x split into FP32 hi + lo for the residual (N x 2 pairs_max each)
   float* xsl = nullptr;
   double *G = nullptr, *V = nullptr, *lam = nullptr, *B1 = nullptr, *Tm = nullptr, *VS = nullptr, *sig = nullptr;
@@ -401,6 +406,15 @@ az_status zstar_chain(az_setup_t* h, int mode, const TB* b, int64_t ldb, int nco
   const bool own = mode == 1 && h->X1s;   // the sketch chain on its own workspace
   const int step = own ? h->pairs_s : h->pairs_max;
   if (first_col & 1) { set_error("zstar_chain: odd first column"); return AZ_ERR_ARG; }
+  if constexpr (Prec<T>::fp64 && sizeof(TB) == 8) {
+    if (h->use_cluster && mode != 1) {
+      // the whole chain in one cluster-resident launch per column pair
+      const int p0 = first_col / 2;
+      if (p0 >= npairs_total) return AZ_OK;
+      return launch_zstar_cluster(g, (const double*)b, ldb, ncols, h->pos2m, h->H64, mode != 0 ? h->bits : nullptr,
+                                  h->nw, (double*)zout, ldz, h->tw64, p0, npairs_total - p0, h->tc_err, st);
+    }
+  }
   for (int p0 = first_col / 2; p0 < npairs_total; p0 += step) {
     const int np = std::min(step, npairs_total - p0);
     V* X1 = (V*)(own ? h->X1s : h->X1);
@@ -455,13 +469,13 @@ az_status sketch_and_factor(az_setup_t* h, cudaStream_t st) {
     AZ_CUDA(cudaMemsetAsync(h->info, 0, sizeof(FactorInfo), st));
     return AZ_OK;
   }
-  if (h->kind == 0) {
+  if (h->kind == 0 && !h->use_cluster) {
     // W = (I - Z* A) R through the fused FFT chain (A R by the local stencil)
     AZ_TRY((zstar_chain<T, double>(h, 1, nullptr, 0, k, W, g.N, st, k0)));
   } else {
-    // Collocation: v = A R on all rows by the stencil rows (R materialised in
-    // FP64), then W = R - Z* v through the gather chain (Z* has zero columns
-    // for the boundary rows).
+    // Collocation (and the cluster-resident chain): v = A R on all rows by the
+    // stencil rows (R materialised in FP64), then W = R - Z* v through the
+    // gather chain (Z* has zero columns for the boundary rows).
     T* v = (T*)h->gb;    // Mtot x k scratch (gb holds >= k columns)
     AZ_TRY(launch_bits_to_R(h->bits, g.N, k, h->Rd, st));
     AZ_TRY((apply_rows<T, double, double, T>(h, h->Rd + (size_t)k0 * g.N, g.N, nullptr, 0, (T)0, (T)1,
@@ -933,7 +947,14 @@ static az_status setup_fixed(const az_grid* gr, const uint8_t* mask, const doubl
     if (cudaEventCreateWithFlags(&h->info_ev, cudaEventDisableTiming) != cudaSuccess) { cudaGetLastError(); set_error("event"); rc = AZ_ERR_CUDA; break; }
     if (cudaMemsetAsync(h->tc_err, 0, sizeof(int), st) != cudaSuccess) { cudaGetLastError(); set_error("memset"); rc = AZ_ERR_CUDA; break; }
     rc = dalloc_t(h, &h->Q1, (size_t)std::max<int64_t>(h->Mtot, (h->ldm + 1) / 2) * h->k); if (rc) break;   // also holds FP32 Q1 with ld ldm
-    if (h->kind == 1) { rc = dalloc_t(h, &h->Rd, (size_t)g.N * h->k); if (rc) break; }
+    {
+      // opt-in: AZ_SKETCH_CLUSTER=1 (the chain is FP64-arithmetic bound on
+      // this GPU, where the three-pass chain spreads over every SM and is
+      // faster; both are tested against each other and the oracle)
+      const char* ev = std::getenv("AZ_SKETCH_CLUSTER");
+      h->use_cluster = store64(h) && ev && ev[0] == '1' && zstar_cluster_ok(g, st);
+    }
+    if (h->kind == 1 || h->use_cluster) { rc = dalloc_t(h, &h->Rd, (size_t)g.N * h->k); if (rc) break; }
     for (double** p : {&h->G, &h->V, &h->B1, &h->Tm, &h->VS}) { rc = dalloc_t(h, p, (size_t)h->k * h->k); if (rc) break; }
     if (rc) break;
     rc = dalloc_t(h, &h->lam, h->k); if (rc) break;
