@@ -396,6 +396,45 @@ def config_2d_leg(name, nrhs=64):
     return out
 
 
+def cluster_leg():
+    """The FP64 Z* chain of the config-4 sketch (n = 128, L = 256^2, k = 2048,
+    1024 column pairs) as three passes through device memory (the default)
+    and as the cluster-resident kernel (AZ_SKETCH_CLUSTER=1: one 16-CTA
+    cluster per pair, the grid in distributed shared memory): device time of
+    the chain from CUDA events around its launches during az_setup."""
+    import numpy as np
+    import torch
+    import paper_2308_14490_gb300 as az
+    import workloads as W
+    dev = torch.device("cuda", 0)
+    p = W.config4(n=128, nb=2048, k=2048)
+    g = p.grid
+    mask = torch.from_numpy(np.ascontiguousarray(p.mask.reshape(-1))).to(dev)
+    bnd = torch.from_numpy(np.ascontiguousarray(p.boundary)).to(dev)
+    out = {}
+    for tag, env in (("three_pass", "0"), ("cluster", "1")):
+        os.environ["AZ_SKETCH_CLUSTER"] = env
+        try:
+            opts = az.make_options(az.AZ_FP64, p.k, 1e-8, 0.0, 13, 0)
+            az.az_profile_begin()
+            h = az.az_setup(az.make_grid(2, g.n, g.s, g.T), mask, g.eps, az.AZ_NEG_LAPLACE_GAUSS, bnd, p.weight, opts)
+            prof = az.az_profile_end()
+            az.az_destroy(h)
+        finally:
+            os.environ.pop("AZ_SKETCH_CLUSTER", None)
+        keys = [k for k in prof if k.startswith(("colfwd_", "rowfold_", "colinv_", "zstar_cluster"))]
+        ms = sum(prof[k]["ms"] for k in keys)
+        out[tag] = {"ms": round(ms, 3), "us_per_pair": round(1000.0 * ms / (p.k // 2), 2), "kernels": sorted(keys)}
+    # FP64 flops per pair: forward 2D FFT of the L-grid, inverse of the N-grid (5 n log2 n each), fold
+    L2, N2 = (2 * g.n[0]) ** 2, g.n[0] ** 2
+    flop = 5 * L2 * np.log2(L2) + 5 * N2 * np.log2(N2) + 8 * L2
+    for tag in out:
+        out[tag]["fp64_tflops"] = round(flop * (p.k // 2) / (out[tag]["ms"] / 1000.0) / 1e12, 3)
+    out["what"] = ("config-4 sketch Z* chain (FP64, 1024 column pairs): three passes vs the cluster-resident kernel; "
+                   "FP64-arithmetic bound (peak about 1.26 TFLOP/s on this GPU)")
+    return out
+
+
 def fp64_step_leg(h_grid, mask, b_dev, x_dev, stream, steps=5):
     """The library's own all-FP64 config-2 step (az_refactor + az_solve of 64 RHS)."""
     import torch
@@ -498,7 +537,7 @@ TRAFFIC_LABELS = [
     (r"^k_rowfold_r<float", "rowfold_f32"), (r"^k_colinv_r<float", "colinv_f32"),
     (r"^k_stencil_rows<float", "stencil_rows_f32"), (r"^k_resid_df", "resid_df"),
     (r"^k_update_x", "update_x"), (r"^k_tc_tsgram", "proj_tc"), (r"^k_gram_reduce", "gram_reduce"),
-    (r"^k_gram_partial", "gram_df32"), (r"^k_tsprod_df", "tsprod_df32"),
+    (r"^k_gram_partial", "gram_df32"), (r"^k_tsprod_df", "tsprod_df32"), (r"^k_tsprod<", "tsprod"),
     (r"^k_small_mm", "small_mm"), (r"^k_factor1", "factor1"), (r"^k_factor2", "factor2"),
     (r"^k_count|^k_scan_blocks|^k_scatter", "compact"), (r"^k_taps", "taps"),
     (r"^k_symbol_closed_1d|^k_fold_S|^k_max_abs|^k_H", "symbol"), (r"^k_philox_bits", "philox_bits"),
@@ -521,13 +560,13 @@ def traffic_from_csv(csv_path, steps=1):
         ent[r[cm]] = float(r[cv].replace(",", ""))
     ids = sorted(per)
     # the timed steps' launches: the step's launch count from the run's last az_refactor (k_count)
-    starts = [i for i in ids if per[i]["name"].startswith("k_count")]
+    starts = [i for i in ids if "k_count(" in per[i]["name"]]
     first = starts[-steps] if len(starts) >= steps else ids[0]
     kern = {}
     for i in ids:
         if i < first:
             continue
-        nm = per[i]["name"]
+        nm = re.sub(r"^void\s+", "", per[i]["name"]).replace("az::", "").replace("<unnamed>::", "")
         lab = next((l for rx, l in TRAFFIC_LABELS if re.search(rx, nm)), nm.split("<")[0])
         e = kern.setdefault(lab, {"dram_bytes_per_step": 0.0, "launches_per_step": 0, "kernels": []})
         e["dram_bytes_per_step"] += (per[i].get("dram__bytes_read.sum", 0) + per[i].get("dram__bytes_write.sum", 0)) / steps
@@ -762,7 +801,7 @@ def run_ours(args):
         line["serving"] = serving_leg(args.serving_seconds)
     if rank == 0 and world == 1 and not args.no_context:
         for nm, fn in (("config1", config1_leg), ("config3", lambda: config_2d_leg("config3")),
-                       ("config4", lambda: config_2d_leg("config4"))):
+                       ("config4", lambda: config_2d_leg("config4")), ("cluster_zstar", cluster_leg)):
             try:
                 line[nm] = fn()
             except Exception as ex:  # context, never the headline
