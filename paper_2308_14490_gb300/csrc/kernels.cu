@@ -713,9 +713,25 @@ __global__ void __launch_bounds__(256) k_stencil_rows(Geom g, int kind, T inv2e2
     const int nwin = whi - wlo + 1;
     __shared__ TZ swin[CPT * STENCIL_WIN];
     if (nwin <= STENCIL_WIN) {
-      for (int t = threadIdx.x; t < nc * nwin; t += blockDim.x) {
-        const int c = t / nwin, o = t - c * nwin;
-        swin[c * STENCIL_WIN + o] = zb[(int64_t)(cbase + c) * ldz + ((wlo + o) & Nm)];
+      // staged in batches of SU loads per thread, all in flight before the stores
+      constexpr int SU = 8;
+      const int tot = nc * nwin;
+      for (int t0 = threadIdx.x; t0 < tot; t0 += SU * blockDim.x) {
+        TZ v[SU];
+#pragma unroll
+        for (int u = 0; u < SU; ++u) {
+          const int t = t0 + u * blockDim.x;
+          const int c = t / nwin, o = t - c * nwin;
+          v[u] = t < tot ? zb[(int64_t)(cbase + c) * ldz + ((wlo + o) & Nm)] : (TZ)0;
+        }
+#pragma unroll
+        for (int u = 0; u < SU; ++u) {
+          const int t = t0 + u * blockDim.x;
+          if (t < tot) {
+            const int c = t / nwin, o = t - c * nwin;
+            swin[c * STENCIL_WIN + o] = v[u];
+          }
+        }
       }
       __syncthreads();
       if (act) {
