@@ -924,13 +924,24 @@ static az_status setup_fixed(const az_grid* gr, const uint8_t* mask, const doubl
     {
       std::vector<double> re, im;
       host_twiddles(4096, re, im);
-      std::vector<double2> t64(4096);
-      std::vector<float2> t32(4096);
+      // master table w_4096^j (j < 4096), then the stage table of the
+      // register FFTs: w_m^(b k) = w_4096^(b k 4096/m) at 4096 + 2m - m/b + k
+      // for each span m <= 4096, power of two b <= m/2 and k < m/(2b)
+      constexpr int NT = 4096 + 8192;
+      std::vector<double2> t64(NT);
+      std::vector<float2> t32(NT);
       for (int m = 0; m < 4096; ++m) { t64[m] = make_double2(re[m], im[m]); t32[m] = make_float2((float)re[m], (float)im[m]); }
-      rc = dalloc_t(h, &h->tw64, 4096); if (rc) break;
-      rc = dalloc_t(h, &h->tw32, 4096); if (rc) break;
-      if (cudaMemcpy(h->tw64, t64.data(), 4096 * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess ||
-          cudaMemcpy(h->tw32, t32.data(), 4096 * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess) { rc = AZ_ERR_CUDA; break; }
+      for (int m = 2; m <= 4096; m *= 2)
+        for (int b = 1; 2 * b <= m; b *= 2)
+          for (int k = 0; k < m / (2 * b); ++k) {
+            const int dst = 4096 + 2 * m - m / b + k, src = b * k * (4096 / m);
+            t64[dst] = t64[src];
+            t32[dst] = t32[src];
+          }
+      rc = dalloc_t(h, &h->tw64, NT); if (rc) break;
+      rc = dalloc_t(h, &h->tw32, NT); if (rc) break;
+      if (cudaMemcpy(h->tw64, t64.data(), NT * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess ||
+          cudaMemcpy(h->tw32, t32.data(), NT * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess) { rc = AZ_ERR_CUDA; break; }
       rc = big_tables(h, g.L, &h->big64[0], &h->big64[1], &h->big32[0], &h->big32[1], st); if (rc) break;
       rc = big_tables(h, g.N, &h->big64[2], &h->big64[3], &h->big32[2], &h->big32[3], st); if (rc) break;
     }

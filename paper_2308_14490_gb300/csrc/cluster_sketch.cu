@@ -152,7 +152,7 @@ __global__ void __launch_bounds__((1 << (2 * LOGL)) / 128)
       return v;
     };
     auto epi = [&](int o, V v) { buf[padix<PADS>(line * L + o)] = v; };
-    fft_reg<V, 8, false, PADS>(buf, LOGL, true, line, tl, L, 1, tw, TWN >> LOGL, pro, epi);
+    fft_reg<V, 8, false, PADS>(buf, LOGL, true, line, tl, L, 1, tw + TWN, pro, epi);
   }
   if (!cluster_sync_bounded(cbar, ep++, failed, err, 11)) return;
 
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__((1 << (2 * LOGL)) / 128)
     if (!cluster_sync_bounded(cbar, ep++, failed, err, 12)) return;
     auto pro = [&](int p, int g, int u) -> V { return pre[g * FS::R0 + u]; };
     auto epi = [&](int o, V v) { buf[padix<PADS>(line * L + o)] = v; };   // [ky local][kx]
-    fft_reg<V, 8, false, PADS>(buf, LOGL, true, line, tl, L, 1, tw, TWN >> LOGL, pro, epi);
+    fft_reg<V, 8, false, PADS>(buf, LOGL, true, line, tl, L, 1, tw + TWN, pro, epi);
   }
   if (!cluster_sync_bounded(cbar, ep++, failed, err, 13)) return;
 
@@ -210,7 +210,7 @@ __global__ void __launch_bounds__((1 << (2 * LOGL)) / 128)
     const bool act = line < RX;
     auto pro = [&](int p) -> V { return buf[padix<PADS>(line * L + p)]; };
     auto epi = [&](int o, V v) { buf[padix<PADS>(line * L + o)] = v; };   // [jy local][nx]
-    fft_reg<V, 8, true, PADS>(buf, LOGN1, act, act ? line : 0, tl, L, 1, tw, TWN >> LOGN1, pro, epi, true);
+    fft_reg<V, 8, true, PADS>(buf, LOGN1, act, act ? line : 0, tl, L, 1, tw + TWN, pro, epi, true);
   }
   if (!cluster_sync_bounded(cbar, ep++, failed, err, 14)) return;
 
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__((1 << (2 * LOGL)) / 128)
       oA[j] = za;
       if (hasB) oB[j] = zb;
     };
-    fft_reg<V, 8, true, PADS>(buf, LOGN1, act, act ? line : 0, tl, N1, 1, tw, TWN >> LOGN1, pro, epi);
+    fft_reg<V, 8, true, PADS>(buf, LOGN1, act, act ? line : 0, tl, N1, 1, tw + TWN, pro, epi);
   }
 }
 

@@ -12,6 +12,12 @@
 // of radix 2^(logn mod log E) first, then radix-E stages) so the E values stay
 // in registers.  Every thread of the block must call this (it contains
 // __syncthreads()); threads with active == false only take part in barriers.
+//
+// Twiddles come from the stage table stw: for a span m = Ns R <= 4096 and a
+// power of two b < R, the values w_m^(b k) for k < m / (2b) sit contiguously
+// at stw[2m - m/b + k], so the gathers of a warp's consecutive k read
+// consecutive entries (a strided read of one master table of w_4096 would
+// touch up to one cache line per thread).
 #pragma once
 #include <type_traits>
 
@@ -43,14 +49,14 @@ template <int PADSH> __device__ __forceinline__ int padix(int e) { return e + (e
 
 template <typename V, int E, int LR, bool INV, int PADSH, class Pro, class Epi>
 __device__ __forceinline__ void fft_stage(V (&v)[E], V* __restrict__ sm, int logn, int Ns, bool first, bool last,
-                                          bool active, int line, int tl, int cs, int is, const V* __restrict__ tw,
-                                          int tws, Pro& pro, Epi& epi, bool sync_first) {
+                                          bool active, int line, int tl, int cs, int is, const V* __restrict__ stw,
+                                          Pro& pro, Epi& epi, bool sync_first) {
   constexpr int R = 1 << LR;
   constexpr int NG = E / R;
   const int n = 1 << logn;
   const int nbf = n >> LR;
   const int P = n / E;
-  const int step = n / (Ns * R);
+  const int m = Ns * R;   // span of this stage: its twiddles are w_m^(u k), k < Ns
   if (active) {
 #pragma unroll
     for (int g = 0; g < NG; ++g) {
@@ -74,7 +80,7 @@ __device__ __forceinline__ void fft_stage(V (&v)[E], V* __restrict__ sm, int log
         V w[R];
 #pragma unroll
         for (int b = 1; b < R; b <<= 1) {
-          w[b] = __ldg(tw + ((b * k * step) & (n - 1)) * tws);
+          w[b] = __ldg(stw + 2 * m - m / b + k);
           if (INV) w[b].y = -w[b].y;
         }
 #pragma unroll
@@ -111,7 +117,7 @@ __device__ __forceinline__ void fft_stage(V (&v)[E], V* __restrict__ sm, int log
 // stage must also wait for every thread's reads before storing.
 template <typename V, int E, bool INV, int PADSH, class Pro, class Epi>
 __device__ __forceinline__ void fft_reg(V* __restrict__ sm, int logn, bool active, int line, int tl, int cs, int is,
-                                        const V* __restrict__ tw, int tws, Pro pro, Epi epi, bool sync_first = false) {
+                                        const V* __restrict__ stw, Pro pro, Epi epi, bool sync_first = false) {
   constexpr int LOGE = E == 16 ? 4 : (E == 8 ? 3 : (E == 4 ? 2 : 1));
   V v[E];
   const int r0 = logn % LOGE;
@@ -120,18 +126,18 @@ __device__ __forceinline__ void fft_reg(V* __restrict__ sm, int logn, bool activ
   bool first = true;
   if (r0 != 0) {
     const bool last = nfull == 0;
-    if (r0 == 1) fft_stage<V, E, 1, INV, PADSH>(v, sm, logn, Ns, true, last, active, line, tl, cs, is, tw, tws, pro, epi, sync_first);
+    if (r0 == 1) fft_stage<V, E, 1, INV, PADSH>(v, sm, logn, Ns, true, last, active, line, tl, cs, is, stw, pro, epi, sync_first);
     if constexpr (LOGE > 2) {
-      if (r0 == 2) fft_stage<V, E, 2, INV, PADSH>(v, sm, logn, Ns, true, last, active, line, tl, cs, is, tw, tws, pro, epi, sync_first);
+      if (r0 == 2) fft_stage<V, E, 2, INV, PADSH>(v, sm, logn, Ns, true, last, active, line, tl, cs, is, stw, pro, epi, sync_first);
     }
     if constexpr (LOGE > 3) {
-      if (r0 == 3) fft_stage<V, E, 3, INV, PADSH>(v, sm, logn, Ns, true, last, active, line, tl, cs, is, tw, tws, pro, epi, sync_first);
+      if (r0 == 3) fft_stage<V, E, 3, INV, PADSH>(v, sm, logn, Ns, true, last, active, line, tl, cs, is, stw, pro, epi, sync_first);
     }
     Ns <<= r0;
     first = false;
   }
   for (int st = 0; st < nfull; ++st) {
-    fft_stage<V, E, LOGE, INV, PADSH>(v, sm, logn, Ns, first, st == nfull - 1, active, line, tl, cs, is, tw, tws, pro, epi,
+    fft_stage<V, E, LOGE, INV, PADSH>(v, sm, logn, Ns, first, st == nfull - 1, active, line, tl, cs, is, stw, pro, epi,
                                       first && sync_first);
     Ns <<= LOGE;
     first = false;

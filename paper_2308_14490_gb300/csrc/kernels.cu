@@ -1476,7 +1476,7 @@ __global__ void __launch_bounds__(S::THR, S::MINB) k_colfwd_r(Geom g_in, const i
     if (g.dim == 1) v = cmul(v, tw.at(twA, twB, n1, u, o0, false));
     st1(X1 + (k0 << g.logD1) + n1, v);
   };
-  fft_reg<V, E, false, PADC>(sm, g.logD0, true, line, tl, 1, C, twp, TW_N >> g.logD0, pro, epi, MODE == 1);
+  fft_reg<V, E, false, PADC>(sm, g.logD0, true, line, tl, 1, C, twp + TW_N, pro, epi, MODE == 1);
 }
 
 template <typename T, int E2, class S>
@@ -1511,7 +1511,7 @@ __global__ void __launch_bounds__(REG_THREADS, REG_MINB) k_rowfold_r(Geom g_in, 
     {
       auto pro = [&](int p) -> V { return ld1(xr + p); };
       auto epi = [&](int o, V v, int u, int o0, int Ns) { fwd[u] = v; };
-      fft_reg<V, E, false, PADC>(smX, g.logD1, true, lr, tl, g.D1, 1, twp, TW_N >> g.logD1, pro, epi);
+      fft_reg<V, E, false, PADC>(smX, g.logD1, true, lr, tl, g.D1, 1, twp + TW_N, pro, epi);
     }
     const T* hr = H + ((int64_t)row << g.logD1);
     BigTwPow<V> tw;
@@ -1535,7 +1535,7 @@ __global__ void __launch_bounds__(REG_THREADS, REG_MINB) k_rowfold_r(Geom g_in, 
       v = cmul(v, tw.at(nA, nB, row, u, o0, true));
       st1(X3 + (row << g.logN1) + n1, v);
     };
-    fft_reg<V, E2, true, PADC>(smF, g.logN1, true, lr, tl, g.N1, 1, twp, TW_N >> g.logN1, pro, epi);
+    fft_reg<V, E2, true, PADC>(smF, g.logN1, true, lr, tl, g.N1, 1, twp + TW_N, pro, epi);
     return;
   }
   // forward FFT of the rows: P1 = D1/E threads per row
@@ -1547,7 +1547,7 @@ __global__ void __launch_bounds__(REG_THREADS, REG_MINB) k_rowfold_r(Geom g_in, 
     const V* xr = X1 + ((int64_t)row << g.logD1);
     auto pro = [&](int p) -> V { return ld1(xr + p); };
     auto epi = [&](int o, V v) { smX[padix<PADC>((lr << g.logD1) + o)] = v; };
-    fft_reg<V, E, false, PADC>(smX, g.logD1, true, lr, tl, g.D1, 1, twp, TW_N >> g.logD1, pro, epi);
+    fft_reg<V, E, false, PADC>(smX, g.logD1, true, lr, tl, g.D1, 1, twp + TW_N, pro, epi);
   }
   __syncthreads();
   // fold (prologue of the inverse FFT of length N1, P2 = N1/E2 threads per line)
@@ -1585,7 +1585,7 @@ __global__ void __launch_bounds__(REG_THREADS, REG_MINB) k_rowfold_r(Geom g_in, 
       if (g.dim == 1) v = cmul(v, tw.at(nA, nB, k0, u, o0, true));
       st1(X3 + (k0 << g.logN1) + n1, v);
     };
-    fft_reg<V, E2, true, PADC>(smF, g.logN1, true, gg, tl, g.N1, 1, twp, TW_N >> g.logN1, pro, epi);
+    fft_reg<V, E2, true, PADC>(smF, g.logN1, true, gg, tl, g.N1, 1, twp + TW_N, pro, epi);
   }
 }
 
@@ -1621,7 +1621,7 @@ __global__ void __launch_bounds__(S::THR, S::MINB) k_colinv_r(Geom g_in, const t
     oA[j] = (TO)za;
     if (hasB) oB[j] = (TO)zb;
   };
-  fft_reg<V, E, true, PADC>(sm, g.logG0, true, line, tl, 1, C, (const V*)tb.tw, TW_N >> g.logG0, pro, epi);
+  fft_reg<V, E, true, PADC>(sm, g.logG0, true, line, tl, 1, C, (const V*)tb.tw + TW_N, pro, epi);
 }
 
 // Column count per CTA for the register passes: C * (n / E) threads <= 512.

@@ -40,7 +40,7 @@ az_status launch_philox_bits(uint32_t* bits, int64_t N, int k, uint64_t seed, cu
 az_status launch_bits_to_R(const uint32_t* bits, int64_t N, int k, double* R, cudaStream_t st);
 
 struct PassTabs {
-  const void* tw;        // master twiddle table (4096 entries), float2 or double2
+  const void* tw;        // master twiddle table (4096 entries) then the stage table (8192), float2 or double2
   const void* bigA;      // four-step twiddles for L (1D): w_L^m = bigA[m>>12]*bigB[m&4095]
   const void* bigB;
   const void* bigNA;     // same for N (fold inverse twiddle)
