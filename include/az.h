@@ -264,6 +264,15 @@ int64_t az_launch_count(void);
  * returns AZ_ERR_TIMEOUT once.  One-shot; AZ_ERR_ARG for iteration < 0 or
  * wait_ns <= 0. */
 az_status az_debug_tc_withhold(int32_t iteration, int64_t wait_ns);
+
+/* Test hook for the FP64 output of the mixed path (not part of the paper's
+ * method): out[i] = the FP64 number nearest to a[i] + b[i] (ties to even),
+ * computed by the routine the solve uses to write x = x_fp32 + correction
+ * without FP64 arithmetic; it must equal (double)a[i] + (double)b[i] bit for
+ * bit.  a, b: n FP32 values, out: n FP64 values, all device memory owned by
+ * the caller; enqueued on `stream` (a cudaStream_t, NULL = legacy default),
+ * no synchronisation.  AZ_ERR_ARG for n < 0 or a null pointer with n > 0. */
+az_status az_debug_f32_sum_f64(const float* a, const float* b, double* out, int64_t n, void* stream);
 void az_profile_begin(void);
 az_status az_profile_end(void);
 az_status az_profile_query(int32_t i, char* name, int32_t name_len, int64_t* launches, double* ms,

@@ -65,6 +65,7 @@ _SIGS = {
     "az_rademacher_noalloc": [_I64, _I32, ctypes.c_uint64, _P, _P],
     "az_launch_count": [],
     "az_debug_tc_withhold": [_I32, _I64],
+    "az_debug_f32_sum_f64": [_P, _P, _P, _I64, _P],
     "az_profile_begin": [],
     "az_profile_end": [],
     "az_profile_query": [_I32, ctypes.c_char_p, _I32, ctypes.POINTER(_I64), ctypes.POINTER(_D), ctypes.POINTER(_D)],
@@ -212,6 +213,17 @@ def az_debug_tc_withhold(iteration, wait_ns):
     """Test hook: the next tensor-core projection launch withholds its TMA copies
     from `iteration` on, with waits bounded by wait_ns (see include/az.h)."""
     _check(_lib.az_debug_tc_withhold(int(iteration), int(wait_ns)), "az_debug_tc_withhold")
+
+
+def az_debug_f32_sum_f64(a, b, out, stream=None):
+    """Test hook: out = FP64 nearest to a + b for FP32 device tensors a, b of
+    the same length, by the solve's FP64-pipe-free routine (see include/az.h)."""
+    import torch
+    n = a.numel()
+    if b.numel() != n or out.numel() != n or a.dtype != torch.float32 or b.dtype != torch.float32 \
+            or out.dtype != torch.float64 or not (a.is_contiguous() and b.is_contiguous() and out.is_contiguous()):
+        raise ValueError("az_debug_f32_sum_f64: a, b FP32 and out FP64, contiguous, same length")
+    _check(_lib.az_debug_f32_sum_f64(_ptr(a), _ptr(b), _ptr(out), n, _stream(stream)), "az_debug_f32_sum_f64")
 
 
 def az_last_error():

@@ -751,6 +751,21 @@ az_status az_debug_tc_withhold(int32_t iteration, int64_t wait_ns) {
   return AZ_OK;
 }
 
+__global__ void k_debug_f32_sum(const float* __restrict__ a, const float* __restrict__ b, double* __restrict__ out,
+                                int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = f32_sum_f64(a[i], b[i]);
+}
+
+az_status az_debug_f32_sum_f64(const float* a, const float* b, double* out, int64_t n, void* stream) {
+  if (n < 0 || (n > 0 && (!a || !b || !out))) { set_error("az_debug_f32_sum_f64: bad arguments"); return AZ_ERR_ARG; }
+  if (n == 0) return AZ_OK;
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
+  k_debug_f32_sum<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(a, b, out, n);
+  AZ_CUDA(cudaGetLastError());
+  return AZ_OK;
+}
+
 az_status az_query_footprint(const az_grid* gr, int64_t M, int64_t n_boundary, const az_options* opt, int64_t nrhs_max,
                              size_t* bytes) {
   if (!bytes) { set_error("az_query_footprint: null output"); return AZ_ERR_ARG; }

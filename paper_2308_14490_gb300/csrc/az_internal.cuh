@@ -90,6 +90,33 @@ __device__ __forceinline__ void d2ff_int(double d, float& hi, float& lo) {
   lo = __fmul_rn(sign ? -lf : lf, __uint_as_float((unsigned)(fe - 52) << 23));
 }
 
+// The FP64 number nearest to a + b for FP32 a and b (ties to even), which is
+// (double)a + (double)b, formed without the FP64 pipe: Knuth's two-sum gives
+// s = fl(a + b) and the exact error e (a + b = s + e, |e| <= ulp32(s)/2);
+// e in units of ulp64(s), rounded to an integer, is added to the FP64 bit
+// pattern of s (the carry can never leave the binade of s, and when s is a
+// power of two and e points toward zero the units below s are half as
+// large).  The rounding of that integer is the rounding of the sum, and the
+// FP64 mantissa of s is even, so ties go to even as in the FP64 add.  Sums
+// that are zero, subnormal, below 2^-75 in magnitude, infinite or NaN take
+// the FP64 pipe.
+__device__ __forceinline__ double f32_sum_f64(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bv = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bv)), __fsub_rn(b, bv));
+  const unsigned sb = __float_as_uint(s);
+  const unsigned ex = (sb >> 23) & 0xffu;
+  if (ex < 52u || ex == 255u) return (double)a + (double)b;
+  const bool neg = (sb >> 31) != 0u;
+  const unsigned mant = sb & 0x7fffffu;
+  float es = __fmul_rn(e, __uint_as_float((306u - ex) << 23));   // e / ulp64(s), |es| <= 2^28
+  if (mant == 0u && (neg ? es > 0.f : es < 0.f)) es = __fmul_rn(es, 2.f);
+  const long long r = __float2int_rn(es);
+  const long long mag = (long long)(((unsigned long long)(ex + 896u) << 52) | ((unsigned long long)mant << 29));
+  const long long bits = (mag + (neg ? -r : r)) | (neg ? (long long)0x8000000000000000ull : 0ll);
+  return __longlong_as_double(bits);
+}
+
 // FP64 -> FP32 without branches (integer pipe): round to nearest with ties
 // away from zero on the magnitude; FP32-subnormal inputs flush to a signed
 // zero and values beyond the FP32 range become infinities.  Branch-free, so

@@ -819,7 +819,7 @@ __global__ void __launch_bounds__(256) k_update_x_v4(const float* __restrict__ W
 // in groups of 8, reading u for a group as two 16-byte shared loads per a.
 // Every global access is a contiguous warp transaction (8 bytes of z, 16 of x
 // per lane).
-template <int KB>
+template <int KB, bool ACC64>
 __global__ void __launch_bounds__(256) k_update_x_r2(const float* __restrict__ W, int64_t ldw, int k,
                                                      const double* __restrict__ u, const float* z, int64_t ldz,
                                                      int64_t N, int nrhs, double* x, int64_t ldx, int accumulate,
@@ -838,19 +838,21 @@ __global__ void __launch_bounds__(256) k_update_x_r2(const float* __restrict__ W
   float2 w[KB];
 #pragma unroll
   for (int a = 0; a < KB; ++a) w[a] = a < k ? *(const float2*)(W + (int64_t)a * ldw + j) : make_float2(0.f, 0.f);
+  // x = base + s in FP64: base is the FP32 xbase or zero (ACC64 false: the
+  // FP64 pipe is never used), or the FP64 x itself (ACC64: accumulating
+  // without xbase)
   for (int c0 = 0; c0 < nrhs; c0 += CG) {
     float2 s[CG];
-    double2 xo[CG];
+    float2 xb[CG];
+    double2 xo[ACC64 ? CG : 1];
 #pragma unroll
     for (int q = 0; q < CG; ++q) {
       const int c = c0 + q;
       s[q] = c < nrhs ? *(const float2*)(z + (int64_t)c * ldz + j) : make_float2(0.f, 0.f);
-      xo[q] = make_double2(0.0, 0.0);
-      if (c < nrhs && xbase) {
-        const float2 v = *(const float2*)(xbase + (int64_t)c * ldz + j);
-        xo[q] = make_double2(v.x, v.y);
-      } else if (c < nrhs && accumulate && x) {
-        xo[q] = *(const double2*)(x + (int64_t)c * ldx + j);
+      if constexpr (ACC64) {
+        if (c < nrhs) xo[q] = *(const double2*)(x + (int64_t)c * ldx + j);
+      } else {
+        xb[q] = (c < nrhs && xbase) ? *(const float2*)(xbase + (int64_t)c * ldz + j) : make_float2(0.f, 0.f);
       }
     }
 #pragma unroll
@@ -869,9 +871,15 @@ __global__ void __launch_bounds__(256) k_update_x_r2(const float* __restrict__ W
       const int c = c0 + q;
       if (c >= nrhs) break;
       if (x) {
-        xo[q].x += cvt<double>(s[q].x);
-        xo[q].y += cvt<double>(s[q].y);
-        *(double2*)(x + (int64_t)c * ldx + j) = xo[q];
+        double2 r;
+        if constexpr (ACC64) {
+          r.x = xo[q].x + cvt<double>(s[q].x);
+          r.y = xo[q].y + cvt<double>(s[q].y);
+        } else {
+          r.x = f32_sum_f64(xb[q].x, s[q].x);
+          r.y = f32_sum_f64(xb[q].y, s[q].y);
+        }
+        *(double2*)(x + (int64_t)c * ldx + j) = r;
       }
       if (xf) *(float2*)(xf + (int64_t)c * ldz + j) = s[q];   // exact FP32 copy
     }
@@ -895,13 +903,16 @@ az_status launch_update_x(const TW* W, int64_t ldw, int k, const double* u, cons
       const int nc8 = (nrhs + 7) / 8 * 8;
       const unsigned grid2 = (unsigned)((N / 2 + 255) / 256);
       const int acc = accumulate ? 1 : 0;
-      if (k <= 8) {
-        k_update_x_r2<8><<<grid2, 256, 8 * nc8 * sizeof(float), st>>>(W, ldw, k, u, z, ldz, N, nrhs, x, ldx, acc, xf, xbase);
-      } else if (k <= 16) {
-        k_update_x_r2<16><<<grid2, 256, 16 * nc8 * sizeof(float), st>>>(W, ldw, k, u, z, ldz, N, nrhs, x, ldx, acc, xf, xbase);
-      } else {
-        k_update_x_r2<24><<<grid2, 256, 24 * nc8 * sizeof(float), st>>>(W, ldw, k, u, z, ldz, N, nrhs, x, ldx, acc, xf, xbase);
-      }
+      const bool a64 = accumulate && x && !xbase;
+#define AZ_UPX_R2(KB)                                                                                 \
+  {                                                                                                   \
+    auto kern = a64 ? k_update_x_r2<KB, true> : k_update_x_r2<KB, false>;                             \
+    kern<<<grid2, 256, KB * nc8 * sizeof(float), st>>>(W, ldw, k, u, z, ldz, N, nrhs, x, ldx, acc, xf, xbase); \
+  }
+      if (k <= 8) AZ_UPX_R2(8)
+      else if (k <= 16) AZ_UPX_R2(16)
+      else AZ_UPX_R2(24)
+#undef AZ_UPX_R2
       AZ_LCHECK();
       return AZ_OK;
     }

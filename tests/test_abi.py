@@ -9,7 +9,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     src = open(os.path.join(ROOT, "include", "az.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"\b(az_[A-Za-z_]+)\s*\(", src)
+    names = re.findall(r"\b(az_[A-Za-z0-9_]+)\s*\(", src)
     return sorted(set(n for n in names if n not in ("az_handle",)))
 
 
