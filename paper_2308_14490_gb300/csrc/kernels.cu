@@ -683,6 +683,30 @@ az_status launch_colinv_v1(const Geom& g, const typename C2<T>::t* X3, int pair0
 // One thread per kept point m and a group of CPT columns (index arithmetic and
 // taps shared across the group).
 constexpr int STENCIL_WIN = 512;   // coefficients staged per block and column (1D)
+// b into the arithmetic type of the stencil rows; FP64 -> FP32 branch-free
+// (round to nearest, ties away; the loads of all columns stay in flight)
+template <typename T, typename TB> __device__ __forceinline__ T cvt_b(TB v) {
+  if constexpr (sizeof(T) == 4 && sizeof(TB) == 8) return d2f_fast(v);
+  else return cvt<T>(v);
+}
+// The block's window of coefficients, columns cbase .. cbase + nc - 1 and
+// entries wlo .. wlo + nwin - 1 (periodic index), into swin[c * STENCIL_WIN + o]:
+// a thread takes entries o = threadIdx.x + q blockDim.x and issues the loads
+// of all its columns before any store (no integer division).
+template <typename TZ, int CPT>
+__device__ __forceinline__ void stage_window(TZ* swin, const TZ* __restrict__ zb, int64_t ldz, int cbase, int nc, int wlo,
+                                             int nwin, int Nm) {
+  for (int o = threadIdx.x; o < nwin; o += blockDim.x) {
+    const int64_t jj = (wlo + o) & Nm;
+    TZ v[CPT];
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) v[c] = c < nc ? zb[(int64_t)(cbase + c) * ldz + jj] : (TZ)0;
+#pragma unroll
+    for (int c = 0; c < CPT; ++c)
+      if (c < nc) swin[c * STENCIL_WIN + o] = v[c];
+  }
+  __syncthreads();
+}
 template <typename T, typename TZ, typename TB, typename TO, int CPT>
 __global__ void __launch_bounds__(256) k_stencil_rows(Geom g, int kind, T inv2e2, const int32_t* __restrict__ idx, int M,
                                                       const T* __restrict__ x0, const T* __restrict__ x2,
@@ -713,27 +737,7 @@ __global__ void __launch_bounds__(256) k_stencil_rows(Geom g, int kind, T inv2e2
     const int nwin = whi - wlo + 1;
     __shared__ TZ swin[CPT * STENCIL_WIN];
     if (nwin <= STENCIL_WIN) {
-      // staged in batches of SU loads per thread, all in flight before the stores
-      constexpr int SU = 8;
-      const int tot = nc * nwin;
-      for (int t0 = threadIdx.x; t0 < tot; t0 += SU * blockDim.x) {
-        TZ v[SU];
-#pragma unroll
-        for (int u = 0; u < SU; ++u) {
-          const int t = t0 + u * blockDim.x;
-          const int c = t / nwin, o = t - c * nwin;
-          v[u] = t < tot ? zb[(int64_t)(cbase + c) * ldz + ((wlo + o) & Nm)] : (TZ)0;
-        }
-#pragma unroll
-        for (int u = 0; u < SU; ++u) {
-          const int t = t0 + u * blockDim.x;
-          if (t < tot) {
-            const int c = t / nwin, o = t - c * nwin;
-            swin[c * STENCIL_WIN + o] = v[u];
-          }
-        }
-      }
-      __syncthreads();
+      stage_window<TZ, CPT>(swin, zb, ldz, cbase, nc, wlo, nwin, Nm);
       if (act) {
         for (int j = jlo; j <= jhi; ++j) {
           const T tap = __ldg(x0 + (i - s * j + Wx));
@@ -777,7 +781,7 @@ __global__ void __launch_bounds__(256) k_stencil_rows(Geom g, int kind, T inv2e2
   for (int c = 0; c < CPT; ++c) {
     if (c < nc) {
       T r = beta * acc[c];
-      if (bb) r += alpha * cvt<T>(bv[c]);
+      if (bb) r += alpha * cvt_b<T>(bv[c]);
       outb[(int64_t)(cbase + c) * ldo + m] = cvt<TO>(r);
     }
   }
@@ -817,6 +821,19 @@ __device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, f
   ph = ah * bh;
   pl = fmaf(ah, bh, -ph) + fmaf(ah, bl, al * bh);
 }
+// the staged 1D window: acc[c] += sum_j tap(i - s j) x[j, c] for j in [jlo, jhi]
+template <int CPT, bool FULL>
+__device__ __forceinline__ void resid_win(DFa (&acc)[CPT], const float* swin, int jlo, int jhi, int wlo, int i, int s,
+                                          int Wx, const float* __restrict__ x0h, const float* __restrict__ x0l, int nc) {
+  for (int j = jlo; j <= jhi; ++j) {
+    const int ti = i - s * j + Wx;
+    const float th = __ldg(x0h + ti), tl = __ldg(x0l + ti);
+    const float* w = swin + (j - wlo);
+#pragma unroll
+    for (int c = 0; c < CPT; ++c)
+      if (FULL || c < nc) dfa_add(acc[c], w[c * STENCIL_WIN], th, tl);
+  }
+}
 template <int CPT>
 __global__ void __launch_bounds__(256) k_resid_df(Geom g, int kind, double inv2e2, const int32_t* __restrict__ idx, int M,
                                                   const float* __restrict__ x0h, const float* __restrict__ x0l,
@@ -844,19 +861,11 @@ __global__ void __launch_bounds__(256) k_resid_df(Geom g, int kind, double inv2e
     const int nwin = whi - wlo + 1;
     __shared__ float swin[CPT * STENCIL_WIN];
     if (nwin <= STENCIL_WIN) {
-      for (int t = threadIdx.x; t < nc * nwin; t += blockDim.x) {
-        const int c = t / nwin, o = t - c * nwin;
-        swin[c * STENCIL_WIN + o] = xf[(int64_t)(cbase + c) * ldx + ((wlo + o) & Nm)];
-      }
-      __syncthreads();
+      stage_window<float, CPT>(swin, xf, ldx, cbase, nc, wlo, nwin, Nm);
       if (act) {
-        for (int j = jlo; j <= jhi; ++j) {
-          const int ti = i - s * j + Wx;
-          const float th = __ldg(x0h + ti), tl = __ldg(x0l + ti);
-#pragma unroll
-          for (int c = 0; c < CPT; ++c)
-            if (c < nc) dfa_add(acc[c], swin[c * STENCIL_WIN + (j - wlo)], th, tl);
-        }
+        // block-uniform: a full group of CPT columns runs without per-column predicates
+        if (nc == CPT) resid_win<CPT, true>(acc, swin, jlo, jhi, wlo, i, s, Wx, x0h, x0l, nc);
+        else resid_win<CPT, false>(acc, swin, jlo, jhi, wlo, i, s, Wx, x0h, x0l, nc);
       }
     } else if (act) {
       for (int j = jlo; j <= jhi; ++j) {
