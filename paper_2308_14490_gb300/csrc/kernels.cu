@@ -708,7 +708,7 @@ __device__ __forceinline__ void stage_window(TZ* swin, const TZ* __restrict__ zb
   __syncthreads();
 }
 template <typename T, typename TZ, typename TB, typename TO, int CPT>
-__global__ void __launch_bounds__(256) k_stencil_rows(Geom g, int kind, T inv2e2, const int32_t* __restrict__ idx, int M,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 5) k_stencil_rows(Geom g, int kind, T inv2e2, const int32_t* __restrict__ idx, int M,
                                                       const T* __restrict__ x0, const T* __restrict__ x2,
                                                       const T* __restrict__ y0, const T* __restrict__ y2, int Wx, int Wy,
                                                       const TZ* __restrict__ zb, int64_t ldz, const TB* __restrict__ bb,
@@ -719,10 +719,6 @@ __global__ void __launch_bounds__(256) k_stencil_rows(Geom g, int kind, T inv2e2
   const int cbase = blockIdx.y * CPT;
   const int nc = min(CPT, ncols - cbase);
   const int i = act ? __ldg(idx + m) : 0;
-  // the b values are independent of the stencil: issue their loads first
-  TB bv[CPT];
-#pragma unroll
-  for (int c = 0; c < CPT; ++c) bv[c] = (bb && act && c < nc) ? bb[(int64_t)(cbase + c) * ldb + m] : (TB)0;
   T acc[CPT];
 #pragma unroll
   for (int c = 0; c < CPT; ++c) acc[c] = 0;
@@ -777,6 +773,10 @@ __global__ void __launch_bounds__(256) k_stencil_rows(Geom g, int kind, T inv2e2
     }
   }
   if (!act) return;
+  // b after the stencil: its registers stay free during the window loop
+  TB bv[CPT];
+#pragma unroll
+  for (int c = 0; c < CPT; ++c) bv[c] = (bb && c < nc) ? bb[(int64_t)(cbase + c) * ldb + m] : (TB)0;
 #pragma unroll
   for (int c = 0; c < CPT; ++c) {
     if (c < nc) {
