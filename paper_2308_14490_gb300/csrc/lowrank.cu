@@ -364,21 +364,26 @@ __device__ int jacobi_onesided(TJ* a, int m, int n, TJ* V, int* flag, double flo
   __shared__ TJ fro2;
   // identity V; ||a||_F^2 is invariant under the rotations and sets the level
   // below which column pairs are rounding noise and are left alone
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) V[t] = (t % n == t / n) ? (TJ)1 : (TJ)0;
-  if (threadIdx.x == 0) {
+  for (int c = warp; c < n; c += nwarps)
+    for (int r = lane; r < n; r += 32) V[c * n + r] = (r == c) ? (TJ)1 : (TJ)0;
+  if (threadIdx.x == 0) fro2 = 0;
+  __syncthreads();
+  {
     TJ f = 0;
-    for (int t = 0; t < m * n; ++t) f += a[t] * a[t];
-    fro2 = f;
+    for (int t = threadIdx.x; t < m * n; t += blockDim.x) f += a[t] * a[t];
+    for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+    if (lane == 0) atomicAdd(&fro2, f);
   }
   __syncthreads();
   // a pair is orthogonal to working precision once |gamma| is below the
   // rounding level of the larger column against the whole matrix (floor_rel;
   // 0 = plain relative criterion)
-  const TJ fro = sqrt(fro2);
-  // relative orthogonality reachable by an m-term dot product in TJ
+  // relative orthogonality reachable by an m-term dot product in TJ; the
+  // tests below compare squares (|g| > f sqrt(x)  <=>  g^2 > f^2 x)
   const TJ ueps = sizeof(TJ) == 8 ? (TJ)1.1e-16 : (TJ)6e-8;
   const TJ reltol = fmax((TJ)(10 * ueps), (TJ)(2 * m) * ueps);
-  const TJ flr = (TJ)floor_rel;
+  const TJ rel2 = reltol * reltol;
+  const TJ flr2 = (TJ)floor_rel * (TJ)floor_rel * fro2;
   const int nn = (n + 1) & ~1;  // even count for round-robin (a dummy column if n odd)
   int sweeps = 0;
   for (int sweep = 0; sweep < 30; ++sweep) {
@@ -407,10 +412,26 @@ __device__ int jacobi_onesided(TJ* a, int m, int n, TJ* V, int* flag, double flo
           be += __shfl_xor_sync(0xffffffffu, be, o);
           ga += __shfl_xor_sync(0xffffffffu, ga, o);
         }
-        if (fabs(ga) > flr * fro * sqrt(fmax(al, be)) && fabs(ga) > reltol * sqrt(al * be)) {
-          TJ zeta = (be - al) / ((TJ)2 * ga);
-          TJ t = (zeta >= 0 ? (TJ)1 : (TJ)-1) / (fabs(zeta) + sqrt((TJ)1 + zeta * zeta));
-          TJ c = (TJ)1 / sqrt((TJ)1 + t * t), s = c * t;
+        const TJ ga2 = ga * ga;
+        if (ga2 > flr2 * fmax(al, be) && ga2 > rel2 * (al * be)) {
+          TJ c, s;
+          if constexpr (sizeof(TJ) == 4) {
+            // the rotation angle only steers convergence (fast divides); the
+            // cosine is normalised to working precision (rsqrt and one Newton
+            // step), so that c^2 + s^2 = 1 and V stays orthogonal
+            const float zeta = __fdividef(be - al, 2.f * ga);
+            const float t = __fdividef(zeta >= 0.f ? 1.f : -1.f, fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+            const float x = fmaf(t, t, 1.f);
+            float r = rsqrtf(x);
+            r = r * fmaf(-0.5f * x, r * r, 1.5f);
+            c = r;
+            s = r * t;
+          } else {
+            TJ zeta = (be - al) / ((TJ)2 * ga);
+            TJ t = (zeta >= 0 ? (TJ)1 : (TJ)-1) / (fabs(zeta) + sqrt((TJ)1 + zeta * zeta));
+            c = (TJ)1 / sqrt((TJ)1 + t * t);
+            s = c * t;
+          }
           for (int r = lane; r < m; r += 32) {
             TJ x = a[i * m + r], y = a[j * m + r];
             a[i * m + r] = c * x - s * y;
@@ -446,7 +467,8 @@ __global__ void k_factor1(const double* __restrict__ G1, int k, double tol, doub
   double* R = G + k * k;           // r1 x k rows (ld k): R[i*k + c]
   __shared__ int perm[64];
   __shared__ int piv, r1s, stop;
-  __shared__ double dmax;
+  __shared__ double dmax, dpiv, rdpiv;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   for (int t = threadIdx.x; t < k * k; t += blockDim.x) { G[t] = G1[t]; R[t] = 0.0; }
   for (int t = threadIdx.x; t < k; t += blockDim.x) perm[t] = t;
   if (threadIdx.x == 0) { r1s = 0; stop = 0; }
@@ -473,6 +495,8 @@ __global__ void k_factor1(const double* __restrict__ G1, int k, double tol, doub
         if (j == 0) dmax = best;
         if (!(best > tol * dmax) || !(best > floor2) || !isfinite(best)) stop = 1;
         piv = p;
+        // the pivot's square root and its reciprocal, once
+        if (!stop) { dpiv = sqrt(best); rdpiv = 1.0 / dpiv; }
       }
     }
     __syncthreads();
@@ -492,13 +516,11 @@ __global__ void k_factor1(const double* __restrict__ G1, int k, double tol, doub
       if (threadIdx.x == 0) { int u = perm[j]; perm[j] = perm[p]; perm[p] = u; }
       __syncthreads();
     }
-    const double d = sqrt(G[j * k + j]);
-    for (int c = j + threadIdx.x; c < k; c += blockDim.x) R[j * k + c] = (c == j) ? d : G[c * k + j] / d;
+    const double d = dpiv, rd = rdpiv;
+    for (int c = j + threadIdx.x; c < k; c += blockDim.x) R[j * k + c] = (c == j) ? d : G[c * k + j] * rd;
     __syncthreads();
-    for (int t = threadIdx.x; t < (k - j - 1) * (k - j - 1); t += blockDim.x) {
-      const int i = j + 1 + t % (k - j - 1), c = j + 1 + t / (k - j - 1);
-      G[c * k + i] -= R[j * k + i] * R[j * k + c];
-    }
+    for (int c = j + 1 + warp; c < k; c += nwarps)
+      for (int i = j + 1 + lane; i < k; i += 32) G[c * k + i] -= R[j * k + i] * R[j * k + c];
     if (threadIdx.x == 0) r1s = j + 1;
     __syncthreads();
   }
@@ -512,7 +534,7 @@ __global__ void k_factor1(const double* __restrict__ G1, int k, double tol, doub
   for (int c = threadIdx.x; c < k; c += blockDim.x) {
     for (int i = 0; i < k; ++i) B1[(int64_t)c * k + i] = 0.0;
     if (c < r1) {
-      double y[64];
+      double* y = G + (size_t)c * k;   // G is free after the Cholesky; column c is this thread's
       for (int i = r1 - 1; i >= 0; --i) {
         double sacc = (i == c) ? 1.0 : 0.0;
         for (int l = i + 1; l < r1; ++l) sacc -= R[i * k + l] * y[l];
@@ -568,20 +590,23 @@ __global__ void k_factor2(const double* __restrict__ G2, int k, const double* __
     if (i <= j) R[j * k + i] = G2[(int64_t)j * k + i];
   }
   __syncthreads();
+  __shared__ double rdj;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   for (int j = 0; j < r1; ++j) {
     if (threadIdx.x == 0) {
       double d = R[j * k + j];
       if (!(d > 0.0) || !isfinite(d)) { fail = 1; d = 1.0; }
-      R[j * k + j] = sqrt(d);
+      const double sd = sqrt(d);
+      R[j * k + j] = sd;
+      rdj = 1.0 / sd;
     }
     __syncthreads();
-    const double djj = R[j * k + j];
-    for (int c = j + 1 + threadIdx.x; c < r1; c += blockDim.x) R[c * k + j] /= djj;
+    const double rd = rdj;
+    for (int c = j + 1 + threadIdx.x; c < r1; c += blockDim.x) R[c * k + j] *= rd;
     __syncthreads();
-    for (int t = threadIdx.x; t < r1 * r1; t += blockDim.x) {
-      int i = t % r1, c = t / r1;
-      if (i > j && c >= i) R[c * k + i] -= R[i * k + j] * R[c * k + j];
-    }
+    // trailing update of the upper triangle, j < i <= c < r1
+    for (int c = j + 1 + warp; c < r1; c += nwarps)
+      for (int i = j + 1 + lane; i <= c; i += 32) R[c * k + i] -= R[i * k + j] * R[c * k + j];
     __syncthreads();
   }
   // A = Rs^T = R1P^T R2^T : A[c, i] = sum_{l >= i} R1P[l, c] R2[i, l]  (R2 upper)
@@ -655,6 +680,12 @@ __global__ void k_factor2(const double* __restrict__ G2, int k, const double* __
   // solved in a shared-memory scratch (after the sort buffers) and written out once
   {
     double* Ts = (double*)((int*)(sg + k) + k + (k & 1)) + (size_t)k * k;   // after rank + sort scratch
+    __shared__ double rdiag[64], rsg2[64];
+    for (int i = threadIdx.x; i < r1; i += blockDim.x) {
+      rdiag[i] = 1.0 / R[i * k + i];
+      rsg2[i] = i < r ? 1.0 / (sg[i] * sg[i]) : 0.0;
+    }
+    __syncthreads();
     for (int c = threadIdx.x; c < k; c += blockDim.x) {
       double* tc = Ts + (size_t)c * k;
       for (int i = 0; i < k; ++i) tc[i] = 0.0;
@@ -662,17 +693,15 @@ __global__ void k_factor2(const double* __restrict__ G2, int k, const double* __
         for (int i = r1 - 1; i >= 0; --i) {
           double sacc = VR[c * r1 + i];
           for (int l = i + 1; l < r1; ++l) sacc -= R[l * k + i] * tc[l];
-          tc[i] = sacc / R[i * k + i];
+          tc[i] = sacc * rdiag[i];
         }
       }
     }
     __syncthreads();
     for (int t = threadIdx.x; t < k * k; t += blockDim.x) T[t] = Ts[t];
-  }
-  // VS = V_R[:, :r] Sigma^{-1} = A[:, c] / sigma_c^2
-  for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
-    const int i = t % k, c = t / k;
-    VS[t] = c < r ? A[c * k + i] / (sg[c] * sg[c]) : 0.0;
+    // VS = V_R[:, :r] Sigma^{-1} = A[:, c] / sigma_c^2
+    for (int c = warp; c < k; c += nwarps)
+      for (int i = lane; i < k; i += 32) VS[c * k + i] = c < r ? A[c * k + i] * rsg2[c] : 0.0;
   }
   for (int t = threadIdx.x; t < k; t += blockDim.x) sig[t] = t < r1 ? sg[t] : 0.0;
 }
