@@ -273,6 +273,18 @@ az_status az_debug_tc_withhold(int32_t iteration, int64_t wait_ns);
  * the caller; enqueued on `stream` (a cudaStream_t, NULL = legacy default),
  * no synchronisation.  AZ_ERR_ARG for n < 0 or a null pointer with n > 0. */
 az_status az_debug_f32_sum_f64(const float* a, const float* b, double* out, int64_t n, void* stream);
+
+/* Test hook for the first Gram of the mixed factorisation (G1 = Y^T Y of the
+ * sketch, the SVQB pass that replaces the SVD of Sec. 3.2.3): G (k x k FP64,
+ * column-major, device) = Y^T Y for Y (M x k FP32, column-major, leading
+ * dimension ldy, device) by route 0, exact FP32 products with double-float
+ * sums on the FP32 pipe, or route 1, the exact split on the tensor cores (BF16
+ * slices of the power-of-two-scaled columns, per-CTA slice-pair sums exact in
+ * FP32, FP64 fold; k <= 24, ldy a multiple of 4, Y 16-byte aligned).  Both
+ * are what az_setup uses.  Allocates its own scratch and synchronises
+ * `stream` (a cudaStream_t, NULL = legacy default).  AZ_ERR_ARG for bad
+ * sizes; AZ_ERR_TIMEOUT if a tensor-core pipeline wait ran out. */
+az_status az_debug_gram(const float* Y, int64_t ldy, int32_t k, int64_t M, double* G, int32_t route, void* stream);
 void az_profile_begin(void);
 az_status az_profile_end(void);
 az_status az_profile_query(int32_t i, char* name, int32_t name_len, int64_t* launches, double* ms,

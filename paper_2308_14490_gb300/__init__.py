@@ -66,6 +66,7 @@ _SIGS = {
     "az_launch_count": [],
     "az_debug_tc_withhold": [_I32, _I64],
     "az_debug_f32_sum_f64": [_P, _P, _P, _I64, _P],
+    "az_debug_gram": [_P, _I64, _I32, _I64, _P, _I32, _P],
     "az_profile_begin": [],
     "az_profile_end": [],
     "az_profile_query": [_I32, ctypes.c_char_p, _I32, ctypes.POINTER(_I64), ctypes.POINTER(_D), ctypes.POINTER(_D)],
@@ -224,6 +225,14 @@ def az_debug_f32_sum_f64(a, b, out, stream=None):
             or out.dtype != torch.float64 or not (a.is_contiguous() and b.is_contiguous() and out.is_contiguous()):
         raise ValueError("az_debug_f32_sum_f64: a, b FP32 and out FP64, contiguous, same length")
     _check(_lib.az_debug_f32_sum_f64(_ptr(a), _ptr(b), _ptr(out), n, _stream(stream)), "az_debug_f32_sum_f64")
+
+
+def az_debug_gram(Y, G, route, stream=None):
+    """Test hook: G (k, k) float64 = Y^T Y for Y (k, M) float32 CUDA tensor
+    viewed column-major (row c of the tensor is column c); route 0 double-float
+    SIMT, route 1 exact tensor-core split (see include/az.h)."""
+    k, M = Y.shape
+    _check(_lib.az_debug_gram(_ptr(Y), _ld(Y), int(k), int(M), _ptr(G), int(route), _stream(stream)), "az_debug_gram")
 
 
 def az_last_error():

@@ -489,8 +489,13 @@ az_status sketch_and_factor(az_setup_t* h, cudaStream_t st) {
     // wide sketch: Householder QR of Y (Q into the Q1 scratch), SVD of R
     return large_factor(h->wide, Y, h->Mtot, h->Q1, h->Ut, h->ldm, h->tau_svd, h->floor, h->VS, h->sig, h->info, st);
   }
-  // pass 1: G1 = Y^T Y, SVQB
-  AZ_TRY((launch_gram<T, T>(Y, h->Mtot, k, Y, h->Mtot, k, h->Mtot, h->partial, h->G, st)));
+  // pass 1: G1 = Y^T Y, SVQB; an FP32 sketch takes the exact tensor-core
+  // Gram (BF16 slices, FP64 fold) where its shape allows, else double-float
+  if (!Prec<T>::fp64 && tc_gram_oz_ok(Y, h->Mtot, k, h->Mtot)) {
+    AZ_TRY(launch_tc_gram_oz((const float*)Y, h->Mtot, k, h->Mtot, h->partial, h->G, h->tc_err, st));
+  } else {
+    AZ_TRY((launch_gram<T, T>(Y, h->Mtot, k, Y, h->Mtot, k, h->Mtot, h->partial, h->G, st)));
+  }
   const double taug = Prec<T>::fp64 ? kGramTau : 1e-7;
   AZ_TRY(launch_factor1(h->G, k, taug, h->floor * h->floor, h->V, h->lam, h->B1, h->info, st));
   // pass 2: Q1 = Y B1, G2 = Q1^T Q1, Cholesky, SVD of the small factor, Ut = Q1 T
@@ -764,6 +769,40 @@ az_status az_debug_f32_sum_f64(const float* a, const float* b, double* out, int6
   k_debug_f32_sum<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(a, b, out, n);
   AZ_CUDA(cudaGetLastError());
   return AZ_OK;
+}
+
+az_status az_debug_gram(const float* Y, int64_t ldy, int32_t k, int64_t M, double* G, int32_t route, void* stream) {
+  if (!Y || !G || k < 1 || k > 64 || M < 1 || ldy < M || (route != 0 && route != 1)) {
+    set_error("az_debug_gram: bad arguments");
+    return AZ_ERR_ARG;
+  }
+  if (route == 1 && !tc_gram_oz_ok(Y, ldy, k, M)) {
+    set_error("az_debug_gram: the tensor-core route needs k <= 24, ldy a multiple of 4 and 16-byte aligned Y");
+    return AZ_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t nb = (size_t)std::max(gram_blocks(M), tc_gram_oz_blocks(M));
+  double* partial = nullptr;
+  int* err = nullptr;
+  AZ_CUDA(cudaMalloc((void**)&partial, nb * k * k * sizeof(double)));
+  az_status rc = AZ_OK;
+  if (cudaMalloc((void**)&err, sizeof(int)) != cudaSuccess || cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) {
+    set_error("az_debug_gram: scratch");
+    rc = AZ_ERR_CUDA;
+  }
+  if (rc == AZ_OK) {
+    rc = route == 1 ? launch_tc_gram_oz(Y, ldy, k, M, partial, G, err, st)
+                    : launch_gram<float, float>(Y, ldy, k, Y, ldy, k, M, partial, G, st);
+  }
+  int e = 0;
+  if (cudaStreamSynchronize(st) != cudaSuccess) rc = AZ_ERR_CUDA;
+  if (err && cudaMemcpy(&e, err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && e != 0 && rc == AZ_OK) {
+    set_error(tc_wait_message(e));
+    rc = AZ_ERR_TIMEOUT;
+  }
+  cudaFree(partial);
+  if (err) cudaFree(err);
+  return rc;
 }
 
 az_status az_query_footprint(const az_grid* gr, int64_t M, int64_t n_boundary, const az_options* opt, int64_t nrhs_max,

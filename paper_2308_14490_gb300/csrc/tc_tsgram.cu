@@ -21,6 +21,7 @@
 // MMAs, frees its tensor memory and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_bf16.h>
 
 #include <algorithm>
 #include <mutex>
@@ -386,6 +387,249 @@ size_t smem_bytes(int NB, int* stages_out) {
   return 1024 + (size_t)stages * SB + XCH_BYTES + (3 * stages + 1) * 8 + 16;
 }
 
+
+// ---------------------------------------------------------------- exact Gram on BF16 slices
+// G = Y^T Y for FP32 Y (M x k, k <= OZ_KMAX) on the tensor cores, to FP64
+// accuracy, with an exact split in the manner of Ozaki et al.: every column a
+// is scaled by 2^-E_a into [-1/2, 1/2) (E_a from the largest magnitude of the
+// column in the CTA's rows, a first pass), and each scaled value is cut into six slices
+// s_i = t_i 2^(-8i), |t_i| <= 128 an integer (so s_i is exact in BF16),
+// covering 48 bits below the column's scale.  The product of two slices is an
+// integer multiple of 2^(-8(i+j)) below 2^14 in units; a CTA sums at most
+// OZ_ROWS = 1024 rows, so every per-CTA sum of one slice pair is an integer
+// below 2^24 units, exact in the FP32 accumulator whatever the order.  The
+// operand holds rows (i, a) = slice i of column a, i < 6, in one K-major
+// 128-byte-swizzled tile per 64 rows of Y; A = its first 128 rows (slices
+// 1-5 when 5k <= 128), B = all 6k rows, D = A B^T in tensor memory.  The
+// missing pair (6, 6) weighs 2^-80 of the column scales.  The epilogue folds
+// the 35 slice pairs of each entry in FP64 and scales by 2^(E_a + E_b).
+constexpr int OZ_KMAX = 24;         // 6 k <= 144 B rows, 5 k <= 128 A rows
+constexpr int OZ_ROWS = 1024;       // rows per CTA (exactness bound above)
+constexpr int OZ_SLICES = 6;
+constexpr int OZ_STAGE_ROWS = 64;   // rows of Y per operand tile (128 bytes of BF16)
+constexpr int OZ_NB = 4;            // operand tiles in flight
+constexpr int OZ_TILE_BYTES = 144 * 128;
+constexpr int OZ_THREADS = 256;     // warp 0: MMA + TMEM owner; warps 1-7 convert
+constexpr int OZ_TMEM_COLS = 256;
+constexpr int OZ_DST = 145;         // row stride of D in shared memory (odd: no bank conflicts)
+constexpr int OZ_AREA = 75776;      // >= max(tiles, 128 x OZ_DST floats), a multiple of 1024
+
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// E with max|y| < 2^(E-1) (clamped to the range where 2^-E is a normal float)
+__device__ __forceinline__ int oz_exp(unsigned mbits) {
+  const int eb = (int)(mbits >> 23);
+  const int E = mbits == 0 ? 0 : (eb == 0 ? -125 : eb - 125);
+  return min(max(E, -126), 126);
+}
+
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+    k_tc_gram_oz(const float* __restrict__ Y, int64_t ldy, int k, int64_t M, double* __restrict__ partial,
+                 int* __restrict__ err, uint64_t wait_ns) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const uint32_t s0 = saddr(smem_raw);
+  unsigned char* base = smem_raw + (((s0 + 1023u) & ~1023u) - s0);
+  static_assert(OZ_NB * OZ_TILE_BYTES <= OZ_AREA && 128 * OZ_DST * 4 <= OZ_AREA, "shared-memory area");
+  uint64_t* full = (uint64_t*)(base + OZ_AREA);
+  uint64_t* empty = full + OZ_NB;
+  uint64_t* done = empty + OZ_NB;
+  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  volatile int* abort = (volatile int*)(tmem_slot + 1);
+  int* Es = (int*)(tmem_slot + 2);    // OZ_KMAX column exponents
+  float* Dsm = (float*)base;          // 128 x OZ_DST FP32 after the contraction (aliases the tiles)
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t r0 = (int64_t)blockIdx.x * OZ_ROWS;
+  const int64_t r1 = min(M, r0 + OZ_ROWS);
+  const int nst = (int)((r1 - r0 + OZ_STAGE_ROWS - 1) / OZ_STAGE_ROWS);
+  const int NB_ = 6 * k;                 // B rows (MMA N)
+  const int Nmma = (NB_ + 15) / 16 * 16;
+
+  // rows of the tiles that no converter writes stay zero
+  for (int i = threadIdx.x; i < OZ_NB * OZ_TILE_BYTES / 16; i += OZ_THREADS) ((int4*)base)[i] = make_int4(0, 0, 0, 0);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < OZ_NB; ++s) {
+      mbar_init(&full[s], 7);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  fence_async_smem();
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(tmem_slot)),
+                 "r"(OZ_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(128, Nmma);
+      for (int st = 0; st < nst; ++st) {
+        const int b = st % OZ_NB;
+        if (!mbar_wait(&full[b], (st / OZ_NB) & 1, abort, wait_ns)) {
+          give_up(err, abort, 12);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t ta = saddr(base + b * OZ_TILE_BYTES);
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks)
+          mma_bf16(tmem, desc_sw128(ta + ks * 32), desc_sw128(ta + ks * 32), idesc, (st | ks) != 0 ? 1u : 0u);
+        mma_commit(&empty[b]);
+      }
+      mma_commit(done);
+    }
+  } else {
+    // converters: task (column a, 8-row group g) of each 64-row tile
+    const int ct = threadIdx.x - 32;
+    const bool has = ct < k * 8;
+    const int a = ct >> 3, g = ct & 7;
+    const float* src0 = Y + (int64_t)(has ? a : 0) * ldy + r0 + 8 * g;
+    auto load8 = [&](int st, float (&v)[8]) {
+      const int64_t rb = r0 + (int64_t)st * OZ_STAGE_ROWS + 8 * g;
+      const float* src = src0 + (int64_t)st * OZ_STAGE_ROWS;
+      if (!has || st >= nst) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = 0.f;
+      } else if (rb + 8 <= r1) {
+        const float4 p = *(const float4*)src, q = *(const float4*)(src + 4);
+        v[0] = p.x; v[1] = p.y; v[2] = p.z; v[3] = p.w; v[4] = q.x; v[5] = q.y; v[6] = q.z; v[7] = q.w;
+      } else {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = rb + u < r1 ? src[u] : 0.f;
+      }
+    };
+    // pass 1: this CTA's largest magnitude of column a (its 8 row groups are
+    // 8 consecutive lanes), all loads in flight; the scale 2^E_a is this CTA's
+    unsigned mb = 0;
+#pragma unroll 4
+    for (int st = 0; st < nst; ++st) {
+      float v[8];
+      load8(st, v);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) mb = max(mb, __float_as_uint(v[u]) & 0x7fffffffu);
+    }
+    mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, 1));
+    mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, 2));
+    mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, 4));
+    const int E = oz_exp(mb);
+    if (has && g == 0) Es[a] = E;
+    const float sc = __uint_as_float((unsigned)(127 - E) << 23);   // 2^-E
+    // pass 2: slices, with the next two tiles' loads in flight
+    float v0[8], v1[8], v2[8];
+    load8(0, v0);
+    load8(1, v1);
+    for (int st = 0; st < nst; ++st) {
+      const int b = st % OZ_NB;
+      load8(st + 2, v2);
+      if (st >= OZ_NB && !mbar_wait(&empty[b], ((st / OZ_NB) + 1) & 1, abort, wait_ns)) {
+        give_up(err, abort, 13);
+        break;
+      }
+      if (has) {
+        unsigned char* tile = base + b * OZ_TILE_BYTES;
+        float r[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) r[u] = v0[u] * sc;   // exact: a power-of-two scaling
+#pragma unroll
+        for (int i = 0; i < OZ_SLICES; ++i) {
+          const float up = __uint_as_float((unsigned)(127 + 8 * (i + 1)) << 23), dn = __uint_as_float((unsigned)(127 - 8 * (i + 1)) << 23);
+          uint32_t w[4];
+#pragma unroll
+          for (int u = 0; u < 8; u += 2) {
+            const float s0v = rintf(r[u] * up) * dn, s1v = rintf(r[u + 1] * up) * dn;   // exact slices
+            r[u] -= s0v;
+            r[u + 1] -= s1v;
+            const __nv_bfloat162 h = __floats2bfloat162_rn(s0v, s1v);
+            w[u >> 1] = *(const uint32_t*)&h;
+          }
+          // row (i, a), 16-byte chunk g of its 128 bytes, 128-byte swizzle
+          const int row = i * k + a;
+          *(uint4*)(tile + row * 128 + ((g ^ (row & 7)) << 4)) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+      }
+      fence_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&full[b]);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) { v0[u] = v1[u]; v1[u] = v2[u]; }
+    }
+  }
+
+  // epilogue: D (128 lanes x Nmma columns) to shared memory, then the fold
+  __syncwarp();
+  bool ok = true;
+  if (warp < 4) {
+    ok = nst > 0 && mbar_wait(done, 0, nullptr, wait_ns) && !*abort;
+    tc_fence_after();
+  }
+  __syncthreads();   // every converter is past its last tile; the tiles are free
+  __shared__ int all_ok;
+  if (threadIdx.x == 0) all_ok = 1;
+  __syncthreads();
+  if (warp < 4 && !ok) all_ok = 0;
+  __syncthreads();
+  const bool have = all_ok != 0;
+  if (warp < 4 && have) {
+    const int row = warp * 32 + lane;
+    for (int j0 = 0; j0 < Nmma; j0 += 8) {
+      float d[8];
+      tmem_ld8(tmem + ((uint32_t)(warp * 32) << 16) + j0, d);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) Dsm[row * OZ_DST + j0 + q] = d[q];
+    }
+  }
+  __syncthreads();
+  double* out = partial + (int64_t)blockIdx.x * k * k;
+  for (int e = threadIdx.x; e < k * k; e += OZ_THREADS) {
+    const int a = e % k, b2 = e / k;
+    if (a > b2) continue;
+    double s = 0.0;
+    if (have) {
+      // pairs (i, j) by increasing weight 2^-8(i+j): i < 5 from the A rows,
+      // (5, j < 5) from the transposed entry D[(j, b), (5, a)]; summed in
+      // double-float on the FP32 pipe (each term is exact), widened once
+      float hi = 0.f, lo = 0.f;
+      for (int w2 = 0; w2 <= 9; ++w2)
+        for (int i = 0; i < OZ_SLICES; ++i) {
+          const int j = w2 - i;
+          if (j < 0 || j >= OZ_SLICES || (i == 5 && j == 5)) continue;
+          const float t = i < 5 ? Dsm[(i * k + a) * OZ_DST + j * k + b2] : Dsm[(j * k + b2) * OZ_DST + 5 * k + a];
+          const float u = hi + t, bv = u - hi;
+          lo += (hi - (u - bv)) + (t - bv);
+          hi = u;
+        }
+      s = ldexp(f2d_int(hi) + f2d_int(lo), Es[a] + Es[b2]);
+    }
+    out[a + (int64_t)b2 * k] = s;
+    out[b2 + (int64_t)a * k] = s;
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_TMEM_COLS) : "memory");
+  }
+}
+
 }  // namespace
 
 // The kernel's dynamic shared-memory limit, shared by both launchers and
@@ -535,6 +779,40 @@ az_status launch_tc_tsgram_wide(const float* A, int64_t lda, int ka, const float
   k_tc_wide_reduce<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(partial, gx, ka, kb, G);
   AZ_CUDA(cudaGetLastError());
   return AZ_OK;
+}
+
+
+// ---------------------------------------------------------------- exact Gram launcher
+bool tc_gram_oz_ok(const void* Y, int64_t ldy, int k, int64_t M) {
+  return k >= 1 && k <= OZ_KMAX && M >= 1 && ldy % 4 == 0 && ((uintptr_t)Y & 15) == 0 && encode_fn() != nullptr;
+}
+
+int tc_gram_oz_blocks(int64_t M) { return (int)((M + OZ_ROWS - 1) / OZ_ROWS); }
+
+az_status launch_tc_gram_oz(const float* Y, int64_t ldy, int k, int64_t M, double* partial, double* G, int* err,
+                            cudaStream_t st) {
+  if (!tc_gram_oz_ok(Y, ldy, k, M) || !partial || !G || !err) {
+    set_error("tensor-core exact Gram: unsupported shape or alignment");
+    return AZ_ERR_ARG;
+  }
+  ProfScope ps("gram_oz", (double)M * k * 4.0, st, 2);
+  static std::once_flag once;
+  static cudaError_t attr_rc = cudaSuccess;
+  const size_t sm = 1024 + (size_t)OZ_AREA + (2 * OZ_NB + 1) * 8 + 8 + OZ_KMAX * 4 + 64;
+  std::call_once(once, [&] {
+    attr_rc = cudaFuncSetAttribute(k_tc_gram_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  });
+  AZ_CUDA(attr_rc);
+  const int nblk = tc_gram_oz_blocks(M);
+  k_tc_gram_oz<<<nblk, OZ_THREADS, sm, st>>>(Y, ldy, k, M, partial, err, WAIT_NS);
+  {
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      set_error(std::string("tensor-core exact Gram launch: ") + cudaGetErrorString(e));
+      return AZ_ERR_CUDA;
+    }
+  }
+  return launch_gram_reduce(partial, nblk, k, k, G, st);
 }
 
 }  // namespace az

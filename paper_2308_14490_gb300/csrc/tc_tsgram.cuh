@@ -28,6 +28,15 @@ bool tc_tsgram_wide_ok(const void* A, int64_t lda, int ka, const void* B, int64_
 size_t tc_tsgram_wide_partial(int64_t M, int ka, int kb);
 az_status launch_tc_tsgram_wide(const float* A, int64_t lda, int ka, const float* B, int64_t ldb, int kb, int64_t M,
                                 double* partial, double* G, int* err, cudaStream_t st);
+// Exact G = Y^T Y (k x k, FP64, column-major) for FP32 Y (M x k, ld ldy) on
+// the tensor cores: BF16 slices of the power-of-two-scaled columns, exact
+// per-CTA sums of every slice pair, folded in FP64.  k <= 24, ldy a multiple
+// of 4, Y 16-byte aligned.  partial: >= tc_gram_oz_blocks(M) * k * k doubles;
+// err as for launch_tc_tsgram.
+bool tc_gram_oz_ok(const void* Y, int64_t ldy, int k, int64_t M);
+int tc_gram_oz_blocks(int64_t M);
+az_status launch_tc_gram_oz(const float* Y, int64_t ldy, int k, int64_t M, double* partial, double* G, int* err,
+                            cudaStream_t st);
 // Test hook: the next launch stops issuing TMA copies at `iteration` (so its
 // consumers' waits run out) and bounds every wait by wait_ns.  One-shot.
 void tc_tsgram_debug_withhold(int iteration, uint64_t wait_ns);
