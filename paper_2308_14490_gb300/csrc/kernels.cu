@@ -1400,6 +1400,28 @@ __global__ void __launch_bounds__(S::THR, S::MINB) k_colfwd_r(Geom g_in, const i
     // buffer (keeps the stencil out of the unrolled first stage)
     const int tot = g.D0 << logC;
     const bool hasB = colB < in.k;
+    // FP32 1D windows of at most 16 taps: a point's window starts at tap
+    // 2W - ph (ph = its phase mod s), so the signed sum of 8 consecutive taps
+    // (+tap for a set Rademacher bit, -tap for a clear one) for a byte of bits
+    // is a table entry T[ph][chunk][byte], and v = T[ph][0][b0] + T[ph][1][b1]
+    float* tab = (float*)stg;
+    const bool use_tab = sizeof(T) == 4 && g.dim == 1 && (2 * in.Wx) / g.s[0] + 1 <= 16;
+    if (use_tab) {
+      const int s = g.s[0], W = in.Wx;
+      for (int e = threadIdx.x; e < s * 512; e += blockDim.x) {
+        const int byte = e & 255, ch = (e >> 8) & 1, ph = e >> 9;
+        float acc = 0.f;
+        for (int u = 0; u < 8; ++u) {
+          const int ti = 2 * W - ph - s * (8 * ch + u);
+          if (ti >= 0) {
+            const float tv = (float)__ldg(in.tapx + ti);
+            acc += ((byte >> u) & 1) ? tv : -tv;
+          }
+        }
+        tab[e] = acc;
+      }
+      __syncthreads();
+    }
     for (int t = threadIdx.x; t < tot; t += blockDim.x) {
       const int c = t & (C - 1), p = t >> logC;
       const int pos = (p << g.logD1) + c0 + c;
@@ -1420,11 +1442,19 @@ __global__ void __launch_bounds__(S::THR, S::MINB) k_colfwd_r(Geom g_in, const i
               const uint32_t* bbp = in.bits + (int64_t)colB * nw + w0;
               bitsB = (uint64_t)__ldg(bbp) | ((int64_t)(w0 + 1) < nw ? (uint64_t)__ldg(bbp + 1) << 32 : 0ull);
             }
-            for (int j = jlo; j <= jhi; ++j) {
-              const T tap = __ldg(in.tapx + (pos - s * j + W));
-              const int sh = j - (w0 << 5);
-              v.x += ((bitsA >> sh) & 1ull) ? tap : -tap;
-              v.y += ((bitsB >> sh) & 1ull) ? tap : -tap;
+            if (use_tab) {
+              const int sh = jlo - (w0 << 5);
+              const float* tp = tab + (W - pos + s * jlo) * 512;   // phase 2W - (pos + W - s jlo)
+              const unsigned bA = (unsigned)(bitsA >> sh) & 0xFFFFu, bB = (unsigned)(bitsB >> sh) & 0xFFFFu;
+              v.x = (T)(tp[bA & 255u] + tp[256 + (bA >> 8)]);
+              v.y = (T)(tp[bB & 255u] + tp[256 + (bB >> 8)]);
+            } else {
+              for (int j = jlo; j <= jhi; ++j) {
+                const T tap = __ldg(in.tapx + (pos - s * j + W));
+                const int sh = j - (w0 << 5);
+                v.x += ((bitsA >> sh) & 1ull) ? tap : -tap;
+                v.y += ((bitsB >> sh) & 1ull) ? tap : -tap;
+              }
             }
             if (!hasB) v.y = 0;
           } else {
@@ -1657,7 +1687,9 @@ az_status launch_colfwd_stencil(const Geom& g, const SketchIn<T>& in, int pair0,
   const bool fx = sizeof(T) == 4 && is_shape_21_1(g);
   const int C = fx ? 1 << AZ_COL_LC : reg_cols<T>(g.D0, g.D1);
   const int threads = C * (g.D0 / EPT<T>::E);
-  size_t sm = ((size_t)padix_host(g.D0 * C, PADC) + 32 + (g.dim == 2 ? (size_t)g.n[0] * C : 0)) * sizeof(V);
+  // after the FFT buffer: the 2D staging, or the 1D FP32 sign-sum tables (s x 512 floats)
+  const size_t extra = g.dim == 2 ? (size_t)g.n[0] * C * sizeof(V) : (sizeof(T) == 4 ? (size_t)g.s[0] * 512 * 4 : 0);
+  size_t sm = ((size_t)padix_host(g.D0 * C, PADC) + 32) * sizeof(V) + extra;
   auto kern = k_colfwd_r<T, 1, double, ShapeRT>;
   if (fx) kern = k_colfwd_r<T, 1, double, Shape1D<21, 1, AZ_COL_LC>>;
   if (set_smem(kern, sm) != cudaSuccess) { set_error("smem attribute"); return AZ_ERR_CUDA; }
