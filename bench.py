@@ -536,7 +536,8 @@ TRAFFIC_LABELS = [
     (r"^k_colfwd_r<float, 0", "colfwd_gather_f32"), (r"^k_colfwd_r<float, 1", "colfwd_sketch_f32"),
     (r"^k_rowfold_r<float", "rowfold_f32"), (r"^k_colinv_r<float", "colinv_f32"),
     (r"^k_stencil_rows<float", "stencil_rows_f32"), (r"^k_resid_df", "resid_df"),
-    (r"^k_update_x", "update_x"), (r"^k_tc_tsgram", "proj_tc"), (r"^k_gram_reduce", "gram_reduce"),
+    (r"^k_update_x", "update_x"), (r"^k_tc_tsgram", "proj_tc"), (r"^k_tc_gram_oz", "gram_oz"),
+    (r"^k_gram_reduce", "gram_reduce"),
     (r"^k_gram_partial", "gram_df32"), (r"^k_tsprod_df", "tsprod_df32"), (r"^k_tsprod<", "tsprod"),
     (r"^k_small_mm", "small_mm"), (r"^k_factor1", "factor1"), (r"^k_factor2", "factor2"),
     (r"^k_count|^k_scan_blocks|^k_scatter", "compact"), (r"^k_taps", "taps"),
@@ -713,6 +714,25 @@ def run_ours(args):
     e2e = {"value": e_val, "unit": "RHS/s",
            "h2d_bytes_per_step": int(b_host.nbytes), "d2h_bytes_per_step": int(x_pin.numel() * 8),
            "copies": "pinned host buffers; H2D and D2H on their own streams, double-buffered against the compute"}
+    # the same two copies alone on this machine (both directions at once, no
+    # compute): whether the end-to-end rate is bound by the link or the step
+    c_evs = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ncopy = 3
+    torch.cuda.synchronize(dev)
+    c_evs[0].record(h2d)
+    d2h.wait_stream(h2d)
+    for i in range(ncopy):
+        with torch.cuda.stream(h2d):
+            b_bufs[1].copy_(b_pin, non_blocking=True)
+        with torch.cuda.stream(d2h):
+            x_pins[1].copy_(x_bufs[1], non_blocking=True)
+    h2d.wait_stream(d2h)
+    c_evs[1].record(h2d)
+    torch.cuda.synchronize(dev)
+    copy_ms = c_evs[0].elapsed_time(c_evs[1]) / ncopy
+    e2e["copies_only_ms_per_step"] = round(copy_ms, 3)
+    e2e["compute_ms_per_step"] = round(total_ms / args.steps, 3)
+    e2e["bound_by"] = "copies" if copy_ms > total_ms / args.steps else "compute"
 
     # parity: relres of the mixed result vs the library's all-FP64 path on the same batch
     rr_mixed = az.az_solve(h, b_dev, x_dev, stream, relres=True)
